@@ -1,0 +1,215 @@
+/*
+ * slingbag.h -- C ABI of the GB300 (sm_103a) SlingBAG Pro hot path.
+ *
+ * The library renders a point cloud of spherical sources ("balls") onto an
+ * arbitrary array of oriented sensors (the differentiable radiator that
+ * Section 4.1 of the paper calls Simulate; Section 4.2, equation for y_sim;
+ * Section 4.3, equation for y_sim^(k)), gathers a trace-space gradient back
+ * onto every ball parameter (the backpropagation step of Algorithm 1), and
+ * filters and grows the cloud (zero-gradient filtering, Section 4.2 and
+ * Algorithm 1; destroy / split / duplicate, Section 4.1 and Algorithm 1).
+ *
+ * Conventions that hold for every entry point:
+ *  - Units: positions and radii in mm, time in microseconds, speed of sound
+ *    in mm/us, sampling frequency in MHz.
+ *  - A ball is (x, y, z, R, p0): centre, radius and initial pressure. A
+ *    point cloud is passed as five caller-owned device arrays of float32
+ *    (structure of arrays), each at least `n_cap` long.
+ *  - The current number of balls lives in DEVICE memory (`n_dev`, int32), so
+ *    that growth can change it without a host round trip; every kernel reads
+ *    it and the grid is sized from `n_cap`. Passing n_dev = NULL means
+ *    "n = n_cap".
+ *  - Traces are float32 row-major [M][T_k] device arrays owned by the caller.
+ *  - All work is enqueued on `stream` (a cudaStream_t passed as void*; NULL
+ *    is the legacy default stream); calls do not synchronise unless stated.
+ *  - Return value: SBP_OK or a negative sbp_status for argument or launch
+ *    errors, detected on the host before anything is enqueued where
+ *    possible. Device-side conditions (capacity overflow during growth) are
+ *    latched in the array object and reported by sbp_sync_status.
+ *  - No C++ exception crosses this boundary. sbp_last_error returns a
+ *    thread-local message describing the last failure.
+ */
+#ifndef SLINGBAG_H
+#define SLINGBAG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sbp_array_s* sbp_array; /* opaque; owned by the library */
+typedef void* sbp_stream;              /* cudaStream_t */
+
+typedef enum {
+    SBP_OK = 0,
+    SBP_ERR_ARG = -1,      /* invalid argument (null pointer, size, level) */
+    SBP_ERR_CUDA = -2,     /* a CUDA call or kernel launch failed */
+    SBP_ERR_CAPACITY = -3, /* growth would exceed n_cap (device-latched) */
+    SBP_ERR_LEVEL = -4,    /* level index out of range */
+    SBP_ERR_TIMEOUT = -5,  /* reserved: a bounded device wait gave up */
+    SBP_ERR_NUMERIC = -6   /* non-finite input detected */
+} sbp_status;
+
+/* Orientation weight w of a (sensor m, ball i) pair with unit normal n_m and
+ * unit direction u = (c_i - s_m)/|c_i - s_m|. The paper asks the method to
+ * handle "complex transducer orientations" (Section 1) and builds inward
+ * normals of the array envelope (Section 4.2) but prints no weighting law;
+ * this library reads it as the obliquity factor w = max(0, n.u). */
+enum { SBP_W_CLAMP = 0, SBP_W_NONE = 1, SBP_W_COS = 2 };
+
+/* Gradient components (bit mask). The coarse stage of Section 4.1 updates
+ * p0 and R only; the fine stage updates all five. */
+enum { SBP_MASK_P0 = 1, SBP_MASK_R = 2, SBP_MASK_XYZ = 4, SBP_MASK_ALL = 7 };
+
+/* sbp_filter_grow modes. The three zero-gradient rules are the readings of
+ * Section 4.2: Algorithm 1 keeps g < 0 (SBP_KEEP_NEG, default), the
+ * equations of Section 4.2 keep g <= 0 (SBP_KEEP_NONPOS), and a literal
+ * "drop exactly-zero gradients" keeps g != 0 (SBP_DROP_ZERO). SBP_GROW
+ * applies the growth rules of sbp_grow_params. */
+enum { SBP_KEEP_NEG = 0, SBP_KEEP_NONPOS = 1, SBP_DROP_ZERO = 2, SBP_GROW = 3 };
+
+/* Forward flags. Every forward of this library accumulates traces in
+ * fixed-point integers, so it is bitwise reproducible for any launch order;
+ * SBP_DETERMINISTIC is accepted for clarity and changes nothing. */
+enum { SBP_DETERMINISTIC = 1 };
+
+typedef struct {
+    float *x, *y, *z, *R, *p0;
+} sbp_balls;
+
+typedef struct {
+    float *gx, *gy, *gz, *gR, *gp0;
+} sbp_grads;
+
+typedef struct {
+    int weight_mode;      /* SBP_W_* (default SBP_W_CLAMP) */
+    int reserved[7];
+} sbp_params;
+
+/* Growth rules (Section 4.1 / Algorithm 1 name the operations; the paper
+ * gives no thresholds or geometry, so these are parameters). For ball i, in
+ * this order of precedence:
+ *   pruned      if prune_zero and every gradient component selected by
+ *               grad_mask is exactly zero;
+ *   destroyed   if destroy and (p0 < p_min or R < R_min);
+ *   split       if split and R > R_max: two balls at c +- (R/2) v, radius
+ *               R * 2^(-1/3), same p0, zero gradients and carried state;
+ *   duplicated  if duplicate and gx^2+gy^2+gz^2 > g_dup^2 (evaluated in
+ *               double): the ball is kept and followed by a clone at
+ *               c + (R/2) v with zero gradients and carried state;
+ *   kept        otherwise.
+ * v is a unit vector drawn from SplitMix64: three 24-bit draws
+ * u_r = mix(seed + (3i + r + 1) * 0x9E3779B97F4A7C15) >> 40, r = 0, 1, 2,
+ * mapped to (2 u_r + 1 - 2^24) / 2^24 and normalised. Output order is stable;
+ * children take their parent's place. */
+typedef struct {
+    float p_min, R_min, R_max, g_dup;
+    uint64_t seed;
+    int grad_mask;
+    int prune_zero, destroy, split, duplicate;
+} sbp_grow_params;
+
+/* Adam (the paper names no optimizer; Section 2.1 only fixes that both
+ * methods use the same learning rates). lr[] is per component in the order
+ * x, y, z, R, p0. */
+typedef struct {
+    float lr[5];
+    float beta1, beta2, eps;
+} sbp_adam_params;
+
+/* ---------------------------------------------------------------------- */
+
+/* Create a sensor array and its sampling hierarchy (Section 4.3:
+ * dt_k = f_k dt, T_k = T / f_k, rounded up when f_k does not divide T).
+ *   pos_host, normal_host: host float32 [M][3]; normals need not be unit
+ *                          length (they are normalised on the device copy).
+ *   M >= 1, c_mm_per_us > 0, fs_mhz > 0, T >= 1.
+ *   factors_host: host int32 [n_levels], each >= 1 (e.g. {4, 2, 1}).
+ *   n_cap: largest point cloud any later call will pass (sizes scratch).
+ *   params: may be NULL (defaults).
+ * The library copies the sensors to the device, allocates its scratch for
+ * the finest level and returns the handle in *out. The current level is 0. */
+int sbp_create_array(const float* pos_host, const float* normal_host, int M,
+                     double c_mm_per_us, double fs_mhz, int T, const int* factors_host,
+                     int n_levels, int n_cap, const sbp_params* params, sbp_array* out);
+
+int sbp_destroy_array(sbp_array arr);
+
+/* Samples T_k and sampling interval dt_k (us) of level k. */
+int sbp_level_info(sbp_array arr, int k, int* T_k, double* dt_k);
+
+/* Select level k (Section 4.3). If y_full_dev is not NULL, also write
+ * y_k = Downsample_{f_k}(y_full) into y_k_dev: block means of f_k samples,
+ * the record zero-padded to T_k * f_k (reading of the unspecified
+ * Downsample operator; under the cell-average sampling of sbp_forward it is
+ * exact: the level-k traces are block means of the level-0 traces).
+ *   y_full_dev: device float32 [M][T] (finest level), y_k_dev: [M][T_k]. */
+int sbp_set_sampling_level(sbp_array arr, int k, const float* y_full_dev, float* y_k_dev,
+                           sbp_stream stream);
+
+/* Differentiable radiator at the current level (Section 4.2, y_sim; the
+ * model of Section 4.1). Writes S_dev [M][T_k]:
+ *   S[m][j] = sum_i p0_i w_mi (E(e_a)^2 - E(e_b)^2) / (4 d_mi c dt_k),
+ *   e_a = d_mi - c j dt_k, e_b = e_a - c dt_k, E(e) = clamp(e, -R_i, R_i),
+ * i.e. the average over sample cell [j dt_k, (j+1) dt_k) of the uniform-sphere
+ * N-wave p0 w (d - c t)/(2 d) on |d - c t| < R. Pairs with d <= R contribute
+ * nothing (counted, see sbp_get_inside_pairs); samples outside [0, T_k) are
+ * dropped. flags: 0 or SBP_DETERMINISTIC. */
+int sbp_forward(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap, float* S_dev,
+                unsigned flags, sbp_stream stream);
+
+/* Residual of the per-level loss L = ||S - y_k||_2^2 (Section 4.2 and 4.3):
+ * G = 2 (S - y_k) into G_dev [M][T_k]; if loss_dev is not NULL the loss is
+ * written there as one double (a fixed-order reduction, reproducible).
+ * S_dev may be NULL, meaning S = 0 (the all-zero-pressure forward of
+ * zero-gradient filtering). */
+int sbp_residual(sbp_array arr, const float* S_dev, const float* y_k_dev, float* G_dev,
+                 double* loss_dev, sbp_stream stream);
+
+/* Adjoint of sbp_forward at the current level: given G = dL/dS [M][T_k],
+ * writes every ball's dL/dx, dL/dy, dL/dz, dL/dR, dL/dp0 into `out`
+ * (overwritten, each written exactly once; components outside grad_mask are
+ * written as zero). Gradients are derived from the forward's closed form
+ * (the paper prints none). */
+int sbp_adjoint(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap,
+                const float* G_dev, sbp_grads out, unsigned grad_mask, sbp_stream stream);
+
+/* Filter and grow the point cloud in place (stable compaction/expansion).
+ * mode SBP_KEEP_NEG / SBP_KEEP_NONPOS / SBP_DROP_ZERO: zero-gradient
+ * filtering on grads.gp0 (computed by sbp_adjoint with G = -2 y_k, i.e.
+ * sbp_residual with S = NULL); p0 itself is untouched, which restores the
+ * original pressures of the kept balls as Section 4.2 prescribes.
+ * mode SBP_GROW: the rules of sbp_grow_params (gp must not be NULL).
+ * Balls, grads and the n_extra carried arrays extra[e] (float32, n_cap each,
+ * e.g. Adam moments) are permuted together; *n_dev is updated on the device.
+ * If the result would exceed n_cap, nothing changes and SBP_ERR_CAPACITY is
+ * latched (see sbp_sync_status). n_extra <= 16. */
+int sbp_filter_grow(sbp_array arr, sbp_balls balls, sbp_grads grads, float* const* extra,
+                    int n_extra, int* n_dev, int n_cap, const sbp_grow_params* gp, int mode,
+                    sbp_stream stream);
+
+/* One Adam step at step count t >= 1 on the components in mask; m and v
+ * are the first and second moments, laid out like the balls. */
+int sbp_adam_step(sbp_array arr, sbp_balls balls, sbp_grads grads, sbp_balls m, sbp_balls v,
+                  const int* n_dev, int n_cap, int t, const sbp_adam_params* ap,
+                  unsigned mask, sbp_stream stream);
+
+/* Synchronise `stream`, then return SBP_OK or the first device-latched
+ * status since the last call (which is cleared). */
+int sbp_sync_status(sbp_array arr, sbp_stream stream);
+
+/* Pairs with d <= R skipped so far (synchronises `stream`). */
+int sbp_get_inside_pairs(sbp_array arr, sbp_stream stream, long long* count);
+
+/* Thread-local description of the last error (never NULL). */
+const char* sbp_last_error(void);
+
+/* Library version string. */
+const char* sbp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLINGBAG_H */

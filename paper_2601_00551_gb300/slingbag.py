@@ -1,0 +1,305 @@
+"""Thin Python binding of libslingbag (the sm_103a SlingBAG Pro hot path).
+
+Argument marshalling only: every step runs in the CUDA library through its
+C ABI (include/slingbag.h). PyTorch supplies device memory and the current
+stream. There is no CPU fallback: if the library is missing or no GPU is
+present, the calls raise.
+
+Point clouds are (5, n_cap) float32 CUDA tensors with rows x, y, z, R, p0;
+gradients and optimizer moments use the same layout. The live ball count can
+be a Python int or a one-element int32 CUDA tensor (kept on the device so
+that growth needs no host round trip).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libslingbag.so")
+
+SBP_OK = 0
+W_MODES = {"clamp": 0, "none": 1, "cos": 2}
+MASK_P0, MASK_R, MASK_XYZ, MASK_ALL = 1, 2, 4, 7
+KEEP_NEG, KEEP_NONPOS, DROP_ZERO, GROW = 0, 1, 2, 3
+
+_P = ctypes.c_void_p
+
+
+class SlingbagError(RuntimeError):
+    def __init__(self, fn: str, code: int, msg: str):
+        super().__init__(f"{fn} failed with status {code}: {msg}")
+        self.code = code
+
+
+class _Balls(ctypes.Structure):
+    _fields_ = [("x", _P), ("y", _P), ("z", _P), ("R", _P), ("p0", _P)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("weight_mode", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
+class _GrowParams(ctypes.Structure):
+    _fields_ = [("p_min", ctypes.c_float), ("R_min", ctypes.c_float), ("R_max", ctypes.c_float),
+                ("g_dup", ctypes.c_float), ("seed", ctypes.c_uint64), ("grad_mask", ctypes.c_int),
+                ("prune_zero", ctypes.c_int), ("destroy", ctypes.c_int), ("split", ctypes.c_int),
+                ("duplicate", ctypes.c_int)]
+
+
+class _AdamParams(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float * 5), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float)]
+
+
+_lib = None
+
+# name -> (restype, argtypes); the C ABI of include/slingbag.h
+_SIGS = {
+    "sbp_version": (ctypes.c_char_p, []),
+    "sbp_last_error": (ctypes.c_char_p, []),
+    "sbp_create_array": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_int, _P, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(_Params), ctypes.POINTER(_P)]),
+    "sbp_destroy_array": (ctypes.c_int, [_P]),
+    "sbp_level_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "sbp_set_sampling_level": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
+    "sbp_forward": (ctypes.c_int, [_P, _Balls, _P, ctypes.c_int, _P, ctypes.c_uint, _P]),
+    "sbp_residual": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "sbp_adjoint": (ctypes.c_int, [_P, _Balls, _P, ctypes.c_int, _P, _Balls, ctypes.c_uint, _P]),
+    "sbp_filter_grow": (ctypes.c_int, [_P, _Balls, _Balls, ctypes.POINTER(_P), ctypes.c_int, _P,
+                                       ctypes.c_int, ctypes.POINTER(_GrowParams), ctypes.c_int,
+                                       _P]),
+    "sbp_adam_step": (ctypes.c_int, [_P, _Balls, _Balls, _Balls, _Balls, _P, ctypes.c_int,
+                                     ctypes.c_int, ctypes.POINTER(_AdamParams), ctypes.c_uint,
+                                     _P]),
+    "sbp_sync_status": (ctypes.c_int, [_P, _P]),
+    "sbp_get_inside_pairs": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_longlong)]),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libslingbag.so (built by `paper_2601_00551_gb300.build`)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libslingbag is not built ({path} missing); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(fn: str, code: int):
+    if code != SBP_OK:
+        raise SlingbagError(fn, code, load_library().sbp_last_error().decode())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _rows(t: torch.Tensor) -> _Balls:
+    if t.dtype != torch.float32 or not t.is_cuda or t.dim() != 2 or t.shape[0] != 5 \
+            or not t.is_contiguous():
+        raise ValueError("expected a contiguous (5, n) float32 CUDA tensor")
+    base, stride = t.data_ptr(), t.stride(0) * 4
+    return _Balls(*(base + k * stride for k in range(5)))
+
+
+def _dptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+@dataclasses.dataclass
+class GrowParams:
+    """Growth thresholds (see sbp_grow_params in include/slingbag.h)."""
+    p_min: float = 1e-3
+    R_min: float = 0.02
+    R_max: float = 0.3
+    g_dup: float = 1e30
+    seed: int = 0
+    grad_mask: int = MASK_ALL
+    prune_zero: bool = True
+    destroy: bool = True
+    split: bool = True
+    duplicate: bool = False
+
+    def c(self) -> _GrowParams:
+        return _GrowParams(self.p_min, self.R_min, self.R_max, self.g_dup,
+                           self.seed & ((1 << 64) - 1), self.grad_mask, int(self.prune_zero),
+                           int(self.destroy), int(self.split), int(self.duplicate))
+
+
+@dataclasses.dataclass
+class AdamParams:
+    lr: tuple = (1e-3, 1e-3, 1e-3, 1e-3, 1e-2)  # x, y, z, R, p0
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+
+    def c(self) -> _AdamParams:
+        return _AdamParams((ctypes.c_float * 5)(*self.lr), self.beta1, self.beta2, self.eps)
+
+
+class SensorArray:
+    """A sensor array with its sampling hierarchy (sbp_create_array)."""
+
+    def __init__(self, pos, normal, c: float, fs_mhz: float, T: int, factors=(1,),
+                 n_cap: int = 1, weight_mode: str = "clamp", device=None):
+        self._lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libslingbag needs a CUDA GPU")
+        if device is not None:
+            torch.cuda.set_device(device)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float32).reshape(-1, 3))
+        nrm = np.ascontiguousarray(np.asarray(normal, dtype=np.float32).reshape(-1, 3))
+        if pos.shape != nrm.shape:
+            raise ValueError("pos and normal must both be (M, 3)")
+        fac = np.ascontiguousarray(np.asarray(factors, dtype=np.int32))
+        self.M, self.T, self.n_cap = pos.shape[0], int(T), int(n_cap)
+        self.c, self.fs = float(c), float(fs_mhz)
+        self.factors = tuple(int(f) for f in fac)
+        params = _Params(W_MODES[weight_mode])
+        h = _P()
+        torch.cuda.synchronize()
+        _check("sbp_create_array", self._lib.sbp_create_array(
+            pos.ctypes.data, nrm.ctypes.data, self.M, self.c, self.fs, self.T,
+            fac.ctypes.data, len(fac), self.n_cap, ctypes.byref(params), ctypes.byref(h)))
+        self._h = h
+        self.level = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sbp_destroy_array(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ levels
+    def level_info(self, k: int):
+        T = ctypes.c_int()
+        dt = ctypes.c_double()
+        _check("sbp_level_info", self._lib.sbp_level_info(self._h, k, ctypes.byref(T),
+                                                          ctypes.byref(dt)))
+        return T.value, dt.value
+
+    @property
+    def Tk(self) -> int:
+        return self.level_info(self.level)[0]
+
+    def set_sampling_level(self, k: int, y_full: torch.Tensor | None = None,
+                           out: torch.Tensor | None = None):
+        """Select level k; with y_full (M, T) also return Downsample_{f_k}(y_full)."""
+        Tk = self.level_info(k)[0]
+        if y_full is not None:
+            self._check_traces(y_full, self.T)
+            if out is None:
+                out = torch.empty((self.M, Tk), dtype=torch.float32, device=self.device)
+            self._check_traces(out, Tk)
+        _check("sbp_set_sampling_level", self._lib.sbp_set_sampling_level(
+            self._h, k, _dptr(y_full), _dptr(out if y_full is not None else None), _stream()))
+        self.level = k
+        return out
+
+    def _check_traces(self, t, T):
+        if t.dtype != torch.float32 or not t.is_cuda or tuple(t.shape) != (self.M, T) \
+                or not t.is_contiguous():
+            raise ValueError(f"expected a contiguous ({self.M}, {T}) float32 CUDA tensor")
+
+    def _n(self, n, n_cap):
+        if n is None or isinstance(n, torch.Tensor):
+            if n is not None and (n.dtype != torch.int32 or not n.is_cuda):
+                raise ValueError("n must be an int32 CUDA tensor")
+            return n
+        return torch.tensor([int(n)], dtype=torch.int32, device=self.device)
+
+    # ----------------------------------------------------------------- hot path
+    def forward(self, balls: torch.Tensor, n=None, out: torch.Tensor | None = None):
+        """Traces S (M, T_k) at the current level (sbp_forward)."""
+        Tk = self.Tk
+        if out is None:
+            out = torch.empty((self.M, Tk), dtype=torch.float32, device=self.device)
+        self._check_traces(out, Tk)
+        nd = self._n(n, balls.shape[1])
+        _check("sbp_forward", self._lib.sbp_forward(self._h, _rows(balls), _dptr(nd),
+                                                    balls.shape[1], _dptr(out), 0, _stream()))
+        return out
+
+    def residual(self, S: torch.Tensor | None, y_k: torch.Tensor, G: torch.Tensor | None = None,
+                 loss: torch.Tensor | None = None, want_loss: bool = True):
+        """G = 2 (S - y_k) and L = ||S - y_k||^2 (sbp_residual); S=None means S = 0."""
+        Tk = self.Tk
+        self._check_traces(y_k, Tk)
+        if S is not None:
+            self._check_traces(S, Tk)
+        if G is None:
+            G = torch.empty((self.M, Tk), dtype=torch.float32, device=self.device)
+        if want_loss and loss is None:
+            loss = torch.zeros(1, dtype=torch.float64, device=self.device)
+        _check("sbp_residual", self._lib.sbp_residual(self._h, _dptr(S), _dptr(y_k), _dptr(G),
+                                                      _dptr(loss if want_loss else None),
+                                                      _stream()))
+        return G, loss
+
+    def adjoint(self, balls: torch.Tensor, G: torch.Tensor, n=None, mask: int = MASK_ALL,
+                out: torch.Tensor | None = None):
+        """Per-ball gradients (5, n_cap) in the order x, y, z, R, p0 (sbp_adjoint)."""
+        self._check_traces(G, self.Tk)
+        if out is None:
+            out = torch.empty_like(balls)
+        nd = self._n(n, balls.shape[1])
+        _check("sbp_adjoint", self._lib.sbp_adjoint(self._h, _rows(balls), _dptr(nd),
+                                                    balls.shape[1], _dptr(G), _rows(out),
+                                                    mask, _stream()))
+        return out
+
+    def filter_grow(self, balls: torch.Tensor, grads: torch.Tensor, n_dev: torch.Tensor,
+                    mode: int = KEEP_NEG, grow: GrowParams | None = None, extra=()):
+        """Filter/grow in place (sbp_filter_grow); n_dev is updated on the device."""
+        ex = []
+        for t in extra:
+            if t.dim() == 2:
+                ex.extend(t[k] for k in range(t.shape[0]))
+            else:
+                ex.append(t)
+        for t in ex:
+            if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() \
+                    or t.numel() < balls.shape[1]:
+                raise ValueError("extra arrays must be contiguous float32 CUDA tensors of n_cap")
+        arr = (_P * max(1, len(ex)))(*[t.data_ptr() for t in ex])
+        gp = grow.c() if grow is not None else None
+        _check("sbp_filter_grow", self._lib.sbp_filter_grow(
+            self._h, _rows(balls), _rows(grads), arr, len(ex), _dptr(n_dev), balls.shape[1],
+            ctypes.byref(gp) if gp is not None else None, mode, _stream()))
+
+    def adam_step(self, balls, grads, m, v, t: int, ap: AdamParams, n=None,
+                  mask: int = MASK_ALL):
+        nd = self._n(n, balls.shape[1])
+        p = ap.c()
+        _check("sbp_adam_step", self._lib.sbp_adam_step(
+            self._h, _rows(balls), _rows(grads), _rows(m), _rows(v), _dptr(nd), balls.shape[1],
+            int(t), ctypes.byref(p), mask, _stream()))
+
+    def sync_status(self) -> int:
+        return int(self._lib.sbp_sync_status(self._h, _stream()))
+
+    def inside_pairs(self) -> int:
+        c = ctypes.c_longlong()
+        _check("sbp_get_inside_pairs", self._lib.sbp_get_inside_pairs(self._h, _stream(),
+                                                                       ctypes.byref(c)))
+        return c.value

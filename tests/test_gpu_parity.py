@@ -1,0 +1,373 @@
+"""GPU parity: the sm_103a library, called through its C ABI, against the FP64
+oracle on identical seeded inputs.
+
+Bars (from the method's accuracy target): traces within relative L2 1e-5,
+gradients within relative L2 1e-4 per component, integer decisions (which
+balls survive filtering, which split or duplicate, in which order)
+identical outside the oracle's list of sign-ambiguous balls.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TRACE_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def sb():
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_2601_00551_gb300 import slingbag
+
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    return slingbag
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def threads():
+    return max(1, oracle.num_procs())
+
+
+def make_array(sb, wl, factors, n_cap, wmode="clamp"):
+    return sb.SensorArray(wl.sensors.pos, wl.sensors.normal, wl.c, wl.fs_mhz, wl.T, factors,
+                          n_cap=n_cap, weight_mode=wmode)
+
+
+def dt_of(wl, f):
+    return f / wl.fs_mhz
+
+
+# ------------------------------------------------------------------ forward
+
+@pytest.mark.parametrize("wmode", ["clamp", "cos", "none"])
+def test_forward_tiny_all_levels(sb, wmode):
+    wl = workloads.tiny()
+    b = wl.init.stack()
+    arr = make_array(sb, wl, (4, 2, 1), b.shape[1], wmode)
+    balls = torch.from_numpy(b).cuda()
+    for k, f in enumerate((4, 2, 1)):
+        arr.set_sampling_level(k)
+        S = arr.forward(balls).cpu().numpy()
+        ref = oracle.forward(b, wl.sensors.pos, wl.sensors.normal, wl.c, dt_of(wl, f),
+                             wl.T // f, wmode=wmode, threads=threads())
+        assert np.count_nonzero(ref) > 0
+        e = rel_l2(S, ref)
+        assert e <= TRACE_TOL, (f, e)
+        # element-wise: no single sample far off
+        assert np.max(np.abs(S - ref)) <= 1e-4 * np.max(np.abs(ref))
+
+
+def test_forward_is_bitwise_deterministic_and_order_independent(sb):
+    wl = workloads.tiny()
+    b = wl.init.stack()
+    arr = make_array(sb, wl, (1,), b.shape[1])
+    S1 = arr.forward(torch.from_numpy(b).cuda()).cpu().numpy()
+    S2 = arr.forward(torch.from_numpy(b).cuda()).cpu().numpy()
+    perm = np.random.default_rng(0).permutation(b.shape[1])
+    S3 = arr.forward(torch.from_numpy(np.ascontiguousarray(b[:, perm])).cuda()).cpu().numpy()
+    assert np.array_equal(S1, S2)
+    assert np.array_equal(S1, S3)
+
+
+def test_forward_edge_cases(sb):
+    wl = workloads.tiny(M=8, T=600)
+    pos, nrm = wl.sensors.pos, wl.sensors.normal
+    cap = 1000
+    arr = make_array(sb, wl, (3, 1), cap)   # 600 / 3 = 200 samples at level 0
+    rng = np.random.default_rng(4)
+    b = wl.init.stack()[:, :cap].copy()
+    # a few balls beyond the record, one on top of sensor 0 (d <= R), one with p0 = 0
+    b[:3, 0] = [0.0, 0.0, 60.0]
+    b[:3, 1] = pos[0] + np.float32(0.01)
+    b[3, 1] = 0.2
+    b[4, 2] = 0.0
+    balls = torch.from_numpy(b).cuda()
+    for k, f in enumerate((3, 1)):
+        arr.set_sampling_level(k)
+        Tk = -(-600 // f)
+        # ragged live count: garbage beyond n must be ignored
+        for n in (0, 1, 37, 513, cap):
+            junk = balls.clone()
+            junk[:, n:] = torch.from_numpy(rng.normal(size=(5, cap - n)).astype(np.float32)).cuda()
+            S = arr.forward(junk, n=n).cpu().numpy()
+            ref, inside = oracle.forward(b[:, :n], pos, nrm, wl.c, dt_of(wl, f), Tk,
+                                         return_inside=True)
+            if n == 0:
+                assert np.all(S == 0)
+            else:
+                assert rel_l2(S, ref) <= TRACE_TOL, (f, n)
+    # the d <= R pair is counted (once per forward that sees it)
+    assert arr.inside_pairs() > 0
+
+
+def test_forward_vessel_sampled_sensors(sb):
+    """Full-size vessel workload (200k balls, 512 sensors, T = 4096 at 40 MHz and
+    the 10 / 20 MHz levels) in the benchmark's launch configuration; the oracle
+    evaluates a sample of sensors exactly."""
+    wl = workloads.vessel()
+    b = wl.init.stack()
+    arr = make_array(sb, wl, wl.levels, b.shape[1])
+    balls = torch.from_numpy(b).cuda()
+    pick = np.array([0, 77, 255, 300, 511])
+    for k, f in enumerate(wl.levels):
+        arr.set_sampling_level(k)
+        S = arr.forward(balls).cpu().numpy()
+        ref = oracle.forward(b, wl.sensors.pos[pick], wl.sensors.normal[pick], wl.c,
+                             dt_of(wl, f), wl.T // f, threads=threads())
+        e = rel_l2(S[pick], ref)
+        assert e <= TRACE_TOL, (f, e)
+
+
+# ---------------------------------------------------------- residual, level
+
+def test_downsample_and_residual(sb):
+    wl = workloads.tiny(M=16, T=1000)
+    rng = np.random.default_rng(1)
+    y = rng.normal(size=(16, 1000)).astype(np.float32)
+    arr = make_array(sb, wl, (8, 3, 1), 10)
+    for k, f in enumerate((8, 3, 1)):
+        yk = arr.set_sampling_level(k, torch.from_numpy(y).cuda()).cpu().numpy()
+        np.testing.assert_allclose(yk, oracle.downsample(y, f), rtol=1e-6, atol=1e-6)
+    arr.set_sampling_level(2)
+    S = rng.normal(size=(16, 1000)).astype(np.float32)
+    G, loss = arr.residual(torch.from_numpy(S).cuda(), torch.from_numpy(y).cuda())
+    L_ref, G_ref = oracle.loss_and_residual(S, y)
+    np.testing.assert_allclose(G.cpu().numpy(), G_ref, rtol=1e-6, atol=1e-6)
+    assert abs(loss.item() - L_ref) <= 1e-9 * L_ref
+    G0, _ = arr.residual(None, torch.from_numpy(y).cuda(), want_loss=False)
+    np.testing.assert_array_equal(G0.cpu().numpy(), -2 * y)
+    # reproducible loss
+    _, loss2 = arr.residual(torch.from_numpy(S).cuda(), torch.from_numpy(y).cuda())
+    assert loss2.item() == loss.item()
+
+
+# ------------------------------------------------------------------ adjoint
+
+_MEASURED = {}
+
+
+def _measured(wl, f, noise=True):
+    """'Measured' traces: the oracle's forward of the ground-truth cloud at the
+    finest level, rounded to float32, plus 1% Gaussian noise."""
+    key = (wl.name, noise)
+    if key not in _MEASURED:
+        y = oracle.forward(wl.truth.stack(), wl.sensors.pos, wl.sensors.normal, wl.c,
+                           dt_of(wl, 1), wl.T, threads=threads())
+        y = y.astype(np.float32)
+        _MEASURED[key] = workloads.add_noise(y) if noise else y
+    return _MEASURED[key]
+
+
+@pytest.mark.parametrize("wmode", ["clamp", "cos"])
+def test_adjoint_tiny_all_components(sb, wmode):
+    wl = workloads.tiny()
+    b = wl.init.stack()
+    n = b.shape[1]
+    arr = make_array(sb, wl, (4, 1), n, wmode)
+    y = _measured(wl, 1)
+    balls = torch.from_numpy(b).cuda()
+    for k, f in enumerate((4, 1)):
+        Tk = wl.T // f
+        S = oracle.forward(b, wl.sensors.pos, wl.sensors.normal, wl.c, dt_of(wl, f), Tk,
+                           wmode=wmode, threads=threads())
+        yk = oracle.downsample(y, f)
+        G = (2.0 * (S - yk)).astype(np.float32)
+        arr.set_sampling_level(k)
+        g = arr.adjoint(balls, torch.from_numpy(G).cuda()).cpu().numpy()
+        ref = oracle.adjoint(b, wl.sensors.pos, wl.sensors.normal, wl.c, dt_of(wl, f), Tk,
+                             G.astype(np.float64), wmode=wmode, threads=threads())
+        for c in range(5):
+            e = rel_l2(g[c], ref[c])
+            assert e <= GRAD_TOL, (f, c, e)
+        gc = arr.adjoint(balls, torch.from_numpy(G).cuda(), mask=sb.MASK_P0 | sb.MASK_R)
+        gc = gc.cpu().numpy()
+        assert np.all(gc[:3] == 0)
+        np.testing.assert_array_equal(gc[3:], g[3:])
+
+
+def test_adjoint_small_cloud_splits_sensors(sb):
+    """Few balls: the sensors are split across CTAs and reduced in fixed order."""
+    wl = workloads.tiny(n_init=150)
+    b = wl.init.stack()
+    arr = make_array(sb, wl, (1,), b.shape[1])
+    rng = np.random.default_rng(2)
+    G = rng.normal(size=(wl.sensors.M, wl.T)).astype(np.float32)
+    g1 = arr.adjoint(torch.from_numpy(b).cuda(), torch.from_numpy(G).cuda()).cpu().numpy()
+    g2 = arr.adjoint(torch.from_numpy(b).cuda(), torch.from_numpy(G).cuda()).cpu().numpy()
+    assert np.array_equal(g1, g2)
+    ref = oracle.adjoint(b, wl.sensors.pos, wl.sensors.normal, wl.c, dt_of(wl, 1), wl.T,
+                         G.astype(np.float64))
+    for c in range(5):
+        assert rel_l2(g1[c], ref[c]) <= GRAD_TOL, c
+
+
+def test_adjoint_vessel_sampled_balls(sb):
+    """Full-size vessel workload: gradients of a sample of balls at each level,
+    against the oracle's, for G = -2 y_k (the zero-gradient pass)."""
+    wl = workloads.vessel()
+    b = wl.init.stack()
+    arr = make_array(sb, wl, wl.levels, b.shape[1])
+    y = _measured(wl, 1, noise=True)
+    balls = torch.from_numpy(b).cuda()
+    pick = np.random.default_rng(5).choice(b.shape[1], 300, replace=False)
+    for k, f in enumerate(wl.levels):
+        yk = arr.set_sampling_level(k, torch.from_numpy(y).cuda())
+        G, _ = arr.residual(None, yk, want_loss=False)
+        g = arr.adjoint(balls, G).cpu().numpy()
+        Gref = -2.0 * oracle.downsample(y, f)
+        ref = oracle.adjoint(b[:, pick], wl.sensors.pos, wl.sensors.normal, wl.c, dt_of(wl, f),
+                             wl.T // f, Gref, threads=threads())
+        for c in range(5):
+            e = rel_l2(g[c, pick], ref[c])
+            assert e <= GRAD_TOL, (f, c, e)
+
+
+# --------------------------------------------------------- filtering, growth
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_zero_gradient_filter_survivors(sb, mode):
+    wl = workloads.tiny()
+    b = wl.init.stack()
+    n = b.shape[1]
+    arr = make_array(sb, wl, (4, 1), n)
+    y = _measured(wl, 1)
+    yk = arr.set_sampling_level(0, torch.from_numpy(y).cuda())
+    G, _ = arr.residual(None, yk, want_loss=False)
+    balls = torch.from_numpy(b).cuda()
+    g = arr.adjoint(balls, G, mask=sb.MASK_P0)
+    n_dev = torch.tensor([n], dtype=torch.int32, device="cuda")
+    arr.filter_grow(balls, g, n_dev, mode=mode)
+    assert arr.sync_status() == 0
+    n_new = int(n_dev.item())
+    keep, gref, amb = oracle.zero_gradient_filter(
+        b, wl.sensors.pos, wl.sensors.normal, wl.c, dt_of(wl, 4), wl.T // 4,
+        oracle.downsample(y, 4), mode=mode)
+    assert amb.size == 0, f"{amb.size} sign-ambiguous balls"
+    assert n_new == keep.size
+    np.testing.assert_array_equal(balls[:, :n_new].cpu().numpy(), b[:, keep])
+    # roughly half the random balls survive (the paper retains 106,924 of 200,000)
+    if mode == 0:
+        assert 0.2 * n < n_new < 0.9 * n
+
+
+def test_zero_gradient_filter_vessel(sb):
+    wl = workloads.vessel()
+    b = wl.init.stack()
+    n = b.shape[1]
+    arr = make_array(sb, wl, wl.levels, n)
+    y = _measured(wl, 1)
+    yk = arr.set_sampling_level(0, torch.from_numpy(y).cuda())
+    G, _ = arr.residual(None, yk, want_loss=False)
+    balls = torch.from_numpy(b).cuda()
+    g = arr.adjoint(balls, G, mask=sb.MASK_P0)
+    gp = g[4].cpu().numpy()
+    n_dev = torch.tensor([n], dtype=torch.int32, device="cuda")
+    arr.filter_grow(balls, g, n_dev, mode=sb.KEEP_NEG)
+    n_new = int(n_dev.item())
+    keep, gref, amb = oracle.zero_gradient_filter(
+        b, wl.sensors.pos, wl.sensors.normal, wl.c, dt_of(wl, wl.levels[0]),
+        wl.T // wl.levels[0], oracle.downsample(y, wl.levels[0]), threads=threads())
+    amb_set = set(amb.tolist())
+    gpu_keep = set(np.nonzero(gp < 0)[0].tolist())
+    ref_keep = set(keep.tolist())
+    assert (gpu_keep ^ ref_keep) <= amb_set
+    assert n_new == len(gpu_keep)
+    assert len(amb_set) <= 1e-3 * n
+
+
+def _grow_case(rng, n):
+    b = np.stack([rng.uniform(-5, 5, n), rng.uniform(-5, 5, n), rng.uniform(-5, 5, n),
+                  rng.uniform(0.0, 0.6, n), rng.uniform(-0.01, 1.0, n)]).astype(np.float32)
+    g = rng.normal(size=(5, n)).astype(np.float32)
+    g[:, rng.random(n) < 0.1] = 0.0
+    g[:3, rng.random(n) < 0.1] = 0.0
+    return b, g
+
+
+@pytest.mark.parametrize("duplicate,mask", [(False, 3), (True, 7)])
+def test_grow_matches_oracle(sb, duplicate, mask):
+    rng = np.random.default_rng(7 + int(duplicate))
+    n, cap = 3000, 7000
+    b, g = _grow_case(rng, n)
+    ex = rng.normal(size=(4, n)).astype(np.float32)
+    gp = oracle.GrowParams(seed=12345, grad_mask=mask, duplicate=duplicate, g_dup=1.5)
+    nb, ng, ne, counts = oracle.grow(b, g, ex, gp)
+    wl = workloads.tiny(M=4, T=64)
+    arr = make_array(sb, wl, (1,), cap)
+    B = torch.zeros((5, cap), device="cuda")
+    Gt = torch.zeros((5, cap), device="cuda")
+    E = torch.zeros((4, cap), device="cuda")
+    B[:, :n] = torch.from_numpy(b)
+    Gt[:, :n] = torch.from_numpy(g)
+    E[:, :n] = torch.from_numpy(ex)
+    n_dev = torch.tensor([n], dtype=torch.int32, device="cuda")
+    arr.filter_grow(B, Gt, n_dev, mode=sb.GROW,
+                    grow=sb.GrowParams(seed=12345, grad_mask=mask, duplicate=duplicate,
+                                       g_dup=1.5),
+                    extra=[E])
+    assert arr.sync_status() == 0
+    m = int(n_dev.item())
+    assert m == nb.shape[1]
+    Bo, Go, Eo = B[:, :m].cpu().numpy(), Gt[:, :m].cpu().numpy(), E[:, :m].cpu().numpy()
+    np.testing.assert_array_equal(Bo[3:], nb[3:])          # R, p0 bit-exact
+    np.testing.assert_allclose(Bo[:3], nb[:3], rtol=0, atol=2e-6)
+    np.testing.assert_array_equal(Go, ng)
+    np.testing.assert_array_equal(Eo, ne)
+
+
+def test_grow_capacity_overflow_is_latched(sb):
+    rng = np.random.default_rng(3)
+    n = 900
+    b, g = _grow_case(rng, n)
+    b[3] = 0.5  # every ball splits
+    b[4] = 0.5
+    g[:] = 1.0
+    wl = workloads.tiny(M=4, T=64)
+    arr = make_array(sb, wl, (1,), 1000)
+    B = torch.zeros((5, 1000), device="cuda")
+    B[:, :n] = torch.from_numpy(b)
+    Gt = torch.ones((5, 1000), device="cuda")
+    before = B.clone()
+    n_dev = torch.tensor([n], dtype=torch.int32, device="cuda")
+    arr.filter_grow(B, Gt, n_dev, mode=sb.GROW, grow=sb.GrowParams())
+    assert arr.sync_status() == -3
+    assert int(n_dev.item()) == n
+    assert torch.equal(B, before)
+    assert arr.sync_status() == 0
+
+
+def test_adam_matches_oracle(sb):
+    rng = np.random.default_rng(6)
+    n = 1000
+    b = rng.normal(size=(5, n)).astype(np.float32)
+    g = rng.normal(size=(5, n)).astype(np.float32)
+    m = (0.1 * rng.normal(size=(5, n))).astype(np.float32)
+    v = (0.1 * rng.random(size=(5, n))).astype(np.float32)
+    wl = workloads.tiny(M=4, T=64)
+    arr = make_array(sb, wl, (1,), n)
+    for mask in (3, 7):
+        B, Gt = torch.from_numpy(b).cuda(), torch.from_numpy(g).cuda()
+        Mt, Vt = torch.from_numpy(m).cuda(), torch.from_numpy(v).cuda()
+        arr.adam_step(B, Gt, Mt, Vt, 3, sb.AdamParams(), mask=mask)
+        rb, rm, rv = oracle.adam(b, g, m, v, 3, oracle.AdamParams(), mask=mask)
+        # float32 moment updates cancel (beta1 m against (1 - beta1) g): compare
+        # against the size of the operands, not of the result
+        np.testing.assert_allclose(B.cpu().numpy(), rb, rtol=2e-6, atol=1e-7)
+        np.testing.assert_allclose(Mt.cpu().numpy(), rm, rtol=0,
+                                   atol=1e-7 * (np.abs(m).max() + np.abs(g).max()))
+        np.testing.assert_allclose(Vt.cpu().numpy(), rv, rtol=0,
+                                   atol=1e-7 * (np.abs(v).max() + (g * g).max()))
