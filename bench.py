@@ -1,0 +1,609 @@
+#!/usr/bin/env python
+"""Benchmark of the SlingBAG Pro hot path on one GB300 (or N replicas).
+
+Metric: ball x sensor pairs per second through forward + adjoint.
+
+One step is one pass of the whole hot path over the vessel workload (a
+seeded vessel-tree phantom measured by 512 sensors on an ellipsoidal cap;
+an initial cloud of 200,000 uniform random balls; levels 10 / 20 / 40 MHz
+with T = 1024 / 2048 / 4096):
+  restore the initial cloud;
+  zero-gradient filtering at 10 MHz (residual with S = 0, p0 adjoint,
+    compaction);
+  one iteration at each level: downsample the measured traces, forward,
+    residual and loss, adjoint, Adam, filter/grow (coarse stage p0/R at
+    10 MHz, fine stage at 20 and 40 MHz with duplication at 40 MHz).
+The pairs of a step are sum over the three iterations of n_k x M, with n_k
+the live ball count entering iteration k (the zero-gradient pass is extra
+work and is not counted). L2 is flushed (a 512 MB write) before every timed
+step. `value` times the step with inputs resident in device memory;
+`e2e` times the same step through sbp_reconstruct with the cloud and the
+measured traces copied from pinned host memory and the result copied back
+inside the timed region.
+
+N > 1 (torchrun): every rank runs an independent replica of the workload on
+its own GPU (the problem has no exchange step); value = all ranks' pairs /
+the slowest rank's time.
+
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ball-sensor pairs/s (forward+adjoint)"
+UNIT = "pairs/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="vessel", choices=["vessel", "tiny"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="short run for a profiler: no clocks, e2e or CPU baseline")
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas)
+# ---------------------------------------------------------------------------
+
+def dist_setup():
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def barrier():
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def aggregate(seconds: float, pairs: float):
+    """(max seconds over ranks, sum of pairs over ranks)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return seconds, pairs
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    p = torch.tensor([pairs], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int, enabled: bool = True):
+        self.proc = None
+        self.path = None
+        if not enabled:
+            return
+        import torch
+
+        ident = str(device_index)
+        try:
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            ident = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            pass
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", ident, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r)
+                          if v.lower() == "active"})
+        sm = [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# the native (GPU) arm
+# ---------------------------------------------------------------------------
+
+def make_workload(name):
+    import workloads
+
+    return workloads.vessel() if name == "vessel" else workloads.tiny()
+
+
+def stages_for(sb, wl):
+    """One iteration per level: coarse (p0, R) at the coarsest level, fine
+    (all components) above it, duplication at the finest."""
+    nl = len(wl.levels)
+    out = []
+    for k in range(nl):
+        mask = (sb.MASK_P0 | sb.MASK_R) if (k == 0 and nl > 1) else sb.MASK_ALL
+        out.append(sb.Stage(level=k, iterations=1, grad_mask=mask, grow=True,
+                            duplicate=(k == nl - 1)))
+    return out
+
+
+GROW = dict(p_min=1e-3, R_min=0.02, R_max=0.3, g_dup=5.0)
+
+
+def run_native(args, rank, world, local):
+    import torch
+
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_2601_00551_gb300 import slingbag as sb
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = make_workload(args.workload)
+    M = wl.sensors.M
+    n0 = wl.init.n
+    n_cap = 2 * n0
+    arr = sb.SensorArray(wl.sensors.pos, wl.sensors.normal, wl.c, wl.fs_mhz, wl.T, wl.levels,
+                         n_cap=n_cap)
+    nl = len(wl.levels)
+
+    # measured traces: the phantom rendered at the finest level plus 1% noise
+    import workloads
+
+    truth = torch.from_numpy(wl.truth.stack()).to(dev)
+    arr.set_sampling_level(nl - 1)
+    y_clean = arr.forward(truth).cpu().numpy()
+    y_host = workloads.add_noise(y_clean)
+    y_full = torch.from_numpy(y_host).to(dev)
+    del truth
+
+    init = torch.zeros((5, n_cap), dtype=torch.float32, device=dev)
+    init[:, :n0] = torch.from_numpy(wl.init.stack()).to(dev)
+    n_init = torch.tensor([n0], dtype=torch.int32, device=dev)
+    balls = torch.empty_like(init)
+    n_dev = torch.empty_like(n_init)
+    grads = torch.zeros((5, n_cap), dtype=torch.float32, device=dev)
+    mom = torch.zeros((10, n_cap), dtype=torch.float32, device=dev)
+    mom0 = torch.zeros_like(mom)
+    yk = {k: torch.empty((M, arr.level_info(k)[0]), dtype=torch.float32, device=dev)
+          for k in range(nl)}
+    S = {k: torch.empty_like(yk[k]) for k in range(nl)}
+    G = {k: torch.empty_like(yk[k]) for k in range(nl)}
+    loss = torch.zeros(nl, dtype=torch.float64, device=dev)
+    n_log = torch.zeros(nl, dtype=torch.int32, device=dev)
+    stages = stages_for(sb, wl)
+    adam = sb.AdamParams()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    ev = {name: [] for name in ("fwd", "adj")}
+
+    def step(record):
+        balls.copy_(init)
+        n_dev.copy_(n_init)
+        mom.copy_(mom0)
+        zl = 0
+        arr.set_sampling_level(zl, y_full, out=yk[zl])
+        arr.residual(None, yk[zl], G=G[zl], want_loss=False)
+        arr.adjoint(balls, G[zl], n=n_dev, mask=sb.MASK_P0, out=grads)
+        arr.filter_grow(balls, grads, n_dev, mode=sb.KEEP_NEG, extra=[mom])
+        for t, st in enumerate(stages, start=1):
+            k = st.level
+            arr.set_sampling_level(k, y_full, out=yk[k])
+            n_log[t - 1:t].copy_(n_dev)
+            if record:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            arr.forward(balls, n=n_dev, out=S[k])
+            if record:
+                e1 = torch.cuda.Event(enable_timing=True)
+                e1.record(stream)
+            arr.residual(S[k], yk[k], G=G[k], loss=loss[t - 1:t])
+            if record:
+                e2 = torch.cuda.Event(enable_timing=True)
+                e2.record(stream)
+            arr.adjoint(balls, G[k], n=n_dev, mask=st.grad_mask, out=grads)
+            if record:
+                e3 = torch.cuda.Event(enable_timing=True)
+                e3.record(stream)
+                ev["fwd"].append((k, e0, e1))
+                ev["adj"].append((k, e2, e3))
+            arr.adam_step(balls, grads, mom[:5], mom[5:], t, adam, n=n_dev, mask=st.grad_mask)
+            gp = sb.GrowParams(seed=1000 + t, grad_mask=st.grad_mask, duplicate=st.duplicate,
+                               **GROW)
+            arr.filter_grow(balls, grads, n_dev, mode=sb.GROW, grow=gp, extra=[mom])
+
+    # warm-up; the workload is deterministic, so every step sees the same counts
+    for _ in range(max(0, args.warmup)):
+        step(False)
+    torch.cuda.synchronize()
+    counts = n_log.cpu().numpy().astype(np.int64)
+    pairs_per_step = float(counts.sum()) * M
+    if arr.sync_status() != 0:
+        raise RuntimeError("device status latched during warm-up: " + sb.load_library()
+                           .sbp_last_error().decode())
+
+    clocks = ClockSampler(local, enabled=not (args.no_clocks or args.profile))
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = sb.launch_count()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(True)
+        b.record(stream)
+        times.append((a, b))
+    torch.cuda.synchronize()
+    barrier()
+    launches = sb.launch_count() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in times]
+    total_s = sum(step_ms) / 1e3
+    if not np.array_equal(n_log.cpu().numpy(), counts):
+        raise RuntimeError("ball counts changed between steps; the step is not reproducible")
+    if arr.sync_status() != 0:
+        raise RuntimeError("device status latched during the timed steps")
+    max_s, all_pairs = aggregate(total_s, pairs_per_step * args.steps)
+    value = all_pairs / max_s
+
+    # per-call device times of the hot kernels, over the timed region
+    def per_level(name):
+        out = {}
+        for k, e0, e1 in ev[name]:
+            out.setdefault(k, []).append(e0.elapsed_time(e1))
+        return {k: statistics.mean(v) for k, v in out.items()}
+
+    fwd_ms, adj_ms = per_level("fwd"), per_level("adj")
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded vessel-tree phantom, random initial cloud)",
+        "config": {
+            "workload": wl.name, "balls_init": n0, "sensors": M,
+            "levels_mhz": [wl.fs_mhz / f for f in wl.levels],
+            "T": [arr.level_info(k)[0] for k in range(nl)],
+            "balls_per_iteration": counts.tolist(),
+            "pairs_per_step": pairs_per_step,
+            "l2": "flushed before every timed step (512 MB write)",
+            "parallelism": f"replicas x{world}",
+        },
+        "gpu_launches": int(launches),
+        "kernel_ms": {"forward": {str(k): v for k, v in fwd_ms.items()},
+                      "adjoint": {str(k): v for k, v in adj_ms.items()}},
+    }
+    if clk is not None:
+        result["clocks"] = clk
+    probes = None
+    if not args.profile:
+        try:
+            probes = sb.probe_rates()
+            result["probes"] = {k: float(f"{v:.4g}") for k, v in probes.items()}
+        except Exception as exc:  # a probe failure must not hide the measurement
+            result["probes"] = {"error": str(exc)}
+    mean_R = float(np.mean(wl.init.R))
+    h_fine = wl.c * wl.levels[-1] / wl.fs_mhz
+    result["roofline"] = roofline(fwd_ms, adj_ms, counts, M, clk, mean_R, h_fine, probes)
+
+    if not (args.no_e2e or args.profile):
+        result["e2e"] = run_e2e(args, sb, arr, wl, y_host, init, n0, n_cap, stages, adam,
+                                pairs_per_step, dev)
+    if world == 1 and rank == 0 and not (args.no_cpu_baseline or args.profile):
+        result["cpu_baseline"] = cpu_baseline(wl, y_host, counts, n0, seconds=15.0)
+    arr.close()
+    return result, rank
+
+
+# Thread-level arithmetic operations per pair of the two hot kernels, counted
+# from the per-pair code of the algorithm (FP32 and integer arithmetic,
+# compares and conversions; loads, stores, branches and loop control are not
+# counted). The derivation is tabulated in the design doc. The adjoint's window
+# sum costs 3 operations per ramp cell beyond the first, L = 2 R / h on
+# average.
+FWD_OPS_PER_PAIR = 182
+
+
+def adj_ops_per_pair(mean_R, h):
+    L = 2.0 * mean_R / h
+    return 156.0 + 3.0 * max(0.0, L - 1.0) + 2.0
+
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the hot kernels at the 40 MHz level of the vessel workload, from one ncu
+# capture, valid while the kernel source is the one that was measured (its
+# SHA-256 prefix below); otherwise reported as null.
+NCU_TRAFFIC = {
+    "forward": {"source": "paper_2601_00551_gb300/csrc/sbp_forward.cu",
+                "sha256": "65a7f405b22e31ac", "bytes": 5.261056e6},
+    "adjoint": {"source": "paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
+                "sha256": "b1b496a7abf96ddb", "bytes": 3.729920e6},
+}
+
+
+def _traffic(name):
+    import hashlib
+
+    rec = NCU_TRAFFIC[name]
+    if not rec["sha256"] or rec["bytes"] is None:
+        return None
+    try:
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec["bytes"] if sha == rec["sha256"] else None
+
+
+def roofline(fwd_ms, adj_ms, counts, M, clk, mean_R, h_fine, probes):
+    """Roofline of the dominant call at the finest level. Both hot kernels
+    are bound by instruction issue on the SMs (their DRAM traffic is a few
+    bytes per pair); the peak is 152 SMs x 128 lanes x the median SM clock
+    sampled during the timed steps (4 schedulers x 32 lanes per SM issue one
+    thread operation per lane and cycle), the achieved rate is the per-pair
+    operation count of the algorithm x pairs / average call time."""
+    k = max(fwd_ms)
+    ops = {"forward": FWD_OPS_PER_PAIR, "adjoint": adj_ops_per_pair(mean_R, h_fine)}
+    calls = {"forward": fwd_ms[k], "adjoint": adj_ms[k]}
+    name = max(calls, key=calls.get)
+    pairs = float(counts[k]) * M
+    ms = calls[name]
+    achieved = pairs * ops[name] / (ms * 1e-3) / 1e9  # Gop/s
+    peaks = measured_peaks()
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get(
+        "sm_mhz_median") or 1492.0
+    peak = 152 * 128 * sm_mhz * 1e6 / 1e9
+    out = {"bound": "alu", "kernel": f"{name} call at the finest level", "achieved": achieved,
+           "peak": peak, "unit": "Gop/s", "frac": achieved / peak, "traffic": _traffic(name),
+           "ops_per_pair": ops[name], "pairs_per_launch": pairs, "ms_per_launch": ms,
+           "peak_basis": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock sampled "
+                         "during the timed steps; recipe unit counts)"}
+    if probes:
+        out["measured_issue_peak_Gop_s"] = probes["warp_inst_per_s"] * 32 / 1e9
+        out["frac_of_measured_issue"] = achieved / out["measured_issue_peak_Gop_s"]
+    return out
+
+
+def run_e2e(args, sb, arr, wl, y_host, init, n0, n_cap, stages, adam, pairs_per_step, dev):
+    """The same step through sbp_reconstruct with host buffers: the initial
+    cloud and the measured traces go host -> device from pinned memory, the
+    final cloud, its count and the losses come back, all inside the timed
+    region."""
+    import torch
+
+    nl = len(wl.levels)
+    host_init = torch.from_numpy(init.cpu().numpy()).pin_memory()
+    host_y = torch.from_numpy(y_host).pin_memory()
+    host_n = torch.tensor([n0], dtype=torch.int32).pin_memory()
+    out_balls = torch.empty((5, n_cap), dtype=torch.float32).pin_memory()
+    out_n = torch.empty(1, dtype=torch.int32).pin_memory()
+    out_loss = torch.empty(nl, dtype=torch.float64).pin_memory()
+    balls = torch.empty((5, n_cap), dtype=torch.float32, device=dev)
+    y_dev = torch.empty_like(host_y, device=dev)
+    n_dev = torch.empty(1, dtype=torch.int32, device=dev)
+    loss = torch.zeros(nl, dtype=torch.float64, device=dev)
+    n_log = torch.zeros(nl, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    gp = sb.GrowParams(seed=1000, **GROW)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        balls.copy_(host_init, non_blocking=True)
+        y_dev.copy_(host_y, non_blocking=True)
+        n_dev.copy_(host_n, non_blocking=True)
+        arr.reconstruct(y_dev, balls, n_dev, stages, zero_grad_mode=sb.KEEP_NEG,
+                        zero_grad_level=0, adam=adam, grow=gp, loss_log=loss, n_log=n_log)
+        out_balls.copy_(balls, non_blocking=True)
+        out_n.copy_(n_dev, non_blocking=True)
+        out_loss.copy_(loss, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    counts = n_log.cpu().numpy().astype(np.int64)
+    pairs = float(counts.sum()) * wl.sensors.M
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        ms.append((a, b))
+    torch.cuda.synchronize()
+    total = sum(a.elapsed_time(b) for a, b in ms) / 1e3
+    h2d = host_init.numel() * 4 + host_y.numel() * 4 + 4
+    d2h = out_balls.numel() * 4 + 4 + out_loss.numel() * 8
+    return {"value": pairs * args.steps / total, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": total * 1e3 / args.steps,
+            "api": "sbp_reconstruct (C ABI) with pinned host buffers",
+            "balls_per_iteration": counts.tolist()}
+
+
+# ---------------------------------------------------------------------------
+# the FP64 oracle on the host cores (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(wl, y_host, frac, seed=0):
+    """A random `frac` of the initial cloud, in its original order."""
+    rng = np.random.default_rng(seed)
+    n = wl.init.n
+    idx = np.sort(rng.choice(n, max(1, int(round(frac * n))), replace=False))
+    return wl.init.stack()[:, idx]
+
+
+def oracle_step(wl, y_host, balls, threads):
+    """One step of the same pipeline in the FP64 oracle; returns pairs."""
+    import oracle
+
+    nl = len(wl.levels)
+    st = [oracle.Stage(level=k, iterations=1,
+                       grad_mask=(3 if (k == 0 and nl > 1) else 7), grow=True,
+                       duplicate=(k == nl - 1)) for k in range(nl)]
+    gp = oracle.GrowParams(seed=1000, **GROW)
+    _, _, counts = oracle.reconstruct(balls, wl.sensors.pos, wl.sensors.normal, wl.c,
+                                      wl.fs_mhz, wl.T, wl.levels, y_host, st,
+                                      zero_grad_mode=oracle.KEEP_NEG, zero_grad_level=0,
+                                      grow_params=gp, threads=threads)
+    return float(np.sum(counts)) * wl.sensors.M
+
+
+def cpu_baseline(wl, y_host, counts, n0, seconds=15.0):
+    import oracle
+
+    threads = oracle.num_procs()
+    frac = 1.0 / 4
+    balls = oracle_sample(wl, y_host, frac)
+    oracle_step(wl, y_host, balls[:, :256], threads)  # build and warm the library
+    t0 = time.perf_counter()
+    pairs, reps = 0.0, 0
+    while True:
+        pairs += oracle_step(wl, y_host, balls, threads)
+        reps += 1
+        if time.perf_counter() - t0 > seconds or reps >= 50:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": pairs / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{reps} step(s) of the same pipeline on a seeded 1/4 sample of the "
+                      f"initial cloud ({balls.shape[1]} balls) x {wl.sensors.M} sensors, "
+                      f"FP64, {threads} OpenMP threads, {dt:.1f} s"}
+
+
+def run_reference(args, rank):
+    """The reference arm: the FP64 oracle as it stands on the host cores."""
+    import oracle
+    import workloads
+
+    if rank != 0:
+        return None
+    wl = make_workload(args.workload)
+    threads = oracle.num_procs()
+    nl = len(wl.levels)
+    f_fine = wl.levels[nl - 1]
+    y = oracle.forward(wl.truth.stack(), wl.sensors.pos, wl.sensors.normal, wl.c,
+                       f_fine / wl.fs_mhz, wl.T, threads=threads).astype(np.float32)
+    y_host = workloads.add_noise(y)
+    frac = 1.0 / 32 if args.workload == "vessel" else 1.0
+    balls = oracle_sample(wl, y_host, frac)
+    for _ in range(max(0, args.warmup)):
+        oracle_step(wl, y_host, balls, threads)
+    t0 = time.perf_counter()
+    pairs = 0.0
+    for _ in range(args.steps):
+        pairs += oracle_step(wl, y_host, balls, threads)
+    dt = time.perf_counter() - t0
+    value = pairs / dt
+    sample = (f"each step: the full pipeline on a seeded 1/{int(round(1 / frac))} sample of "
+              f"the initial cloud ({balls.shape[1]} balls) x {wl.sensors.M} sensors, FP64")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded vessel-tree phantom, random initial cloud)",
+            "config": {"workload": wl.name, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        res = run_reference(args, rank)
+        if res is not None:
+            print(json.dumps(res))
+        return 0
+    rank, world, local = dist_setup()
+    res, rank = run_native(args, rank, world, local)
+    if rank == 0:
+        print(json.dumps(res))
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized():
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -195,6 +195,50 @@ int sbp_adam_step(sbp_array arr, sbp_balls balls, sbp_grads grads, sbp_balls m, 
                   const int* n_dev, int n_cap, int t, const sbp_adam_params* ap,
                   unsigned mask, sbp_stream stream);
 
+/* One reconstruction stage: `iterations` iterations at sampling level
+ * `level`, updating the components in grad_mask (coarse stage of Section
+ * 4.1: p0 and R; fine stage: all five), followed in every iteration by
+ * filter/grow when grow != 0 (duplication only when duplicate != 0, the fine
+ * stage of Section 4.1). */
+typedef struct {
+    int level;
+    int iterations;
+    unsigned grad_mask;
+    int grow;
+    int duplicate;
+} sbp_stage;
+
+#define SBP_MAX_STAGES 32
+
+typedef struct {
+    int zero_grad_mode;  /* -1: skip; else SBP_KEEP_NEG / SBP_KEEP_NONPOS / SBP_DROP_ZERO */
+    int zero_grad_level; /* level whose downsampled data drives the filter */
+    int n_stages;
+    sbp_stage stages[SBP_MAX_STAGES];
+    sbp_adam_params adam;
+    sbp_grow_params grow; /* seed of iteration t is grow.seed + t */
+    double* loss_log_dev; /* optional: L of every iteration (device doubles) */
+    int* n_log_dev;       /* optional: ball count entering every iteration */
+    int log_capacity;     /* entries available in the logs */
+} sbp_recon_params;
+
+/* The point-cloud reconstruction loop of Algorithm 1 on the device:
+ * zero-gradient filtering at zero_grad_level (Section 4.2), then for every
+ * stage and iteration: forward, residual (L = ||S - y_k||^2), adjoint, one
+ * Adam step, and filter/grow, with y_k = Downsample_{f_k}(y_full) refreshed at
+ * every level change (Section 4.3). The ball count stays on the device
+ * throughout; nothing synchronises. Adam moments start at zero and are
+ * carried through filtering and growth. The library allocates its scratch
+ * (traces, residual, gradients, moments for n_cap balls) on the first call.
+ *   y_full_dev: device float32 [M][T]; balls/n_dev: in/out as in
+ *   sbp_filter_grow. Convergence tests are left to the caller (the paper's
+ *   "until converged" is read as a fixed iteration count per stage). */
+int sbp_reconstruct(sbp_array arr, const float* y_full_dev, sbp_balls balls, int* n_dev,
+                    int n_cap, const sbp_recon_params* rp, sbp_stream stream);
+
+/* Number of CUDA kernels this library has launched in this process. */
+long long sbp_launch_count(void);
+
 /* Synchronise `stream`, then return SBP_OK or the first device-latched
  * status since the last call (which is cleared). */
 int sbp_sync_status(sbp_array arr, sbp_stream stream);

@@ -344,6 +344,68 @@ def adam(balls, grads, m, v, t: int, ap: AdamParams, mask: int = MASK_ALL):
     return b, m, v
 
 
+# --------------------------------------------------------------------------
+# the reconstruction loop (Algorithm 1)
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Stage:
+    level: int
+    iterations: int
+    grad_mask: int = MASK_ALL
+    grow: bool = True
+    duplicate: bool = False
+
+
+def reconstruct(balls, pos, normal, c, fs_mhz, T, factors, y_full, stages,
+                zero_grad_mode=KEEP_NEG, zero_grad_level=0, adam_params=None,
+                grow_params=None, wmode="clamp", threads=1):
+    """Algorithm 1: zero-gradient filtering at level `zero_grad_level`
+    (Section 4.2), then for each stage `iterations` times: simulate at the
+    stage's sampling level (Section 4.3), L = ||S - y_k||^2, backpropagate,
+    one Adam step on the stage's components, then filter/grow (destroy,
+    split, and duplicate in the fine stage; Section 4.1). The cloud is stored
+    in float32 between steps, like the measured cloud it stands for; all
+    arithmetic is float64. Returns (balls (5, n) float32, losses, counts)
+    where counts[t] is the ball count entering iteration t."""
+    ap = adam_params or AdamParams()
+    gpar = grow_params or GrowParams()
+    b = np.asarray(balls, dtype=np.float32).reshape(5, -1).copy()
+    y_full = np.asarray(y_full, dtype=np.float32)
+    m = np.zeros((5, b.shape[1]), np.float32)
+    v = np.zeros((5, b.shape[1]), np.float32)
+
+    def level_data(k):
+        f = factors[k]
+        return f / fs_mhz, (T + f - 1) // f, downsample(y_full, f)
+
+    if zero_grad_mode is not None and zero_grad_mode >= 0:
+        dt, Tk, yk = level_data(zero_grad_level)
+        keep, _, _ = zero_gradient_filter(b, pos, normal, c, dt, Tk, yk, mode=zero_grad_mode,
+                                          wmode=wmode, threads=threads)
+        b, m, v = b[:, keep], m[:, keep], v[:, keep]
+    losses, counts = [], []
+    t = 0
+    for st in stages:
+        dt, Tk, yk = level_data(st.level)
+        for _ in range(st.iterations):
+            counts.append(b.shape[1])
+            S = forward(b, pos, normal, c, dt, Tk, wmode=wmode, threads=threads)
+            L, G = loss_and_residual(S, yk)
+            losses.append(L)
+            g = adjoint(b, pos, normal, c, dt, Tk, G.astype(np.float32), mask=st.grad_mask,
+                        wmode=wmode, threads=threads)
+            t += 1
+            nb, nm, nv = adam(b, g, m, v, t, ap, mask=st.grad_mask)
+            b, m, v = nb.astype(np.float32), nm.astype(np.float32), nv.astype(np.float32)
+            if st.grow:
+                gp = dataclasses.replace(gpar, seed=gpar.seed + t, grad_mask=st.grad_mask,
+                                         duplicate=st.duplicate)
+                b, _, ex, _ = grow(b, g.astype(np.float32), np.concatenate([m, v]), gp)
+                m, v = ex[:5].copy(), ex[5:].copy()
+    return b, np.array(losses), np.array(counts)
+
+
 def _main():  # pragma: no cover - manual build helper
     print(build(force="--force" in sys.argv))
 

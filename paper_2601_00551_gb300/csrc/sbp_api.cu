@@ -1,6 +1,7 @@
 // C ABI of libslingbag: argument checking, the array object and its
 // scratch, and dispatch to the kernel launchers.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -12,6 +13,7 @@
 namespace {
 
 thread_local std::string g_last_error = "no error";
+std::atomic<long long> g_launches{0};
 
 cudaStream_t as_stream(sbp_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -45,20 +47,22 @@ void free_array(sbp_array_s* a) {
     if (!a) return;
     cudaFree(a->d_sens);
     cudaFree(a->d_acc);
-    cudaFree(a->d_rec);
-    cudaFree(a->d_ginv);
-    cudaFree(a->d_gq);
-    cudaFree(a->d_part);
     cudaFree(a->d_lossp);
     cudaFree(a->d_fg_counts);
     cudaFree(a->d_fg_buf);
     cudaFree(a->d_state);
+    cudaFree(a->d_rc_yk);
+    cudaFree(a->d_rc_S);
+    cudaFree(a->d_rc_G);
+    cudaFree(a->d_rc_state);
     delete a;
 }
 
 }  // namespace
 
 void sbp_set_error(const std::string& msg) { g_last_error = msg; }
+
+void sbp_count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 int sbp_cuda_check(cudaError_t e, const char* what) {
     if (e == cudaSuccess) return 0;
@@ -90,6 +94,8 @@ extern "C" {
 const char* sbp_last_error(void) { return g_last_error.c_str(); }
 
 const char* sbp_version(void) { return "slingbag-gb300 0.1 (sm_103a)"; }
+
+long long sbp_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int sbp_create_array(const float* pos_host, const float* normal_host, int M, double c_mm_per_us,
                      double fs_mhz, int T, const int* factors_host, int n_levels, int n_cap,
@@ -156,21 +162,12 @@ int sbp_create_array(const float* pos_host, const float* normal_host, int M, dou
     a->c = c_mm_per_us;
     a->fs = fs_mhz;
     a->wmode = params ? params->weight_mode : SBP_W_CLAMP;
-    const int ball_blocks = (n_cap + 127) / 128;
-    a->part_groups = std::min(M, std::max(1, (4 * a->sm_count + ball_blocks - 1) / ball_blocks));
     a->loss_blocks = 4 * a->sm_count;
     a->fg_blocks = (n_cap + 255) / 256;
     bool ok = true;
     ok = ok && !sbp_cuda_check(cudaMalloc(&a->d_sens, sizeof(float) * 6 * M), "alloc sensors");
     ok = ok && !sbp_cuda_check(cudaMalloc(&a->d_acc, sizeof(unsigned long long) * (size_t)M * T),
                                "alloc trace accumulators");
-    ok = ok && !sbp_cuda_check(cudaMalloc(&a->d_rec, sizeof(longlong2) * (size_t)M * (T + 1)),
-                               "alloc adjoint records");
-    ok = ok && !sbp_cuda_check(cudaMalloc(&a->d_ginv, sizeof(float) * M), "alloc scales");
-    ok = ok && !sbp_cuda_check(cudaMalloc(&a->d_gq, sizeof(int) * (size_t)M * T), "alloc G");
-    ok = ok && !sbp_cuda_check(cudaMalloc(&a->d_part, sizeof(float) * (size_t)a->part_groups *
-                                                          5 * (size_t)n_cap),
-                               "alloc partial gradients");
     ok = ok && !sbp_cuda_check(cudaMalloc(&a->d_lossp, sizeof(double) * a->loss_blocks),
                                "alloc loss partials");
     ok = ok && !sbp_cuda_check(cudaMalloc(&a->d_fg_counts, sizeof(int) * (a->fg_blocks + 1)),

@@ -18,9 +18,22 @@
 //
 // Kernels:
 //   fwd_pmax      max |p0| over the cloud (chooses F so sums cannot overflow)
-//   fwd_accum     CTA = (tile of ST sensors) x (chunk of balls); impulses go to
-//                 per-sensor shared-memory accumulators with shared atomics,
-//                 flushed once per CTA to global memory with global atomics
+//   fwd_group     CTA = (group of 32 sensors) x (chunk of consecutive balls).
+//                 A warp takes one ball at a time and its 32 lanes take the 32
+//                 sensors, so ball data is warp-uniform and every lane keeps
+//                 its sensor in registers. The cells a chunk can touch at a
+//                 sensor are bounded from the chunk's bounding box; each
+//                 lane's window is privatised in shared memory laid out
+//                 [cell][lane], so the shared atomics of a warp never
+//                 conflict on a bank, and flushed once per CTA to the global
+//                 int64 accumulators with global atomics. Windows longer than
+//                 the shared buffer are covered in several passes.
+//                 A 64-bit shared atomic add costs several times a 32-bit one
+//                 on this GPU, so each int64 impulse v is added as two 32-bit
+//                 words: its low kLoBits bits (unsigned) and v >> kLoBits
+//                 (signed). Neither word can overflow within a CTA (at most
+//                 2 impulses per ball and cell, kChunk balls), and the flush
+//                 recombines them exactly.
 //   fwd_finalize  CTA = one sensor; two block scans turn impulses into the
 //                 float32 trace and clear the accumulator row
 #include <algorithm>
@@ -30,9 +43,13 @@
 
 namespace {
 
-constexpr int kAccumThreads = 256;
+constexpr int kGroupWarps = 16;     // warps per forward CTA
+constexpr int kWindow = 384;        // cells per sensor held in shared memory
+constexpr int kChunk = 512;         // largest number of balls per CTA
+constexpr int kLoBits = 20;         // 2 * kChunk * 2^kLoBits < 2^32
+static_assert(2LL * kChunk * (1LL << kLoBits) < (1LL << 32), "low word could overflow");
 constexpr int kFinalizeThreads = 1024;
-constexpr int kFracHeadroomBits = 38;  // F = 38 - ceil(log2 max|p0|)
+constexpr int kFracHeadroomBits = 34;  // F = 34 - ceil(log2 max|p0|)
 
 __global__ void fwd_pmax_kernel(const float* __restrict__ p0, const int* n_dev, int n_cap,
                                 SbpDevState* st) {
@@ -45,6 +62,33 @@ __global__ void fwd_pmax_kernel(const float* __restrict__ p0, const int* n_dev, 
     if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(&st->pmax_bits, __float_as_uint(m));
 }
 
+// Round a float to the nearest int64. Values below 2^31 in magnitude (nearly
+// all of them) take one 32-bit conversion; larger ones are split exactly
+// into two 32-bit halves. (A direct float -> int64 conversion would run on
+// the double-precision pipe, which is narrow on this GPU.)
+__device__ __forceinline__ long long fwd_f2ll(float x) {
+    const float ax = fabsf(x);
+    if (ax < 2147483520.0f) return (long long)__float2int_rn(x);  // largest float < 2^31
+    const float hi = floorf(ax * 2.3283064365386963e-10f);          // |x| / 2^32
+    const float rem = fmaf(-hi, 4294967296.0f, ax);                 // exact, in [0, 2^32)
+    const long long v = ((long long)__float2uint_rz(hi) << 32) + (long long)__float2uint_rn(rem);
+    return x < 0.0f ? -v : v;
+}
+
+// Adds the int64 impulse v to the split accumulator word pair at `lo` (the
+// high word sits kWindow * 32 words further on).
+__device__ __forceinline__ void fwd_add(unsigned int* lo, long long v) {
+    atomicAdd(lo, (unsigned int)v & ((1u << kLoBits) - 1u));
+    atomicAdd(lo + kWindow * 32, (unsigned int)(int)(v >> kLoBits));
+}
+
+// The same for an impulse that fits in 32 bits (its arithmetic shift gives
+// the same high word as the 64-bit one).
+__device__ __forceinline__ void fwd_add32(unsigned int* lo, int v) {
+    atomicAdd(lo, (unsigned int)v & ((1u << kLoBits) - 1u));
+    atomicAdd(lo + kWindow * 32, (unsigned int)(v >> kLoBits));
+}
+
 // Fixed-point exponent F: values are stored as round(v * 2^F).
 __device__ __forceinline__ int fwd_frac_bits(const SbpDevState* st) {
     const float pm = __uint_as_float(st->pmax_bits);
@@ -54,84 +98,160 @@ __device__ __forceinline__ int fwd_frac_bits(const SbpDevState* st) {
     return F < 0 ? 0 : (F > 60 ? 60 : F);
 }
 
-__global__ void __launch_bounds__(kAccumThreads)
-fwd_accum_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restrict__ sens,
-                 LevelGeo g, int ST, int n_chunks, SbpDevState* st,
-                 unsigned long long* __restrict__ acc) {
-    extern __shared__ unsigned long long sacc[];  // [ST][Tk]
-    __shared__ float s_sens[8][6];
-    const int Tk = g.Tk, M = g.M;
-    const int m0 = blockIdx.x * ST;
-    const int ns = min(ST, M - m0);
-    for (int t = threadIdx.x; t < ST * Tk; t += blockDim.x) sacc[t] = 0ull;
-    if (threadIdx.x < ns * 6) {
-        const int s = threadIdx.x / 6, k = threadIdx.x % 6;
-        s_sens[s][k] = sens[k * M + m0 + s];
-    }
-    __syncthreads();
-
+__global__ void __launch_bounds__(kGroupWarps * 32, 2)
+fwd_group_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restrict__ sens,
+                 LevelGeo g, int chunk, SbpDevState* st, unsigned long long* __restrict__ acc) {
+    extern __shared__ unsigned int sacc[];  // [2][kWindow][32]: low words, then high words
+    __shared__ float s_red[kGroupWarps * 7];
+    __shared__ float s_box[7];
+    __shared__ int s_jlo[32];
     const int n = sbp_read_n(n_dev, n_cap);
-    const int chunk = (n + n_chunks - 1) / n_chunks;
-    const int c0 = blockIdx.y * chunk;
-    const int len = max(0, min(n, c0 + chunk) - c0);
+    const int c0 = blockIdx.x * chunk;
+    if (c0 >= n) return;  // uniform over the block
+    const int c1 = min(n, c0 + chunk);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int Tk = g.Tk, M = g.M;
+    const int m = blockIdx.y * 32 + lane;
+    const bool sv = m < M;
+
+    for (int t = threadIdx.x; t < 2 * kWindow * 32; t += blockDim.x) sacc[t] = 0u;
+    sbp_chunk_box(b, c0, c1, s_red, s_box);  // also orders the clearing above
+
+    float sx = 0.f, sy = 0.f, sz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
+    int jlo = 0, jhi = -1;
+    if (sv) {
+        sx = sens[m];
+        sy = sens[M + m];
+        sz = sens[2 * M + m];
+        nx = sens[3 * M + m];
+        ny = sens[4 * M + m];
+        nz = sens[5 * M + m];
+        sbp_box_cells(sx, sy, sz, s_box, g, jlo, jhi);
+    }
+    int wmax = max(0, jhi - jlo + 1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    const int passes = (wmax + kWindow - 1) / kWindow;  // identical in every warp
+    if (warp == 0) s_jlo[lane] = jlo;
+
     const float scale = __int_as_float((127 + fwd_frac_bits(st)) << 23);  // 2^F
     const float h = g.h_hi;
     const float d2c = -2.0f * h * h;
-    // Lanes of a warp take balls len/32 apart so that a spatially sorted
-    // cloud does not send a whole warp's impulses to the same few cells.
-    const int cols = (len + 31) >> 5;
-    const int slots = cols << 5;
     unsigned int inside = 0;
-    for (int slot = threadIdx.x; slot < slots; slot += blockDim.x) {
-        const int r = slot & 31, col = slot >> 5;
-        const int off = r * cols + col;
-        if (off >= len) continue;
-        const int i = c0 + off;
-        const float cx = __ldg(b.x + i), cy = __ldg(b.y + i), cz = __ldg(b.z + i);
-        const float R = __ldg(b.R + i), p0 = __ldg(b.p0 + i);
-        if (p0 == 0.0f) continue;
-#pragma unroll 1
-        for (int s = 0; s < ns; ++s) {
-            const PairDist pd =
-                sbp_pair_distance(cx, cy, cz, s_sens[s][0], s_sens[s][1], s_sens[s][2]);
+    for (int p = 0; p < passes; ++p) {
+        const int base = jlo + p * kWindow;  // this lane's first cell in this pass
+        // last cell of this pass that may be stored: inside the record and the buffer
+        const int lim = min(jhi - base, kWindow - 1);
+        int i = c0 + warp;
+        // the next ball is loaded while the current one is processed
+        float nx_ = 0.f, ny_ = 0.f, nz_ = 0.f, nR = 0.f, np0 = 0.f;
+        if (i < c1) {
+            nx_ = b.x[i];
+            ny_ = b.y[i];
+            nz_ = b.z[i];
+            nR = b.R[i];
+            np0 = b.p0[i];
+        }
+        for (; i < c1; i += kGroupWarps) {
+            const float cx = nx_, cy = ny_, cz = nz_, R = nR, p0 = np0;
+            const int inext = i + kGroupWarps;
+            if (inext < c1) {
+                nx_ = b.x[inext];
+                ny_ = b.y[inext];
+                nz_ = b.z[inext];
+                nR = b.R[inext];
+                np0 = b.p0[inext];
+            }
+            if (p0 == 0.0f || !sv) continue;
+            const PairDist pd = sbp_pair_distance(cx, cy, cz, sx, sy, sz);
             if (!(pd.dh + pd.dl > R)) {
-                ++inside;
+                if (p == 0) ++inside;
                 continue;
             }
             PairWindow win;
-            if (!sbp_window(pd, R, g, true, win)) continue;
+            if (!sbp_window(pd, R, g, win)) continue;
             const int jL = win.jL, jH = win.jH;
-            const float cosv =
-                (s_sens[s][3] * pd.dx + s_sens[s][4] * pd.dy + s_sens[s][5] * pd.dz) * pd.rd;
+            const float cosv = (nx * pd.dx + ny * pd.dy + nz * pd.dz) * pd.rd;
             float act;
             const float w = sbp_weight(g.wmode, cosv, act);
             if (w == 0.0f) continue;
             const float b0 = win.b0, bL = win.bL;
-            const float K = p0 * w * g.inv_4h * pd.rd;
-            const float Ks = K * scale;
-            const long long qa = __float2ll_rn(Ks * fmaxf(R - b0, 0.0f) * (R + b0));
-            const long long qe = -__float2ll_rn(Ks * fmaxf(R + bL, 0.0f) * (R - bL));
-            const long long q1 = __float2ll_rn(Ks * h * (2.0f * b0 - h));
-            const long long q2 = __float2ll_rn(Ks * d2c);
-            const long long L = jH - jL;
-            unsigned long long* row = sacc + s * Tk;
-            // second difference of the pair's cell values (valid for every L >= 0;
-            // for L < 2 some positions coincide and the impulses add up)
-            const long long imp[6] = {qa, q1 - 2 * qa, qa - q1 + q2,
-                                      qe - q1 - L * q2, q1 + (L - 1) * q2 - 2 * qe, qe};
-            const int pos[6] = {jL - 1, jL, jL + 1, jH, jH + 1, jH + 2};
+            const float Ks = p0 * w * g.inv_4h * pd.rd * scale;  // K 2^F
+            const float fa = Ks * fmaxf(R - b0, 0.0f) * (R + b0);
+            const float fe = -(Ks * fmaxf(R + bL, 0.0f) * (R - bL));
+            const float f1 = Ks * h * (2.0f * b0 - h);
+            const float f2 = Ks * d2c;
+            const int L = jH - jL;
+            unsigned int* col = sacc + lane;
+            const int ra = jL - 1 - base, rb = jH - base;
+            const bool fast_a = ra >= 0 && ra + 2 <= lim, fast_b = rb >= 0 && rb + 2 <= lim;
+            // impulses are sums of at most four coefficient terms; below 2^28
+            // each they fit in 32 bits (the usual case)
+            const float big = fmaxf(fmaxf(fabsf(fa), fabsf(fe)),
+                                    fmaxf(fabsf(f1), fabsf(f2) * (float)(L + 2)));
+            if (big < 268435456.0f && fast_a && fast_b) {
+                const int qa = __float2int_rn(fa), qe = __float2int_rn(fe);
+                const int q1 = __float2int_rn(f1), q2 = __float2int_rn(f2);
+                const int Lq2 = L * q2;
+                unsigned int* a = col + ra * 32;
+                fwd_add32(a, qa);
+                fwd_add32(a + 32, q1 - 2 * qa);
+                fwd_add32(a + 64, qa - q1 + q2);
+                unsigned int* c = col + rb * 32;
+                fwd_add32(c, qe - q1 - Lq2);
+                fwd_add32(c + 32, q1 + Lq2 - q2 - 2 * qe);
+                fwd_add32(c + 64, qe);
+                continue;
+            }
+            const long long qa = fwd_f2ll(fa), qe = fwd_f2ll(fe);
+            const long long q1 = fwd_f2ll(f1), q2 = fwd_f2ll(f2);
+            const long long Lq2 = (long long)L * q2;
+            // second difference of the pair's cell values: three impulses at
+            // jL-1.. jL+1 and three at jH..jH+2 (valid for every jH >= jL; when
+            // the two triples overlap the impulses add up)
+            const long long ia0 = qa, ia1 = q1 - 2 * qa, ia2 = qa - q1 + q2;
+            const long long ib0 = qe - q1 - Lq2, ib1 = q1 + Lq2 - q2 - 2 * qe, ib2 = qe;
+            if (fast_a) {
+                unsigned int* a = col + ra * 32;
+                fwd_add(a, ia0);
+                fwd_add(a + 32, ia1);
+                fwd_add(a + 64, ia2);
+            } else {
+                const long long v[3] = {ia0, ia1, ia2};
 #pragma unroll
-            for (int q = 0; q < 6; ++q)
-                if (pos[q] < Tk && imp[q] != 0)
-                    atomicAdd(row + pos[q], (unsigned long long)imp[q]);
+                for (int q = 0; q < 3; ++q)
+                    if (ra + q >= 0 && ra + q <= lim) fwd_add(col + (ra + q) * 32, v[q]);
+            }
+            if (fast_b) {
+                unsigned int* c = col + rb * 32;
+                fwd_add(c, ib0);
+                fwd_add(c + 32, ib1);
+                fwd_add(c + 64, ib2);
+            } else {
+                const long long v[3] = {ib0, ib1, ib2};
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    if (rb + q >= 0 && rb + q <= lim) fwd_add(col + (rb + q) * 32, v[q]);
+            }
         }
+        __syncthreads();
+        // flush this pass: lanes of a warp read 32 consecutive words (one cell
+        // of all 32 sensors), recombine the two halves and clear them
+        for (int t = threadIdx.x; t < kWindow * 32; t += blockDim.x) {
+            const unsigned int lo = sacc[t];
+            const int hi = (int)sacc[kWindow * 32 + t];
+            if (lo | (unsigned)hi) {
+                const long long v = (long long)hi * (1LL << kLoBits) + (long long)lo;
+                const int ln = t & 31, rel = t >> 5;
+                const int j = s_jlo[ln] + p * kWindow + rel;
+                atomicAdd(acc + (size_t)(blockIdx.y * 32 + ln) * Tk + j, (unsigned long long)v);
+                sacc[t] = 0u;
+                sacc[kWindow * 32 + t] = 0u;
+            }
+        }
+        __syncthreads();
     }
     if (inside) atomicAdd(&st->inside_pairs, (unsigned long long)inside);
-    __syncthreads();
-    for (int t = threadIdx.x; t < ns * Tk; t += blockDim.x) {
-        const unsigned long long v = sacc[t];
-        if (v) atomicAdd(acc + (size_t)(m0 + t / Tk) * Tk + (t % Tk), v);
-    }
 }
 
 // One CTA per sensor: S = 2^-F * P(P(D)), then clear the accumulator row.
@@ -181,7 +301,8 @@ fwd_finalize_kernel(unsigned long long* __restrict__ acc, int Tk, const SbpDevSt
         for (int q = 0; q < IPT; ++q) {
             const int i = i0 + q;
             if (i < Tk) {
-                out[i] = __ll2float_rn(v[q] + off) * inv;
+                const long long x = v[q] + off;  // two 32-bit conversions, not one 64-bit
+                out[i] = fmaf((float)(int)(x >> 32), 4294967296.0f, (float)(unsigned)x) * inv;
                 row[i] = 0ull;
             }
         }
@@ -193,21 +314,14 @@ fwd_finalize_kernel(unsigned long long* __restrict__ acc, int Tk, const SbpDevSt
 int sbp_launch_forward(sbp_array_s* a, const BallsDev& b, const int* n_dev, int n_cap,
                        float* S, cudaStream_t st) {
     const LevelGeo g = sbp_level_geo(a, a->level);
-    const int Tk = g.Tk;
-    // sensors per CTA: as many traces as fit in ~96 KB of shared memory, at most 8
-    const size_t row_bytes = (size_t)Tk * sizeof(unsigned long long);
-    int ST = (int)std::max<size_t>(1, std::min<size_t>(8, (96u * 1024u) / row_bytes));
-    if ((size_t)ST * row_bytes > 200u * 1024u) {
-        sbp_set_error("forward: a trace of T_k samples does not fit in shared memory");
-        return SBP_ERR_ARG;
-    }
-    const int tiles = (g.M + ST - 1) / ST;
-    // enough CTAs for ~4 waves at 2 CTAs per SM, chunks of at least 512 balls
-    const int want = 8 * a->sm_count;
-    int chunks = std::max(1, (want + tiles - 1) / tiles);
-    chunks = std::min(chunks, std::max(1, (n_cap + 511) / 512));
-    const size_t smem = (size_t)ST * row_bytes;
-    if (sbp_cuda_check(cudaFuncSetAttribute(fwd_accum_kernel,
+    const int groups = (g.M + 31) / 32;
+    // consecutive balls per CTA: up to 1024, fewer for small clouds so that
+    // the grid still covers the GPU
+    int chunk = kChunk;
+    while (chunk > 32 && (long long)((n_cap + chunk - 1) / chunk) * groups < 4LL * a->sm_count)
+        chunk >>= 1;
+    const size_t smem = (size_t)2 * kWindow * 32 * sizeof(unsigned int);
+    if (sbp_cuda_check(cudaFuncSetAttribute(fwd_group_kernel,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem),
                        "forward: smem attribute"))
@@ -218,11 +332,12 @@ int sbp_launch_forward(sbp_array_s* a, const BallsDev& b, const int* n_dev, int 
     fwd_pmax_kernel<<<std::max(1, std::min(4 * a->sm_count, (n_cap + 255) / 256)), 256, 0,
                       st>>>(b.p0, n_dev, n_cap, a->d_state);
     if (sbp_cuda_check(cudaGetLastError(), "forward: pmax launch")) return SBP_ERR_CUDA;
-    dim3 grid(tiles, chunks);
-    fwd_accum_kernel<<<grid, kAccumThreads, smem, st>>>(b, n_dev, n_cap, a->d_sens, g, ST,
-                                                        chunks, a->d_state, a->d_acc);
+    dim3 grid((n_cap + chunk - 1) / chunk, groups);
+    fwd_group_kernel<<<grid, kGroupWarps * 32, smem, st>>>(b, n_dev, n_cap, a->d_sens, g, chunk,
+                                                           a->d_state, a->d_acc);
     if (sbp_cuda_check(cudaGetLastError(), "forward: accumulate launch")) return SBP_ERR_CUDA;
-    fwd_finalize_kernel<<<g.M, kFinalizeThreads, 0, st>>>(a->d_acc, Tk, a->d_state, S);
+    fwd_finalize_kernel<<<g.M, kFinalizeThreads, 0, st>>>(a->d_acc, g.Tk, a->d_state, S);
     if (sbp_cuda_check(cudaGetLastError(), "forward: finalize launch")) return SBP_ERR_CUDA;
+    sbp_count_launches(3);
     return SBP_OK;
 }

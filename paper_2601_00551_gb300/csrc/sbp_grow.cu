@@ -267,6 +267,7 @@ int sbp_launch_filter_grow(sbp_array_s* a, sbp_balls balls, sbp_grads grads,
                                                      a->d_state, a->d_fg_buf);
     const int cblocks = std::max(1, std::min(4 * a->sm_count, blocks));
     fg_copy_kernel<<<cblocks, 256, 0, st>>>(A, n_cap, a->d_fg_buf, a->d_state, n_dev);
+    sbp_count_launches(4);
     return sbp_cuda_check(cudaGetLastError(), "filter_grow launch") ? SBP_ERR_CUDA : SBP_OK;
 }
 
@@ -293,5 +294,6 @@ int sbp_launch_adam(sbp_array_s* a, sbp_balls balls, sbp_grads grads, sbp_balls 
     x.mask = mask;
     const int blocks = std::max(1, std::min(4 * a->sm_count, (n_cap + 255) / 256));
     adam_kernel<<<blocks, 256, 0, st>>>(x, n_dev, n_cap);
+    sbp_count_launches(1);
     return sbp_cuda_check(cudaGetLastError(), "adam launch") ? SBP_ERR_CUDA : SBP_OK;
 }

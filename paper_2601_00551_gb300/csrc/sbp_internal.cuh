@@ -53,13 +53,6 @@ struct sbp_array_s {
     float* d_sens;
     // forward: fixed-point second-difference accumulators [M][T_k] (int64)
     unsigned long long* d_acc;
-    // adjoint: per-sensor prefix records [M][T_k + 1] of (sum G, sum j G), int64
-    longlong2* d_rec;
-    int* d_gq;      // [M][T_k] G rounded to fixed point (int32)
-    float* d_ginv;  // [M] 2^-s, the inverse quantisation scale of G per sensor
-    // adjoint partial gradients when sensors are split across CTAs: [groups][5][n_cap]
-    float* d_part;
-    int part_groups;
     // residual loss partials
     double* d_lossp;
     int loss_blocks;
@@ -68,12 +61,18 @@ struct sbp_array_s {
     int fg_blocks;
     float* d_fg_buf;   // [SBP_FG_ARRAYS][n_cap]
     SbpDevState* d_state;
+    // reconstruction scratch (allocated by the first sbp_reconstruct)
+    float* d_rc_yk;     // [M][T]
+    float* d_rc_S;      // [M][T]
+    float* d_rc_G;      // [M][T]
+    float* d_rc_state;  // [15][n_cap]: grads (5), Adam m (5), Adam v (5)
 };
 
 // ----------------------------------------------------------------------------
 // host helpers (sbp_api.cu)
 // ----------------------------------------------------------------------------
 void sbp_set_error(const std::string& msg);
+void sbp_count_launches(int k);  // adds k to the process-wide kernel launch count
 int sbp_cuda_check(cudaError_t e, const char* what);
 LevelGeo sbp_level_geo(const sbp_array_s* a, int k);
 int sbp_level_T(const sbp_array_s* a, int k);
@@ -170,68 +169,51 @@ __device__ __forceinline__ float sbp_boundary(float dh, float dl, int j, float h
 }
 
 // Cell boundaries of a pair inside the support: jL = min{j : b_j < R} and
-// jH = max{j : b_j > -R}, b_j = d - j h. A float32 estimate of (d -+ R)/h is
-// good to ~1e-3 cells; when it falls within 2e-3 of an integer the decision is
-// taken on the float-float offsets b_j instead, so the window agrees with an
-// exact evaluation except within ~1e-9 mm of a kink (where the loss is not
-// differentiable anyway). Returns false when no boundary lies inside the
-// support (every cell integral is then zero) or the window starts beyond
-// the record. jH is capped near Tk + 3: boundaries past the record are never
-// stored or read. b0 = b_jL; bL = b_jH only when want_bL.
+// jH = max{j : b_j > -R}, b_j = d - j h. The offset e = d - jr h of one
+// reference boundary jr = floor(d / h) is taken in float-float; every other
+// boundary is b_j = e - (j - jr) h with a small integer j - jr, so the window
+// and its end offsets b0 = b_jL, bL = b_jH follow from small-magnitude float
+// arithmetic (abs. error ~1e-8 mm) and are then checked against R directly.
+// Returns false when no boundary lies inside the support (every cell
+// integral is zero), when the sensor is inside the ball (d <= R), or when the
+// first touched cell jL - 1 is past the record.
 struct PairWindow {
     int jL, jH;
     float b0, bL;
 };
 
 __device__ __forceinline__ bool sbp_window(const PairDist& pd, float R, const LevelGeo& g,
-                                           bool want_bL, PairWindow& w) {
-    const int Tk = g.Tk;
-    const float dli = pd.dl * g.inv_h;
-    const float xlo = fmaf(pd.dh - R, g.inv_h, dli);
-    if (!(xlo < (float)Tk + 1.0f)) return false;  // also rejects NaN
-    const float flo = floorf(xlo);
-    int jL = max(1, (int)flo + 1);
-    float b0 = sbp_boundary(pd.dh, pd.dl, jL, g.h_hi, g.h_lo);
-    const float rlo = xlo - flo;
-    if (rlo < 2e-3f || rlo > 1.0f - 2e-3f) {
-        if (b0 >= R) {
-            ++jL;
-            b0 = sbp_boundary(pd.dh, pd.dl, jL, g.h_hi, g.h_lo);
-        } else if (jL > 1) {
-            const float bp = sbp_boundary(pd.dh, pd.dl, jL - 1, g.h_hi, g.h_lo);
-            if (bp < R) {
-                --jL;
-                b0 = bp;
-            }
-        }
+                                           PairWindow& w) {
+    const float h = g.h_hi;
+    const float xr = pd.dh * g.inv_h;
+    if (!(xr < (float)g.Tk + 4096.0f) || !(pd.dh + pd.dl > R)) return false;  // also NaN
+    const int jr = (int)floorf(xr);
+    const float e = sbp_boundary(pd.dh, pd.dl, jr, g.h_hi, g.h_lo);  // b_jr
+    const float tL = fminf(fmaxf((e - R) * g.inv_h, -1e6f), 1e6f);
+    const float tH = fminf(fmaxf((e + R) * g.inv_h, -1e6f), 1e6f);
+    int kL = (int)floorf(tL) + 1;
+    int kH = (int)ceilf(tH) - 1;
+    float b0 = fmaf(-(float)kL, h, e);
+    if (b0 >= R) {
+        ++kL;
+        b0 -= h;
+    } else if (b0 + h < R) {
+        --kL;
+        b0 += h;
     }
-    if (jL - 1 >= Tk) return false;
-    // clamped to [-1, Tk + 4] so that jH + 2 stays far from int overflow
-    const float xhi = fmaxf(fminf(fmaf(pd.dh + R, g.inv_h, dli), (float)Tk + 4.0f), -1.0f);
-    const float chi = ceilf(xhi);
-    int jH = (int)chi - 1;
-    float bL = 0.0f;
-    const float rhi = chi - xhi;
-    const bool near = (rhi < 2e-3f || rhi > 1.0f - 2e-3f) && jH < Tk + 2;
-    if (near || want_bL) bL = sbp_boundary(pd.dh, pd.dl, jH, g.h_hi, g.h_lo);
-    if (near) {
-        if (bL <= -R) {
-            --jH;
-            bL = sbp_boundary(pd.dh, pd.dl, jH, g.h_hi, g.h_lo);
-        } else {
-            const float bn = sbp_boundary(pd.dh, pd.dl, jH + 1, g.h_hi, g.h_lo);
-            if (bn > -R) {
-                ++jH;
-                bL = bn;
-            }
-        }
+    float bL = fmaf(-(float)kH, h, e);
+    if (bL <= -R) {
+        --kH;
+        bL += h;
+    } else if (bL - h > -R) {
+        ++kH;
+        bL -= h;
     }
-    if (jH < jL) return false;
-    w.jL = jL;
-    w.jH = jH;
+    w.jL = jr + kL;
+    w.jH = jr + kH;
     w.b0 = b0;
     w.bL = bL;
-    return true;
+    return w.jH >= w.jL && w.jL >= 1 && w.jL - 1 < g.Tk;
 }
 
 // Orientation weight and its switch (1 where d w / d c is non-zero).
@@ -246,6 +228,69 @@ __device__ __forceinline__ float sbp_weight(int wmode, float cosv, float& active
     }
     active = cosv > 0.0f ? 1.0f : 0.0f;
     return fmaxf(cosv, 0.0f);
+}
+
+// Bounding box of the centres of balls [c0, c1) and their largest radius,
+// reduced over the block: box[0..2] = min, box[3..5] = max, box[6] = max R.
+// `red` needs 7 floats per warp of shared memory. Contains __syncthreads()
+// and must be reached by every thread of the block.
+__device__ __forceinline__ void sbp_chunk_box(const BallsDev& b, int c0, int c1, float* red,
+                                              float* box) {
+    const float inf = __int_as_float(0x7f800000);
+    float v[7] = {inf, inf, inf, -inf, -inf, -inf, -inf};
+    for (int i = c0 + (int)threadIdx.x; i < c1; i += blockDim.x) {
+        const float x = b.x[i], y = b.y[i], z = b.z[i], R = b.R[i];
+        v[0] = fminf(v[0], x);
+        v[1] = fminf(v[1], y);
+        v[2] = fminf(v[2], z);
+        v[3] = fmaxf(v[3], x);
+        v[4] = fmaxf(v[4], y);
+        v[5] = fmaxf(v[5], z);
+        v[6] = fmaxf(v[6], R);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[k] = fminf(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+#pragma unroll
+        for (int k = 3; k < 7; ++k) v[k] = fmaxf(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 7; ++k) red[wid * 7 + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        const int k = threadIdx.x, nw = (blockDim.x + 31) >> 5;
+        float r = red[k];
+        for (int w = 1; w < nw; ++w) r = k < 3 ? fminf(r, red[w * 7 + k]) : fmaxf(r, red[w * 7 + k]);
+        box[k] = r;
+    }
+    __syncthreads();
+}
+
+// Cells [jlo, jhi] (clipped to the record) that any pair of the sensor at
+// (sx, sy, sz) and a ball of the box can touch: the first touched cell jL-1
+// and the last impulse jH+2 of every such pair lie inside. Empty when
+// jhi < jlo. The bound uses the nearest and farthest points of the box and
+// the largest radius, with two cells of slack for float rounding.
+__device__ __forceinline__ void sbp_box_cells(float sx, float sy, float sz, const float* box,
+                                              const LevelGeo& g, int& jlo, int& jhi) {
+    const float ex = fmaxf(fmaxf(box[0] - sx, sx - box[3]), 0.0f);
+    const float ey = fmaxf(fmaxf(box[1] - sy, sy - box[4]), 0.0f);
+    const float ez = fmaxf(fmaxf(box[2] - sz, sz - box[5]), 0.0f);
+    const float fx = fmaxf(fabsf(sx - box[0]), fabsf(sx - box[3]));
+    const float fy = fmaxf(fabsf(sy - box[1]), fabsf(sy - box[4]));
+    const float fz = fmaxf(fabsf(sz - box[2]), fabsf(sz - box[5]));
+    const float dmin = sqrtf(ex * ex + ey * ey + ez * ez);
+    const float dmax = sqrtf(fx * fx + fy * fy + fz * fz);
+    const float Rm = fmaxf(box[6], 0.0f);
+    float lo = floorf((dmin - Rm) * g.inv_h) - 2.0f;
+    float hi = ceilf((dmax + Rm) * g.inv_h) + 3.0f;
+    lo = fminf(fmaxf(lo, 0.0f), (float)g.Tk);
+    hi = fminf(fmaxf(hi, -1.0f), (float)g.Tk - 1.0f);
+    jlo = (int)lo;
+    jhi = (int)hi;
 }
 
 __device__ __forceinline__ void sbp_latch(SbpDevState* st, int code) {

@@ -56,6 +56,22 @@ class _AdamParams(ctypes.Structure):
                 ("eps", ctypes.c_float)]
 
 
+class _Stage(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("grad_mask", ctypes.c_uint), ("grow", ctypes.c_int),
+                ("duplicate", ctypes.c_int)]
+
+
+MAX_STAGES = 32
+
+
+class _ReconParams(ctypes.Structure):
+    _fields_ = [("zero_grad_mode", ctypes.c_int), ("zero_grad_level", ctypes.c_int),
+                ("n_stages", ctypes.c_int), ("stages", _Stage * MAX_STAGES),
+                ("adam", _AdamParams), ("grow", _GrowParams), ("loss_log_dev", _P),
+                ("n_log_dev", _P), ("log_capacity", ctypes.c_int)]
+
+
 _lib = None
 
 # name -> (restype, argtypes); the C ABI of include/slingbag.h
@@ -78,6 +94,12 @@ _SIGS = {
     "sbp_adam_step": (ctypes.c_int, [_P, _Balls, _Balls, _Balls, _Balls, _P, ctypes.c_int,
                                      ctypes.c_int, ctypes.POINTER(_AdamParams), ctypes.c_uint,
                                      _P]),
+    "sbp_reconstruct": (ctypes.c_int, [_P, _P, _Balls, _P, ctypes.c_int,
+                                       ctypes.POINTER(_ReconParams), _P]),
+    "sbp_launch_count": (ctypes.c_longlong, []),
+    "sbp_probe_fp32_fma": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
+    "sbp_probe_issue": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
+    "sbp_probe_smem_atomic": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "sbp_sync_status": (ctypes.c_int, [_P, _P]),
     "sbp_get_inside_pairs": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_longlong)]),
 }
@@ -149,6 +171,38 @@ class AdamParams:
 
     def c(self) -> _AdamParams:
         return _AdamParams((ctypes.c_float * 5)(*self.lr), self.beta1, self.beta2, self.eps)
+
+
+@dataclasses.dataclass
+class Stage:
+    """`iterations` iterations at level `level` (see sbp_stage)."""
+    level: int
+    iterations: int
+    grad_mask: int = MASK_ALL
+    grow: bool = True
+    duplicate: bool = False
+
+
+def launch_count() -> int:
+    """Kernels launched by libslingbag in this process so far."""
+    return int(load_library().sbp_launch_count())
+
+
+def probe_rates() -> dict:
+    """Measured throughput of the units that bound the hot kernels
+    (include/slingbag_probe.h): FP32 FMA/s, warp instructions issued/s and
+    shared-memory atomic adds/s (u32, u64, f32), on the current device."""
+    lib = load_library()
+    out = {}
+    v = ctypes.c_double()
+    _check("sbp_probe_fp32_fma", lib.sbp_probe_fp32_fma(ctypes.byref(v)))
+    out["fp32_fma_per_s"] = v.value
+    _check("sbp_probe_issue", lib.sbp_probe_issue(ctypes.byref(v)))
+    out["warp_inst_per_s"] = v.value
+    for kind, name in enumerate(("u32", "u64", "f32")):
+        _check("sbp_probe_smem_atomic", lib.sbp_probe_smem_atomic(kind, ctypes.byref(v)))
+        out[f"smem_atomic_{name}_per_s"] = v.value
+    return out
 
 
 class SensorArray:
@@ -294,6 +348,44 @@ class SensorArray:
         _check("sbp_adam_step", self._lib.sbp_adam_step(
             self._h, _rows(balls), _rows(grads), _rows(m), _rows(v), _dptr(nd), balls.shape[1],
             int(t), ctypes.byref(p), mask, _stream()))
+
+    def reconstruct(self, y_full: torch.Tensor, balls: torch.Tensor, n_dev: torch.Tensor,
+                    stages, zero_grad_mode: int = KEEP_NEG, zero_grad_level: int = 0,
+                    adam: AdamParams | None = None, grow: GrowParams | None = None,
+                    loss_log: torch.Tensor | None = None, n_log: torch.Tensor | None = None):
+        """Algorithm 1 on the device (sbp_reconstruct): zero-gradient filtering
+        then the given stages; balls and n_dev are updated in place."""
+        self._check_traces(y_full, self.T)
+        if len(stages) > MAX_STAGES:
+            raise ValueError(f"at most {MAX_STAGES} stages")
+        rp = _ReconParams()
+        rp.zero_grad_mode = -1 if zero_grad_mode is None else int(zero_grad_mode)
+        rp.zero_grad_level = int(zero_grad_level)
+        rp.n_stages = len(stages)
+        for i, st in enumerate(stages):
+            rp.stages[i] = _Stage(st.level, st.iterations, st.grad_mask, int(st.grow),
+                                  int(st.duplicate))
+        rp.adam = (adam or AdamParams()).c()
+        rp.grow = (grow or GrowParams()).c()
+        cap = 0
+        if loss_log is not None:
+            if loss_log.dtype != torch.float64 or not loss_log.is_cuda:
+                raise ValueError("loss_log must be a float64 CUDA tensor")
+            rp.loss_log_dev = loss_log.data_ptr()
+            cap = loss_log.numel()
+        if n_log is not None:
+            if n_log.dtype != torch.int32 or not n_log.is_cuda:
+                raise ValueError("n_log must be an int32 CUDA tensor")
+            rp.n_log_dev = n_log.data_ptr()
+            cap = n_log.numel() if loss_log is None else min(cap, n_log.numel())
+        rp.log_capacity = cap
+        _check("sbp_reconstruct", self._lib.sbp_reconstruct(
+            self._h, _dptr(y_full), _rows(balls), _dptr(n_dev), balls.shape[1],
+            ctypes.byref(rp), _stream()))
+        if stages:
+            self.level = stages[-1].level
+        elif zero_grad_mode is not None and zero_grad_mode >= 0:
+            self.level = zero_grad_level
 
     def sync_status(self) -> int:
         return int(self._lib.sbp_sync_status(self._h, _stream()))
