@@ -159,6 +159,28 @@ int sbp_set_sampling_level(sbp_array arr, int k, const float* y_full_dev, float*
 int sbp_forward(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap, float* S_dev,
                 unsigned flags, sbp_stream stream);
 
+/* sbp_forward without any device allocation, for callers that cannot call
+ * cudaMalloc (code inside a stream capture or a host callback, or a host
+ * that borrows every buffer from a framework owning all allocations). The
+ * paper has no counterpart; this is a deployment variant of sbp_forward.
+ * It takes no array object: the caller passes the sensors, the level and all
+ * inputs and outputs; the scratch (trace accumulators and state words) is a
+ * file-scope device array of 2^21 int64 cells plus 256 bytes (16 MiB) that
+ * every GPU loading the library holds until the process exits.
+ *   sensors_dev: device float32 [6][M]: x, y, z of every sensor, then the
+ *                UNIT normals nx, ny, nz (not normalised here).
+ *   dt_us = f_k / fs (sampling interval of the level), T_k samples;
+ *   weight_mode: SBP_W_*; balls, n_dev, n_cap, S_dev as in sbp_forward.
+ * Returns SBP_ERR_ARG when M * T_k exceeds 2^21 cells (use sbp_forward then).
+ * The first call on a device looks up the array's device address once
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call clears the part of the array it uses, and all calls share it:
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * corrupt each other's traces; serialise them. */
+int sbp_forward_static(const float* sensors_dev, int M, double c_mm_per_us, double dt_us,
+                       int T_k, int weight_mode, sbp_balls balls, const int* n_dev, int n_cap,
+                       float* S_dev, sbp_stream stream);
+
 /* Residual of the per-level loss L = ||S - y_k||_2^2 (Section 4.2 and 4.3):
  * G = 2 (S - y_k) into G_dev [M][T_k]; if loss_dev is not NULL the loss is
  * written there as one double (a fixed-order reduction, reproducible).

@@ -37,6 +37,7 @@
 //   fwd_finalize  CTA = one sensor; two block scans turn impulses into the
 //                 float32 trace and clear the accumulator row
 #include <algorithm>
+#include <mutex>
 
 #include "sbp_internal.cuh"
 #include "sbp_scan.cuh"
@@ -338,6 +339,129 @@ int sbp_launch_forward(sbp_array_s* a, const BallsDev& b, const int* n_dev, int 
     if (sbp_cuda_check(cudaGetLastError(), "forward: accumulate launch")) return SBP_ERR_CUDA;
     fwd_finalize_kernel<<<g.M, kFinalizeThreads, 0, st>>>(a->d_acc, g.Tk, a->d_state, S);
     if (sbp_cuda_check(cudaGetLastError(), "forward: finalize launch")) return SBP_ERR_CUDA;
+    sbp_count_launches(3);
+    return SBP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Forward without allocation (sbp_forward_static).
+//
+// Some callers cannot allocate device memory at all: code that runs where
+// cudaMalloc is forbidden or unsafe (inside a host callback or a stream
+// capture that must not change the allocation state, or a host process that
+// only borrows buffers from a larger framework that owns every allocation).
+// For them this entry point renders the same traces as sbp_forward without
+// an array object: its scratch (the int64 trace accumulators and the state
+// words) lives in one file-scope device array that every GPU loading this
+// library holds until the process exits. The kernels are the ones
+// sbp_forward launches.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr long long kStaticCells = 1LL << 21;  // largest M * T_k: 16 MiB of accumulators
+constexpr int kStaticStateWords = 32;          // 256 bytes for SbpDevState (padded)
+
+static_assert(sizeof(SbpDevState) <= kStaticStateWords * sizeof(unsigned long long),
+              "state words do not fit");
+
+// [0, kStaticStateWords): SbpDevState; then kStaticCells int64 accumulators.
+static __device__ __align__(256) unsigned long long g_static_scratch[kStaticStateWords + kStaticCells];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+unsigned long long* g_static_ptr[kMaxDevices] = {};  // device address, per device
+int g_static_sms[kMaxDevices] = {};
+
+// One-time set-up per device (with that device current): the device address
+// of the scratch array. A host-side reference to g_static_scratch is only a
+// stand-in, never a usable device pointer, so kernels get this address.
+int static_scratch(int dev, unsigned long long** out, int* sms) {
+    if (dev < 0 || dev >= kMaxDevices) {
+        sbp_set_error("forward_static: device index out of range");
+        return SBP_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        if (sbp_cuda_check(cudaGetSymbolAddress(&p, g_static_scratch),
+                           "forward_static: scratch address"))
+            return SBP_ERR_CUDA;
+        int n = 0;
+        if (sbp_cuda_check(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev),
+                           "forward_static: SM count"))
+            return SBP_ERR_CUDA;
+        g_static_sms[dev] = n > 0 ? n : 1;
+        g_static_ptr[dev] = static_cast<unsigned long long*>(p);
+    }
+    *out = g_static_ptr[dev];
+    *sms = g_static_sms[dev];
+    return SBP_OK;
+}
+
+}  // namespace
+
+extern "C" int sbp_forward_static(const float* sensors_dev, int M, double c_mm_per_us,
+                                  double dt_us, int T_k, int weight_mode, sbp_balls balls,
+                                  const int* n_dev, int n_cap, float* S_dev, sbp_stream stream) {
+    if (!sensors_dev || !S_dev || !balls.x || !balls.y || !balls.z || !balls.R || !balls.p0 ||
+        M < 1 || T_k < 1 || n_cap < 1 || !(c_mm_per_us > 0) || !(dt_us > 0) ||
+        weight_mode < SBP_W_CLAMP || weight_mode > SBP_W_COS) {
+        sbp_set_error("forward_static: invalid argument");
+        return SBP_ERR_ARG;
+    }
+    if ((long long)M * T_k > kStaticCells) {
+        sbp_set_error("forward_static: M * T_k exceeds the static scratch of 2^21 cells "
+                      "(16 MiB); use sbp_forward with an array object");
+        return SBP_ERR_ARG;
+    }
+    int dev = 0, sms = 1;
+    if (sbp_cuda_check(cudaGetDevice(&dev), "forward_static: device")) return SBP_ERR_CUDA;
+    unsigned long long* base = nullptr;
+    if (int e = static_scratch(dev, &base, &sms)) return e;
+    SbpDevState* state = reinterpret_cast<SbpDevState*>(base);
+    unsigned long long* acc = base + kStaticStateWords;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+    LevelGeo g;
+    const double h = c_mm_per_us * dt_us;
+    g.M = M;
+    g.Tk = T_k;
+    g.h_hi = (float)h;
+    g.h_lo = (float)(h - (double)g.h_hi);
+    g.inv_h = (float)(1.0 / h);
+    g.inv_4h = (float)(0.25 / h);
+    g.wmode = weight_mode;
+    g.pad = 0;
+    const BallsDev b{balls.x, balls.y, balls.z, balls.R, balls.p0};
+
+    // the array keeps whatever the last call left: clear the state words and
+    // the accumulators this call uses
+    if (sbp_cuda_check(cudaMemsetAsync(base, 0,
+                                       sizeof(unsigned long long) *
+                                           (kStaticStateWords + (size_t)M * T_k),
+                                       st),
+                       "forward_static: clear scratch"))
+        return SBP_ERR_CUDA;
+    const int groups = (M + 31) / 32;
+    int chunk = kChunk;
+    while (chunk > 32 && (long long)((n_cap + chunk - 1) / chunk) * groups < 4LL * sms) chunk >>= 1;
+    const size_t smem = (size_t)2 * kWindow * 32 * sizeof(unsigned int);
+    if (sbp_cuda_check(cudaFuncSetAttribute(fwd_group_kernel,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem),
+                       "forward_static: smem attribute"))
+        return SBP_ERR_CUDA;
+    fwd_pmax_kernel<<<std::max(1, std::min(4 * sms, (n_cap + 255) / 256)), 256, 0, st>>>(
+        b.p0, n_dev, n_cap, state);
+    if (sbp_cuda_check(cudaGetLastError(), "forward_static: pmax launch")) return SBP_ERR_CUDA;
+    dim3 grid((n_cap + chunk - 1) / chunk, groups);
+    fwd_group_kernel<<<grid, kGroupWarps * 32, smem, st>>>(b, n_dev, n_cap, sensors_dev, g, chunk,
+                                                           state, acc);
+    if (sbp_cuda_check(cudaGetLastError(), "forward_static: accumulate launch"))
+        return SBP_ERR_CUDA;
+    fwd_finalize_kernel<<<M, kFinalizeThreads, 0, st>>>(acc, T_k, state, S_dev);
+    if (sbp_cuda_check(cudaGetLastError(), "forward_static: finalize launch")) return SBP_ERR_CUDA;
     sbp_count_launches(3);
     return SBP_OK;
 }
