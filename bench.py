@@ -376,9 +376,12 @@ def run_native(args, rank, world, local):
 # Thread-level arithmetic operations per pair of the two hot kernels, counted
 # from the per-pair code of the algorithm (FP32 and integer arithmetic,
 # compares and conversions; loads, stores, branches and loop control are not
-# counted). The derivation is tabulated in the design doc. The adjoint's window
-# sum costs 3 operations per ramp cell beyond the first, L = 2 R / h on
-# average.
+# counted). Forward: exact distance 52, inside test 2, window 45, weight 6,
+# K 4, coefficients 15, range test 11, conversions 4, impulses 11, 32-bit
+# split 12, bounds and addresses 8, shared atomics 12. Adjoint: distance 52,
+# window 45, direction and weight 8, tests and bounds 11, chain rule 40, plus
+# the window sums: 3 operations per ramp cell beyond the first and 2 more,
+# with L = 2 R / h cells on average.
 FWD_OPS_PER_PAIR = 182
 
 
