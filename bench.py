@@ -252,7 +252,7 @@ def run_native(args, rank, world, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    ev = {name: [] for name in ("fwd", "adj")}
+    ev = {name: [] for name in ("fwd", "adj", "zero")}
 
     def step(record):
         balls.copy_(init)
@@ -261,7 +261,14 @@ def run_native(args, rank, world, local):
         zl = 0
         arr.set_sampling_level(zl, y_full, out=yk[zl])
         arr.residual(None, yk[zl], G=G[zl], want_loss=False)
+        if record:
+            z0 = torch.cuda.Event(enable_timing=True)
+            z0.record(stream)
         arr.adjoint(balls, G[zl], n=n_dev, mask=sb.MASK_P0, out=grads)
+        if record:
+            z1 = torch.cuda.Event(enable_timing=True)
+            z1.record(stream)
+            ev["zero"].append((zl, z0, z1))
         arr.filter_grow(balls, grads, n_dev, mode=sb.KEEP_NEG, extra=[mom])
         for t, st in enumerate(stages, start=1):
             k = st.level
@@ -332,7 +339,7 @@ def run_native(args, rank, world, local):
             out.setdefault(k, []).append(e0.elapsed_time(e1))
         return {k: statistics.mean(v) for k, v in out.items()}
 
-    fwd_ms, adj_ms = per_level("fwd"), per_level("adj")
+    fwd_ms, adj_ms, zero_ms = per_level("fwd"), per_level("adj"), per_level("zero")
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps,
@@ -349,7 +356,8 @@ def run_native(args, rank, world, local):
         },
         "gpu_launches": int(launches),
         "kernel_ms": {"forward": {str(k): v for k, v in fwd_ms.items()},
-                      "adjoint": {str(k): v for k, v in adj_ms.items()}},
+                      "adjoint": {str(k): v for k, v in adj_ms.items()},
+                      "zero_gradient_adjoint": {str(k): v for k, v in zero_ms.items()}},
     }
     if clk is not None:
         result["clocks"] = clk

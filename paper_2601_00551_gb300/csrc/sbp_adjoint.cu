@@ -110,6 +110,9 @@ struct GradOut {
     float* o[5];  // x, y, z, R, p0
 };
 
+// P0_ONLY: only dL/dp0 is wanted (the zero-gradient pass), so the chain rule
+// for R and the centre is skipped.
+template <bool P0_ONLY>
 __global__ void __cluster_dims__(1, kAdjSplit, 1) __launch_bounds__(kAdjThreads)
 adj_group_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restrict__ sens,
                  LevelGeo g, const float* __restrict__ G, unsigned mask, GradOut out) {
@@ -215,10 +218,11 @@ adj_group_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restric
             const float Df = gf - gl;
             const float A = Df * fmaxf(R - b0, 0.0f) * (R + b0) + E0 * h * (2.0f * b0 - h) -
                             hh2 * E1;
-            const float Bh = h * E0 - b0 * Df;
             const float qd = g.inv_4h * pd.rd;  // 1 / (4 d h)
             const float K0 = w * qd;
             gp += K0 * A;
+            if (P0_ONLY) continue;
+            const float Bh = h * E0 - b0 * Df;
             gR += 2.0f * p0 * K0 * R * Df;
             const float gd = p0 * K0 * (2.0f * Bh - A * pd.rd);
             const float gw = p0 * A * qd * act;
@@ -284,8 +288,12 @@ int sbp_launch_adjoint(sbp_array_s* a, const BallsDev& b, const int* n_dev, int 
     o.o[3] = out.gR;
     o.o[4] = out.gp0;
     const dim3 grid((n_cap + kAdjThreads - 1) / kAdjThreads, kAdjSplit);
-    adj_group_kernel<<<grid, kAdjThreads, 0, st>>>(
-        b, n_dev, n_cap, a->d_sens, g, G, mask, o);
+    if (mask == SBP_MASK_P0)
+        adj_group_kernel<true><<<grid, kAdjThreads, 0, st>>>(b, n_dev, n_cap, a->d_sens, g, G,
+                                                             mask, o);
+    else
+        adj_group_kernel<false><<<grid, kAdjThreads, 0, st>>>(b, n_dev, n_cap, a->d_sens, g, G,
+                                                              mask, o);
     if (sbp_cuda_check(cudaGetLastError(), "adjoint: launch")) return SBP_ERR_CUDA;
     sbp_count_launches(1);
     return SBP_OK;

@@ -395,3 +395,33 @@ class SensorArray:
         _check("sbp_get_inside_pairs", self._lib.sbp_get_inside_pairs(self._h, _stream(),
                                                                        ctypes.byref(c)))
         return c.value
+
+
+class _Radiator(torch.autograd.Function):
+    """Traces S = Simulate(balls) at one level, differentiable in every ball
+    parameter. The forward saves only the cloud (the inputs); the backward
+    recomputes each pair's geometry inside the adjoint kernel instead of
+    storing per-pair windows."""
+
+    @staticmethod
+    def forward(ctx, x, y, z, R, p0, array, level):
+        balls = torch.stack([x, y, z, R, p0]).contiguous()
+        array.set_sampling_level(level)
+        S = array.forward(balls)
+        ctx.save_for_backward(balls)
+        ctx.array, ctx.level = array, level
+        return S
+
+    @staticmethod
+    def backward(ctx, gS):
+        (balls,) = ctx.saved_tensors
+        ctx.array.set_sampling_level(ctx.level)
+        g = ctx.array.adjoint(balls, gS.contiguous(), mask=MASK_ALL)
+        return g[0], g[1], g[2], g[3], g[4], None, None
+
+
+def radiate(array: SensorArray, x, y, z, R, p0, level: int = 0) -> torch.Tensor:
+    """Differentiable forward radiator: (M, T_k) traces of the balls with
+    centres (x, y, z), radii R and pressures p0 (float32 CUDA vectors) at
+    sampling level `level` of `array`."""
+    return _Radiator.apply(x, y, z, R, p0, array, level)

@@ -434,3 +434,42 @@ def test_reconstruct_matches_oracle_loop(sb):
     assert losses[1] < losses[0]
     out = balls[:, :bo.shape[1]].cpu().numpy()
     np.testing.assert_allclose(out, bo, rtol=0, atol=1e-4)
+
+
+# --------------------------------------------------------------- autograd
+
+def test_autograd_function_matches_oracle_adjoint(sb):
+    """torch.autograd through radiate(): L = ||S - y||^2 built from torch ops,
+    gradients against the FP64 oracle's adjoint (itself pinned by central
+    differences and complex-step derivatives); p0 also against a GPU finite
+    difference, exact up to rounding because S is linear in p0."""
+    wl = workloads.tiny(n_init=1000)
+    b = wl.init.stack()
+    arr = make_array(sb, wl, (2, 1), b.shape[1])
+    y = _measured(wl, 1)
+    for k, f in enumerate((2, 1)):
+        Tk = wl.T // f
+        yk = torch.from_numpy(oracle.downsample(y, f).astype(np.float32)).cuda()
+        leaves = [torch.from_numpy(b[c].copy()).cuda().requires_grad_() for c in range(5)]
+        S = sb.radiate(arr, *leaves, level=k)
+        L = ((S - yk) ** 2).sum()
+        L.backward()
+        g = np.stack([t.grad.cpu().numpy() for t in leaves])
+        S_ref = oracle.forward(b, wl.sensors.pos, wl.sensors.normal, wl.c, dt_of(wl, f), Tk)
+        G = (2.0 * (S.detach().cpu().numpy().astype(np.float64) - yk.cpu().numpy()))
+        ref = oracle.adjoint(b, wl.sensors.pos, wl.sensors.normal, wl.c, dt_of(wl, f), Tk, G,
+                             threads=threads())
+        assert rel_l2(S.detach().cpu().numpy(), S_ref) <= TRACE_TOL
+        for c in range(5):
+            assert rel_l2(g[c], ref[c]) <= GRAD_TOL, (f, c)
+        # p0: finite difference on the GPU path along a random direction
+        rng = np.random.default_rng(k)
+        v = torch.from_numpy(rng.normal(size=b.shape[1]).astype(np.float32)).cuda()
+        eps = 1e-2
+        with torch.no_grad():
+            def loss(p):
+                return float(((sb.radiate(arr, *leaves[:4], p, level=k) - yk) ** 2)
+                             .double().sum().item())
+            fd = (loss(leaves[4] + eps * v) - loss(leaves[4] - eps * v)) / (2 * eps)
+        an = float((leaves[4].grad.double() * v.double()).sum().item())
+        assert abs(fd - an) <= 1e-3 * abs(an) + 1e-6
