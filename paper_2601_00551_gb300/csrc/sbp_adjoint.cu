@@ -128,10 +128,38 @@ adj_group_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restric
     const int c0 = blockIdx.x * kAdjThreads;
     if (c0 >= n) return;  // uniform over the whole cluster (same chunk)
     const int c1 = min(n, c0 + kAdjThreads);
-    const int i = c0 + (int)threadIdx.x;
-    const bool valid = i < c1;
+    const int nb = c1 - c0;
     const int Tk = g.Tk, M = g.M;
-    sbp_chunk_box(b, c0, c1, s_red, s_box);
+    // Threads take the chunk's balls in order of their window length class
+    // floor(2R/h), so the lanes of a warp run window loops of nearly equal
+    // length. (The order within a class is arbitrary; every ball's result is
+    // computed by one thread and stored under the ball's own index.)
+    __shared__ int s_cls[32], s_perm[kAdjThreads];
+    if (threadIdx.x < 32) s_cls[threadIdx.x] = 0;
+    sbp_chunk_box(b, c0, c1, s_red, s_box);  // also orders the clearing above
+    int cls = 0;
+    if ((int)threadIdx.x < nb) {
+        const float Rk = b.R[c0 + threadIdx.x] * 2.0f * g.inv_h;
+        cls = (int)fminf(fmaxf(Rk, 0.0f), 31.0f);  // NaN -> 0
+        atomicAdd(&s_cls[cls], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive scan of the 32 class counts
+        const int v = s_cls[threadIdx.x];
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, x, o);
+            if ((int)threadIdx.x >= o) x += t;
+        }
+        s_cls[threadIdx.x] = x - v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nb) s_perm[atomicAdd(&s_cls[cls], 1)] = threadIdx.x;
+    __syncthreads();
+    const bool valid = (int)threadIdx.x < nb;
+    const int li = valid ? s_perm[threadIdx.x] : 0;  // this thread's ball, chunk-local
+    const int i = c0 + li;
     float cx = 0.f, cy = 0.f, cz = 0.f, R = 0.f, p0 = 0.f;
     if (valid) {
         cx = b.x[i];
@@ -200,8 +228,16 @@ adj_group_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restric
                 gl = jH < Tk ? Gw[jH - jL] : 0.0f;
                 // E1 = sum_q q d_q accumulated as the running sums of the tail
                 float run = 0.0f;
-                for (int q = L - 1; q >= 1; --q) {
-                    run += Gw[q] - gl;
+                int q = L - 1;
+                for (; q >= 2; q -= 2) {
+                    const float d1 = Gw[q] - gl, d0 = Gw[q - 1] - gl;
+                    run += d1;
+                    E1 += run;
+                    run += d0;
+                    E1 += run;
+                }
+                if (q == 1) {
+                    run += Gw[1] - gl;
                     E1 += run;
                 }
                 E0 = L > 0 ? run + (Gw[0] - gl) : 0.0f;
@@ -231,25 +267,31 @@ adj_group_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restric
             gz += gd * uz + gw * (nz - cosv * uz) * pd.rd;
         }
     }
-    s_part[threadIdx.x * 5 + 0] = gx;
-    s_part[threadIdx.x * 5 + 1] = gy;
-    s_part[threadIdx.x * 5 + 2] = gz;
-    s_part[threadIdx.x * 5 + 3] = gR;
-    s_part[threadIdx.x * 5 + 4] = gp;
+    if (valid) {  // stored under the ball's chunk-local index
+        s_part[li * 5 + 0] = gx;
+        s_part[li * 5 + 1] = gy;
+        s_part[li * 5 + 2] = gz;
+        s_part[li * 5 + 3] = gR;
+        s_part[li * 5 + 4] = gp;
+    }
     cluster.sync();
     if (part == 0 && valid) {
-        float acc[5] = {gx, gy, gz, gR, gp};
-        for (int r = 1; r < kAdjSplit; ++r) {
-            const float* rp = cluster.map_shared_rank(s_part, r) + threadIdx.x * 5;
+        float ax = gx, ay = gy, az = gz, aR = gR, ap = gp;
 #pragma unroll
-            for (int k = 0; k < 5; ++k) acc[k] += rp[k];
+        for (int r = 1; r < kAdjSplit; ++r) {
+            const float* rp = cluster.map_shared_rank(s_part, r) + li * 5;
+            ax += rp[0];
+            ay += rp[1];
+            az += rp[2];
+            aR += rp[3];
+            ap += rp[4];
         }
         const bool xyz = mask & SBP_MASK_XYZ;
-        out.o[0][i] = xyz ? acc[0] : 0.0f;
-        out.o[1][i] = xyz ? acc[1] : 0.0f;
-        out.o[2][i] = xyz ? acc[2] : 0.0f;
-        out.o[3][i] = (mask & SBP_MASK_R) ? acc[3] : 0.0f;
-        out.o[4][i] = (mask & SBP_MASK_P0) ? acc[4] : 0.0f;
+        out.o[0][i] = xyz ? ax : 0.0f;
+        out.o[1][i] = xyz ? ay : 0.0f;
+        out.o[2][i] = xyz ? az : 0.0f;
+        out.o[3][i] = (mask & SBP_MASK_R) ? aR : 0.0f;
+        out.o[4][i] = (mask & SBP_MASK_P0) ? ap : 0.0f;
     }
     cluster.sync();  // the other CTAs' shared memory must outlive the reads above
 }
