@@ -59,8 +59,10 @@ typedef enum {
 enum { SBP_W_CLAMP = 0, SBP_W_NONE = 1, SBP_W_COS = 2 };
 
 /* Gradient components (bit mask). The coarse stage of Section 4.1 updates
- * p0 and R only; the fine stage updates all five. */
-enum { SBP_MASK_P0 = 1, SBP_MASK_R = 2, SBP_MASK_XYZ = 4, SBP_MASK_ALL = 7 };
+ * p0 and R only; the fine stage updates all five. SBP_SOFTPLUS_R (only for
+ * sbp_adam_step and stages) optimises R through R = softplus(a) with a free
+ * variable a, the positivity-constrained refinement of Section 4.3. */
+enum { SBP_MASK_P0 = 1, SBP_MASK_R = 2, SBP_MASK_XYZ = 4, SBP_MASK_ALL = 7, SBP_SOFTPLUS_R = 8 };
 
 /* sbp_filter_grow modes. The three zero-gradient rules are the readings of
  * Section 4.2: Algorithm 1 keeps g < 0 (SBP_KEEP_NEG, default), the
@@ -212,7 +214,11 @@ int sbp_filter_grow(sbp_array arr, sbp_balls balls, sbp_grads grads, float* cons
                     sbp_stream stream);
 
 /* One Adam step at step count t >= 1 on the components in mask; m and v
- * are the first and second moments, laid out like the balls. */
+ * are the first and second moments, laid out like the balls. With
+ * SBP_SOFTPLUS_R in mask (and SBP_MASK_R), the R component is updated in the
+ * softplus parameterisation of Section 4.3: a = softplus^-1(R), its gradient
+ * sigma(a) dL/dR = (1 - exp(-R)) dL/dR drives the moments, and R becomes
+ * softplus(a - step), which is positive for every step. */
 int sbp_adam_step(sbp_array arr, sbp_balls balls, sbp_grads grads, sbp_balls m, sbp_balls v,
                   const int* n_dev, int n_cap, int t, const sbp_adam_params* ap,
                   unsigned mask, sbp_stream stream);
@@ -225,7 +231,7 @@ int sbp_adam_step(sbp_array arr, sbp_balls balls, sbp_grads grads, sbp_balls m, 
 typedef struct {
     int level;
     int iterations;
-    unsigned grad_mask;
+    unsigned grad_mask; /* may include SBP_SOFTPLUS_R */
     int grow;
     int duplicate;
 } sbp_stage;
@@ -244,6 +250,11 @@ typedef struct {
     int log_capacity;     /* entries available in the logs */
 } sbp_recon_params;
 
+/* The point-cloud reconstruction loop of Algorithm 1 on the device.
+ * A stage whose grad_mask holds SBP_SOFTPLUS_R is the positivity-constrained
+ * refinement of Section 4.3: its R moments restart from zero when it begins
+ * (the free variable is new), and it should run with grow = 0 (the paper
+ * stops adaptive density changes in that phase). */
 /* The point-cloud reconstruction loop of Algorithm 1 on the device:
  * zero-gradient filtering at zero_grad_level (Section 4.2), then for every
  * stage and iteration: forward, residual (L = ||S - y_k||^2), adjoint, one

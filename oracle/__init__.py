@@ -40,6 +40,7 @@ _lib = None
 W_MODES = {"clamp": 0, "none": 1, "cos": 2}
 MASK_P0, MASK_R, MASK_XYZ = 1, 2, 4
 MASK_ALL = 7
+SOFTPLUS_R = 8  # optimise R through R = softplus(a) (Section 4.3)
 
 
 def build(force: bool = False) -> str:
@@ -325,11 +326,26 @@ class AdamParams:
     eps: float = 1e-8
 
 
+def softplus(a):
+    """log(1 + e^a) = max(a, 0) + log(1 + e^-|a|), without overflow."""
+    a = np.asarray(a, dtype=np.float64)
+    return np.maximum(a, 0.0) + np.log1p(np.exp(-np.abs(a)))
+
+
+def softplus_inv(R):
+    """The a with softplus(a) = R > 0: log(e^R - 1) = R + log(1 - e^-R)."""
+    R = np.asarray(R, dtype=np.float64)
+    return R + np.log(-np.expm1(-R))
+
+
 def adam(balls, grads, m, v, t: int, ap: AdamParams, mask: int = MASK_ALL):
     """One Adam step (Kingma & Ba 2015) at step count t >= 1 on the
-    parameters selected by `mask`; returns new (balls, m, v) in float64."""
+    parameters selected by `mask`; returns new (balls, m, v) in float64.
+    With SOFTPLUS_R the radius is optimised as R = softplus(a) (the
+    positivity-constrained refinement of Section 4.3): the moments follow
+    dL/da = sigmoid(a) dL/dR and R becomes softplus(a - step)."""
     b = _f64(balls).reshape(5, -1).copy()
-    g = _f64(grads).reshape(5, -1)
+    g = _f64(grads).reshape(5, -1).copy()
     m = _f64(m).reshape(5, -1).copy()
     v = _f64(v).reshape(5, -1).copy()
     bits = [MASK_XYZ, MASK_XYZ, MASK_XYZ, MASK_R, MASK_P0]
@@ -338,9 +354,15 @@ def adam(balls, grads, m, v, t: int, ap: AdamParams, mask: int = MASK_ALL):
     for k in range(5):
         if not (mask & bits[k]):
             continue
+        sp = k == 3 and (mask & SOFTPLUS_R)
+        p = b[k]
+        if sp:
+            p = softplus_inv(b[k])
+            g[k] = g[k] / (1.0 + np.exp(-p))  # sigmoid(a) dL/dR
         m[k] = ap.beta1 * m[k] + (1.0 - ap.beta1) * g[k]
         v[k] = ap.beta2 * v[k] + (1.0 - ap.beta2) * g[k] * g[k]
-        b[k] = b[k] - ap.lr[k] * (m[k] / c1) / (np.sqrt(v[k] / c2) + ap.eps)
+        p = p - ap.lr[k] * (m[k] / c1) / (np.sqrt(v[k] / c2) + ap.eps)
+        b[k] = softplus(p) if sp else p
     return b, m, v
 
 
@@ -386,20 +408,27 @@ def reconstruct(balls, pos, normal, c, fs_mhz, T, factors, y_full, stages,
         b, m, v = b[:, keep], m[:, keep], v[:, keep]
     losses, counts = [], []
     t = 0
+    prev_sp = False
     for st in stages:
         dt, Tk, yk = level_data(st.level)
+        sp = bool(st.grad_mask & SOFTPLUS_R)
+        if sp and not prev_sp:  # the refinement's free variable starts with fresh moments
+            m[3] = 0.0
+            v[3] = 0.0
+        prev_sp = sp
+        gmask = st.grad_mask & MASK_ALL
         for _ in range(st.iterations):
             counts.append(b.shape[1])
             S = forward(b, pos, normal, c, dt, Tk, wmode=wmode, threads=threads)
             L, G = loss_and_residual(S, yk)
             losses.append(L)
-            g = adjoint(b, pos, normal, c, dt, Tk, G.astype(np.float32), mask=st.grad_mask,
+            g = adjoint(b, pos, normal, c, dt, Tk, G.astype(np.float32), mask=gmask,
                         wmode=wmode, threads=threads)
             t += 1
             nb, nm, nv = adam(b, g, m, v, t, ap, mask=st.grad_mask)
             b, m, v = nb.astype(np.float32), nm.astype(np.float32), nv.astype(np.float32)
             if st.grow:
-                gp = dataclasses.replace(gpar, seed=gpar.seed + t, grad_mask=st.grad_mask,
+                gp = dataclasses.replace(gpar, seed=gpar.seed + t, grad_mask=gmask,
                                          duplicate=st.duplicate)
                 b, _, ex, _ = grow(b, g.astype(np.float32), np.concatenate([m, v]), gp)
                 m, v = ex[:5].copy(), ex[5:].copy()

@@ -292,7 +292,7 @@ int sbp_adam_step(sbp_array arr, sbp_balls balls, sbp_grads grads, sbp_balls m, 
     if (int e = check_array(arr, "adam_step")) return e;
     if (int e = check_cap(arr, n_cap, "adam_step")) return e;
     if (!balls_ok(balls) || !grads_ok(grads) || !balls_ok(m) || !balls_ok(v) || !ap || t < 1 ||
-        (mask & ~SBP_MASK_ALL)) {
+        (mask & ~(SBP_MASK_ALL | SBP_SOFTPLUS_R))) {
         sbp_set_error("adam_step: invalid argument");
         return SBP_ERR_ARG;
     }

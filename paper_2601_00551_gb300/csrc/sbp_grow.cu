@@ -224,12 +224,24 @@ __global__ void adam_kernel(AdamArgs a, const int* n_dev, int n_cap) {
         for (int k = 0; k < 5; ++k) {
             const unsigned bit = k < 3 ? SBP_MASK_XYZ : (k == 3 ? SBP_MASK_R : SBP_MASK_P0);
             if (!(a.mask & bit)) continue;
-            const float g = a.g[k][i];
+            float g = a.g[k][i];
+            const bool sp = k == 3 && (a.mask & SBP_SOFTPLUS_R);
+            float p = a.p[k][i];
+            float u = p;
+            if (sp) {
+                // a = softplus^-1(R) = R + log(1 - exp(-R)); sigma(a) = 1 - exp(-R)
+                p = fmaxf(p, 1e-30f);
+                const float em = expf(-p);
+                g *= 1.0f - em;
+                u = p + log1pf(-em);
+            }
             const float m = a.b1 * a.m[k][i] + (1.0f - a.b1) * g;
             const float v = a.b2 * a.v[k][i] + (1.0f - a.b2) * g * g;
             a.m[k][i] = m;
             a.v[k][i] = v;
-            a.p[k][i] -= a.lr[k] * (m / a.c1) / (sqrtf(v / a.c2) + a.eps);
+            u -= a.lr[k] * (m / a.c1) / (sqrtf(v / a.c2) + a.eps);
+            if (sp) u = fmaxf(u, 0.0f) + log1pf(expf(-fabsf(u)));  // softplus
+            a.p[k][i] = u;
         }
     }
 }

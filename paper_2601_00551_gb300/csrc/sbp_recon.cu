@@ -45,7 +45,7 @@ extern "C" int sbp_reconstruct(sbp_array arr, const float* y_full_dev, sbp_balls
     for (int s = 0; s < rp->n_stages; ++s) {
         const sbp_stage& st = rp->stages[s];
         if (st.level < 0 || st.level >= arr->n_levels || st.iterations < 0 ||
-            (st.grad_mask & ~SBP_MASK_ALL)) {
+            (st.grad_mask & ~(SBP_MASK_ALL | SBP_SOFTPLUS_R))) {
             sbp_set_error("reconstruct: invalid stage");
             return SBP_ERR_ARG;
         }
@@ -87,6 +87,16 @@ extern "C" int sbp_reconstruct(sbp_array arr, const float* y_full_dev, sbp_balls
     int t = 0;
     for (int s = 0; s < rp->n_stages; ++s) {
         const sbp_stage& stg = rp->stages[s];
+        const unsigned gmask = stg.grad_mask & SBP_MASK_ALL;
+        const bool softplus_starts = (stg.grad_mask & SBP_SOFTPLUS_R) &&
+                                     !(s > 0 && (rp->stages[s - 1].grad_mask & SBP_SOFTPLUS_R));
+        if (softplus_starts) {  // the free variable of the refinement starts with fresh moments
+            if (sbp_cuda_check(cudaMemsetAsync(m.R, 0, sizeof(float) * cap, cs),
+                               "reconstruct: reset m") ||
+                sbp_cuda_check(cudaMemsetAsync(v.R, 0, sizeof(float) * cap, cs),
+                               "reconstruct: reset v"))
+                return SBP_ERR_CUDA;
+        }
         for (int it = 0; it < stg.iterations; ++it) {
             if (int e = use_level(stg.level)) return e;
             if (rp->n_log_dev && t < rp->log_capacity &&
@@ -100,8 +110,7 @@ extern "C" int sbp_reconstruct(sbp_array arr, const float* y_full_dev, sbp_balls
             if (int e = sbp_launch_residual(arr, arr->d_rc_S, arr->d_rc_yk, arr->d_rc_G, loss,
                                             cs))
                 return e;
-            if (int e = sbp_launch_adjoint(arr, bd, n_dev, n_cap, arr->d_rc_G, grads,
-                                           stg.grad_mask, cs))
+            if (int e = sbp_launch_adjoint(arr, bd, n_dev, n_cap, arr->d_rc_G, grads, gmask, cs))
                 return e;
             ++t;
             if (int e = sbp_launch_adam(arr, balls, grads, m, v, n_dev, n_cap, t, &rp->adam,
@@ -110,7 +119,7 @@ extern "C" int sbp_reconstruct(sbp_array arr, const float* y_full_dev, sbp_balls
             if (stg.grow) {
                 sbp_grow_params gp = rp->grow;
                 gp.seed = rp->grow.seed + (uint64_t)t;
-                gp.grad_mask = (int)stg.grad_mask;
+                gp.grad_mask = (int)gmask;
                 gp.duplicate = stg.duplicate;
                 if (int e = sbp_launch_filter_grow(arr, balls, grads, extra, 10, n_dev, n_cap, &gp,
                                                    SBP_GROW, cs))

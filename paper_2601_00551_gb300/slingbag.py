@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libslingbag.so")
 SBP_OK = 0
 W_MODES = {"clamp": 0, "none": 1, "cos": 2}
 MASK_P0, MASK_R, MASK_XYZ, MASK_ALL = 1, 2, 4, 7
+SOFTPLUS_R = 8  # optimise R through R = softplus(a) (positivity-constrained refinement)
 KEEP_NEG, KEEP_NONPOS, DROP_ZERO, GROW = 0, 1, 2, 3
 
 _P = ctypes.c_void_p

@@ -473,3 +473,59 @@ def test_autograd_function_matches_oracle_adjoint(sb):
             fd = (loss(leaves[4] + eps * v) - loss(leaves[4] - eps * v)) / (2 * eps)
         an = float((leaves[4].grad.double() * v.double()).sum().item())
         assert abs(fd - an) <= 1e-3 * abs(an) + 1e-6
+
+
+# ------------------------------------------- softplus refinement (Section 4.3)
+
+def test_adam_softplus_matches_oracle(sb):
+    rng = np.random.default_rng(11)
+    n = 2000
+    b = np.abs(rng.normal(size=(5, n))).astype(np.float32) + 0.02
+    g = rng.normal(size=(5, n)).astype(np.float32)
+    m = (0.1 * rng.normal(size=(5, n))).astype(np.float32)
+    v = (0.1 * rng.random(size=(5, n))).astype(np.float32)
+    wl = workloads.tiny(M=4, T=64)
+    arr = make_array(sb, wl, (1,), n)
+    ap = dict(lr=(1e-3, 1e-3, 1e-3, 5e-2, 1e-2))
+    mask = sb.MASK_ALL | sb.SOFTPLUS_R
+    B, Gt = torch.from_numpy(b).cuda(), torch.from_numpy(g).cuda()
+    Mt, Vt = torch.from_numpy(m).cuda(), torch.from_numpy(v).cuda()
+    arr.adam_step(B, Gt, Mt, Vt, 4, sb.AdamParams(**ap), mask=mask)
+    rb, rm, rv = oracle.adam(b, g, m, v, 4, oracle.AdamParams(**ap), mask=mask)
+    np.testing.assert_allclose(B.cpu().numpy(), rb, rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(Mt.cpu().numpy(), rm, rtol=0,
+                               atol=1e-6 * (np.abs(m).max() + np.abs(g).max()))
+    assert np.all(B[3].cpu().numpy() > 0)
+
+
+def test_reconstruct_with_softplus_refinement_matches_oracle(sb):
+    wl = workloads.tiny()
+    b = wl.init.stack()
+    n = b.shape[1]
+    y = _measured(wl, 1)
+    factors = (2, 1)
+    arr = make_array(sb, wl, factors, 2 * n)
+    sp = 7 | oracle.SOFTPLUS_R
+    st_o = [oracle.Stage(0, 2, 3, True, False), oracle.Stage(1, 2, 7, True, True),
+            oracle.Stage(1, 3, sp, False, False)]
+    st_g = [sb.Stage(s.level, s.iterations, s.grad_mask, s.grow, s.duplicate) for s in st_o]
+    grow = dict(p_min=1e-3, R_min=0.02, R_max=0.3, g_dup=5.0, seed=5)
+    ap = dict(lr=(1e-3, 1e-3, 1e-3, 5e-3, 1e-2))
+    bo, losses, counts = oracle.reconstruct(b, wl.sensors.pos, wl.sensors.normal, wl.c,
+                                            wl.fs_mhz, wl.T, factors, y, st_o,
+                                            adam_params=oracle.AdamParams(**ap),
+                                            grow_params=oracle.GrowParams(**grow),
+                                            threads=threads())
+    balls = torch.zeros((5, 2 * n), device="cuda")
+    balls[:, :n] = torch.from_numpy(b)
+    n_dev = torch.tensor([n], dtype=torch.int32, device="cuda")
+    loss = torch.zeros(7, dtype=torch.float64, device="cuda")
+    n_log = torch.zeros(7, dtype=torch.int32, device="cuda")
+    arr.reconstruct(torch.from_numpy(y).cuda(), balls, n_dev, st_g, adam=sb.AdamParams(**ap),
+                    grow=sb.GrowParams(**grow), loss_log=loss, n_log=n_log)
+    assert arr.sync_status() == 0
+    np.testing.assert_array_equal(n_log.cpu().numpy(), counts)
+    np.testing.assert_allclose(loss.cpu().numpy(), losses, rtol=1e-4)
+    out = balls[:, :bo.shape[1]].cpu().numpy()
+    np.testing.assert_allclose(out, bo, rtol=0, atol=1e-4)
+    assert np.all(out[3] > 0)

@@ -455,3 +455,55 @@ def test_adam_first_step_is_signed_learning_rate():
     nb2, _, _ = oracle.adam(b, g, np.zeros((5, 9)), np.zeros((5, 9)), 1, ap,
                             mask=oracle.MASK_P0 | oracle.MASK_R)
     np.testing.assert_array_equal(nb2[:3], b[:3])
+
+
+# ----------------------------------------------- softplus refinement (4.3)
+
+def test_softplus_inverse_and_sigmoid_identity():
+    R = np.array([1e-6, 1e-3, 0.05, 0.3, 1.0, 5.0, 30.0])
+    a = oracle.softplus_inv(R)
+    np.testing.assert_allclose(oracle.softplus(a), R, rtol=1e-12)
+    # sigmoid(softplus^-1(R)) = 1 - exp(-R)
+    np.testing.assert_allclose(1.0 / (1.0 + np.exp(-a)), -np.expm1(-R), rtol=1e-12)
+    np.testing.assert_allclose(oracle.softplus(np.array([-800.0, 0.0, 800.0])),
+                               [0.0, np.log(2.0), 800.0], rtol=1e-15, atol=1e-300)
+
+
+def test_adam_softplus_first_step_and_positivity():
+    rng = np.random.default_rng(3)
+    b = np.abs(rng.normal(size=(5, 7))) + 0.01
+    g = rng.normal(size=(5, 7))
+    ap = oracle.AdamParams(lr=(1e-3, 1e-3, 1e-3, 0.05, 1e-2))
+    mask = oracle.MASK_ALL | oracle.SOFTPLUS_R
+    nb, _, _ = oracle.adam(b, g, np.zeros((5, 7)), np.zeros((5, 7)), 1, ap, mask=mask)
+    step = ap.lr[3] * np.sign(g[3])  # first Adam step of the free variable: lr * sign
+    np.testing.assert_allclose(nb[3], oracle.softplus(oracle.softplus_inv(b[3]) - step),
+                               rtol=1e-6)
+    # a step far larger than R still leaves R positive
+    huge = oracle.AdamParams(lr=(0, 0, 0, 20.0, 0))
+    nb2, _, _ = oracle.adam(b, np.abs(g) + 1, np.zeros((5, 7)), np.zeros((5, 7)), 1, huge,
+                            mask=mask)
+    assert np.all(nb2[3] > 0)
+    np.testing.assert_allclose(nb2[3], oracle.softplus(oracle.softplus_inv(b[3]) - 20.0),
+                               rtol=1e-6)
+
+
+def test_softplus_chain_rule_matches_finite_difference():
+    """dL/da = sigmoid(a) dL/dR through the radiator (oracle forward and
+    adjoint), against a central difference in a."""
+    rng = np.random.default_rng(4)
+    b, pos, nrm = _random_scene(rng, 6, 4)
+    T = 900
+    y = oracle.forward(_random_scene(rng, 6, 4)[0], pos, nrm, C, DT, T)
+    S = oracle.forward(b, pos, nrm, C, DT, T)
+    gR = oracle.adjoint(b, pos, nrm, C, DT, T, 2 * (S - y), mask=oracle.MASK_R)[3]
+    a = oracle.softplus_inv(b[3])
+    h = 1e-6
+    for i in range(6):
+        bp, bm = b.copy(), b.copy()
+        bp[3, i] = oracle.softplus(a[i] + h)
+        bm[3, i] = oracle.softplus(a[i] - h)
+        fd = (np.sum((oracle.forward(bp, pos, nrm, C, DT, T) - y) ** 2) -
+              np.sum((oracle.forward(bm, pos, nrm, C, DT, T) - y) ** 2)) / (2 * h)
+        an = gR[i] / (1.0 + np.exp(-a[i]))
+        assert abs(fd - an) <= 1e-4 * max(abs(an), 1e-8), (i, fd, an)
