@@ -269,6 +269,63 @@ typedef struct {
 int sbp_reconstruct(sbp_array arr, const float* y_full_dev, sbp_balls balls, int* n_dev,
                     int n_cap, const sbp_recon_params* rp, sbp_stream stream);
 
+/* ---------------------------------------------------------------------- */
+/* Batched frames: many acquisitions (e.g. the frames of dynamic imaging) of
+ * the same array, reconstructed together. Frame f's balls occupy the slice
+ * [off[f], off[f+1]) of one packed cloud (five float32 arrays of the array's
+ * n_cap), its live count is n_dev[f] (int32, device), and its traces are the
+ * [M][T_k] block f of a [F][M][T_k] float32 array. Every step below runs all
+ * frames in one launch per kernel, so an iteration over all frames is a fixed
+ * sequence of launches with no host synchronisation (graph-capturable after
+ * the first call). Results equal those of the single-cloud calls applied to
+ * each frame (growth draws its split direction from the ball's index within
+ * its frame). The paper reconstructs one acquisition at a time; batching is
+ * a property of this library. */
+
+/* Define the frame layout: frame f gets capacity frame_cap_host[f] rounded
+ * up to a multiple of 1024; the padded capacities must fit n_cap. Writes
+ * the n_frames + 1 offsets to frame_off_out (host, may be NULL). Allocates
+ * per-frame scratch; synchronises the device. */
+int sbp_set_frames(sbp_array arr, const int* frame_cap_host, int n_frames, int* frame_off_out);
+
+/* Level select and downsampling of all frames' records ([F][M][T] -> [F][M][T_k]). */
+int sbp_set_sampling_level_frames(sbp_array arr, int k, const float* y_full_dev, float* y_k_dev,
+                                  sbp_stream stream);
+
+int sbp_forward_frames(sbp_array arr, sbp_balls packed, const int* n_dev, float* S_dev,
+                       sbp_stream stream);
+
+/* G = 2 (S - y_k) for all frames; loss_dev (may be NULL) receives one double
+ * per frame. S_dev may be NULL (S = 0). */
+int sbp_residual_frames(sbp_array arr, const float* S_dev, const float* y_k_dev, float* G_dev,
+                        double* loss_dev, sbp_stream stream);
+
+int sbp_adjoint_frames(sbp_array arr, sbp_balls packed, const int* n_dev, const float* G_dev,
+                       sbp_grads out, unsigned grad_mask, sbp_stream stream);
+
+/* Filter/grow each frame inside its slice; a frame that would exceed its
+ * capacity is left unchanged and SBP_ERR_CAPACITY is latched. */
+int sbp_filter_grow_frames(sbp_array arr, sbp_balls packed, sbp_grads grads, float* const* extra,
+                           int n_extra, int* n_dev, const sbp_grow_params* gp, int mode,
+                           sbp_stream stream);
+
+int sbp_adam_step_frames(sbp_array arr, sbp_balls packed, sbp_grads grads, sbp_balls m,
+                         sbp_balls v, const int* n_dev, int t, const sbp_adam_params* ap,
+                         unsigned mask, sbp_stream stream);
+
+/* sbp_reconstruct for all frames in lockstep (same schedule). y_full_dev is
+ * [F][M][T]; the logs hold F entries per iteration (loss_log_dev[t*F + f]). */
+int sbp_reconstruct_frames(sbp_array arr, const float* y_full_dev, sbp_balls packed, int* n_dev,
+                           const sbp_recon_params* rp, sbp_stream stream);
+
+/* Tile autotuner for the batched path: times the forward with 256, 512 and
+ * 1024 balls per CTA and the adjoint with clusters of 1, 2, 4 and 8 CTAs on
+ * the given cloud at the current level (S_dev, G_dev: [F][M][T_k] scratch of
+ * the caller, overwritten), keeps the fastest of each for later batched
+ * calls and reports them. Synchronises. */
+int sbp_autotune_frames(sbp_array arr, sbp_balls packed, const int* n_dev, float* S_dev,
+                        float* G_dev, int* fwd_chunk_out, int* adj_split_out);
+
 /* Number of CUDA kernels this library has launched in this process. */
 long long sbp_launch_count(void);
 

@@ -48,7 +48,7 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int kAdjThreads = 128;  // balls (threads) per adjoint CTA
-constexpr int kAdjSplit = 4;      // CTAs per cluster, each taking 1/kAdjSplit of the sensors
+constexpr int kAdjSplit = 4;      // default CTAs per cluster, each taking 1/split of the sensors
 constexpr int kAdjGroup = 16;     // sensors staged per round
 constexpr int kAdjWindow = 256;   // cells per sensor staged in shared memory
 
@@ -112,10 +112,11 @@ struct GradOut {
 
 // P0_ONLY: only dL/dp0 is wanted (the zero-gradient pass), so the chain rule
 // for R and the centre is skipped.
+// Launched with a cluster of gridDim.y CTAs along y (cudaLaunchKernelEx).
 template <bool P0_ONLY>
-__global__ void __cluster_dims__(1, kAdjSplit, 1) __launch_bounds__(kAdjThreads)
-adj_group_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restrict__ sens,
-                 LevelGeo g, const float* __restrict__ G, unsigned mask, GradOut out) {
+__global__ void __launch_bounds__(kAdjThreads)
+adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, LevelGeo g,
+                 const float* __restrict__ G_all, unsigned mask, GradOut out) {
     __shared__ float sG[kAdjGroup * kAdjWindow];  // [sensor][cell]
     __shared__ float4 s_sa[kAdjGroup];            // sx, sy, sz, nx
     __shared__ float4 s_sb[kAdjGroup];            // ny, nz, jlo, len (as int bits)
@@ -124,12 +125,13 @@ adj_group_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restric
     __shared__ int s_lmax;
     __shared__ float s_part[kAdjThreads * 5];  // this CTA's partial sums
     cg::cluster_group cluster = cg::this_cluster();
-    const int n = sbp_read_n(n_dev, n_cap);
     const int c0 = blockIdx.x * kAdjThreads;
-    if (c0 >= n) return;  // uniform over the whole cluster (same chunk)
-    const int c1 = min(n, c0 + kAdjThreads);
+    const FrameSlot fs = sbp_frame_of(ft, c0);
+    if (c0 >= fs.end) return;  // uniform over the whole cluster (same chunk)
+    const int c1 = min(fs.end, c0 + kAdjThreads);
     const int nb = c1 - c0;
     const int Tk = g.Tk, M = g.M;
+    const float* __restrict__ G = G_all + (size_t)fs.f * M * Tk;
     // Threads take the chunk's balls in order of their window length class
     // floor(2R/h), so the lanes of a warp run window loops of nearly equal
     // length. (The order within a class is arbitrary; every ball's result is
@@ -173,7 +175,8 @@ adj_group_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restric
     float gx = 0.f, gy = 0.f, gz = 0.f, gR = 0.f, gp = 0.f;
     // this CTA's share of the sensors, whole groups
     const int part = (int)cluster.block_rank();
-    const int per = ((M + kAdjSplit - 1) / kAdjSplit + kAdjGroup - 1) / kAdjGroup * kAdjGroup;
+    const int split = (int)gridDim.y;  // one cluster spans all of y
+    const int per = ((M + split - 1) / split + kAdjGroup - 1) / kAdjGroup * kAdjGroup;
     const int m_begin = min(M, part * per), m_end = min(M, m_begin + per);
     for (int m0 = m_begin; m0 < m_end; m0 += kAdjGroup) {
         const int cnt = min(kAdjGroup, m_end - m0);
@@ -277,8 +280,7 @@ adj_group_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restric
     cluster.sync();
     if (part == 0 && valid) {
         float ax = gx, ay = gy, az = gz, aR = gR, ap = gp;
-#pragma unroll
-        for (int r = 1; r < kAdjSplit; ++r) {
+        for (int r = 1; r < split; ++r) {
             const float* rp = cluster.map_shared_rank(s_part, r) + li * 5;
             ax += rp[0];
             ay += rp[1];
@@ -309,6 +311,18 @@ int sbp_launch_downsample(sbp_array_s* a, int k, const float* y_full, float* y_k
     return sbp_cuda_check(cudaGetLastError(), "downsample launch") ? SBP_ERR_CUDA : SBP_OK;
 }
 
+// Downsample `rows` consecutive records of T samples (frames x sensors).
+int sbp_launch_downsample_rows(sbp_array_s* a, int k, int rows, const float* y_full,
+                               float* y_k, cudaStream_t st) {
+    const int Tk = sbp_level_T(a, k);
+    const long long total = (long long)rows * Tk;
+    const int blocks = (int)std::max<long long>(
+        1, std::min<long long>(8LL * a->sm_count, (total + 255) / 256));
+    downsample_kernel<<<blocks, 256, 0, st>>>(y_full, rows, a->T, a->factors[k], Tk, y_k);
+    sbp_count_launches(1);
+    return sbp_cuda_check(cudaGetLastError(), "downsample launch") ? SBP_ERR_CUDA : SBP_OK;
+}
+
 int sbp_launch_residual(sbp_array_s* a, const float* S, const float* y, float* G,
                         double* loss, cudaStream_t st) {
     const int Tk = sbp_level_T(a, a->level);
@@ -320,6 +334,35 @@ int sbp_launch_residual(sbp_array_s* a, const float* S, const float* y, float* G
     return sbp_cuda_check(cudaGetLastError(), "residual launch") ? SBP_ERR_CUDA : SBP_OK;
 }
 
+namespace {
+
+int launch_adj(const FrameTable& ft, int total, int split, const BallsDev& b, const float* sens,
+               const LevelGeo& g, const float* G, unsigned mask, const GradOut& o,
+               cudaStream_t st) {
+    if (split != 1 && split != 2 && split != 4 && split != 8) split = kAdjSplit;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((total + kAdjThreads - 1) / kAdjThreads, split);
+    cfg.blockDim = dim3(kAdjThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = split;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e =
+        mask == SBP_MASK_P0
+            ? cudaLaunchKernelEx(&cfg, adj_group_kernel<true>, b, ft, sens, g, G, mask, o)
+            : cudaLaunchKernelEx(&cfg, adj_group_kernel<false>, b, ft, sens, g, G, mask, o);
+    if (sbp_cuda_check(e, "adjoint: launch")) return SBP_ERR_CUDA;
+    sbp_count_launches(1);
+    return SBP_OK;
+}
+
+}  // namespace
+
 int sbp_launch_adjoint(sbp_array_s* a, const BallsDev& b, const int* n_dev, int n_cap,
                        const float* G, sbp_grads out, unsigned mask, cudaStream_t st) {
     const LevelGeo g = sbp_level_geo(a, a->level);
@@ -329,14 +372,82 @@ int sbp_launch_adjoint(sbp_array_s* a, const BallsDev& b, const int* n_dev, int 
     o.o[2] = out.gz;
     o.o[3] = out.gR;
     o.o[4] = out.gp0;
-    const dim3 grid((n_cap + kAdjThreads - 1) / kAdjThreads, kAdjSplit);
-    if (mask == SBP_MASK_P0)
-        adj_group_kernel<true><<<grid, kAdjThreads, 0, st>>>(b, n_dev, n_cap, a->d_sens, g, G,
-                                                             mask, o);
-    else
-        adj_group_kernel<false><<<grid, kAdjThreads, 0, st>>>(b, n_dev, n_cap, a->d_sens, g, G,
-                                                              mask, o);
-    if (sbp_cuda_check(cudaGetLastError(), "adjoint: launch")) return SBP_ERR_CUDA;
-    sbp_count_launches(1);
-    return SBP_OK;
+    const FrameTable ft{1, nullptr, n_dev, n_cap};
+    return launch_adj(ft, n_cap, kAdjSplit, b, a->d_sens, g, G, mask, o, st);
+}
+
+// All frames of the packed layout in one launch (sbp_adjoint_frames).
+int sbp_launch_adjoint_frames(sbp_array_s* a, const BallsDev& b, const int* n_dev,
+                              const float* G, sbp_grads out, unsigned mask, cudaStream_t st) {
+    const LevelGeo g = sbp_level_geo(a, a->level);
+    GradOut o;
+    o.o[0] = out.gx;
+    o.o[1] = out.gy;
+    o.o[2] = out.gz;
+    o.o[3] = out.gR;
+    o.o[4] = out.gp0;
+    const int total = a->h_frame_off[a->frames];
+    const FrameTable ft{a->frames, a->d_frame_off, n_dev, total};
+    return launch_adj(ft, total, a->adj_split_frames ? a->adj_split_frames : kAdjSplit, b,
+                      a->d_sens, g, G, mask, o, st);
+}
+
+namespace {
+
+// Per-frame sums of (S - y)^2: block partials, then one thread per frame adds
+// them in block order (reproducible).
+__global__ void frame_loss_partial_kernel(const float* __restrict__ S, const float* __restrict__ y,
+                                          long long per_frame, double* __restrict__ partials) {
+    __shared__ double warp_sum[32];
+    const int f = blockIdx.y;
+    const float* Sf = S + (size_t)f * per_frame;
+    const float* yf = y + (size_t)f * per_frame;
+    double acc = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < per_frame;
+         t += (long long)gridDim.x * blockDim.x) {
+        const float r = (Sf ? Sf[t] : 0.0f) - yf[t];
+        acc += (double)r * (double)r;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bsum = 0.0;
+        for (int w = 0; w < (blockDim.x + 31) / 32; ++w) bsum += warp_sum[w];
+        partials[(size_t)f * gridDim.x + blockIdx.x] = bsum;
+    }
+}
+
+__global__ void frame_loss_final_kernel(const double* __restrict__ partials, int blocks, int F,
+                                        double* __restrict__ loss) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    double L = 0.0;
+    for (int k = 0; k < blocks; ++k) L += partials[(size_t)f * blocks + k];
+    loss[f] = L;
+}
+
+}  // namespace
+
+// G = 2 (S - y) over all frames and one loss per frame (sbp_residual_frames).
+int sbp_launch_residual_frames(sbp_array_s* a, const float* S, const float* y, float* G,
+                               double* loss, cudaStream_t st) {
+    const int Tk = sbp_level_T(a, a->level);
+    const long long per = (long long)a->M * Tk;
+    const long long total = per * a->frames;
+    const int blocks = (int)std::max<long long>(
+        1, std::min<long long>(a->loss_blocks, (total + 255) / 256));
+    residual_kernel<<<blocks, 256, 0, st>>>(S, y, G, total, a->d_lossp, a->d_state, nullptr);
+    int launched = 1;
+    if (loss) {
+        const int fb = 16;
+        frame_loss_partial_kernel<<<dim3(fb, a->frames), 256, 0, st>>>(S, y, per,
+                                                                       a->d_frame_lossp);
+        frame_loss_final_kernel<<<(a->frames + 127) / 128, 128, 0, st>>>(a->d_frame_lossp, fb,
+                                                                          a->frames, loss);
+        launched += 2;
+    }
+    sbp_count_launches(launched);
+    return sbp_cuda_check(cudaGetLastError(), "residual_frames launch") ? SBP_ERR_CUDA : SBP_OK;
 }

@@ -55,6 +55,14 @@ void free_array(sbp_array_s* a) {
     cudaFree(a->d_rc_S);
     cudaFree(a->d_rc_G);
     cudaFree(a->d_rc_state);
+    cudaFree(a->d_frame_off);
+    cudaFree(a->d_frame_n_new);
+    cudaFree(a->d_frame_lossp);
+    cudaFree(a->d_frame_pmax);
+    cudaFree(a->d_fr_yk);
+    cudaFree(a->d_fr_S);
+    cudaFree(a->d_fr_G);
+    delete[] a->h_frame_off;
     delete a;
 }
 
@@ -168,6 +176,7 @@ int sbp_create_array(const float* pos_host, const float* normal_host, int M, dou
     ok = ok && !sbp_cuda_check(cudaMalloc(&a->d_sens, sizeof(float) * 6 * M), "alloc sensors");
     ok = ok && !sbp_cuda_check(cudaMalloc(&a->d_acc, sizeof(unsigned long long) * (size_t)M * T),
                                "alloc trace accumulators");
+    a->acc_cells = (size_t)M * T;
     ok = ok && !sbp_cuda_check(cudaMalloc(&a->d_lossp, sizeof(double) * a->loss_blocks),
                                "alloc loss partials");
     ok = ok && !sbp_cuda_check(cudaMalloc(&a->d_fg_counts, sizeof(int) * (a->fg_blocks + 1)),

@@ -52,15 +52,18 @@ static_assert(2LL * kChunk * (1LL << kLoBits) < (1LL << 32), "low word could ove
 constexpr int kFinalizeThreads = 1024;
 constexpr int kFracHeadroomBits = 34;  // F = 34 - ceil(log2 max|p0|)
 
-__global__ void fwd_pmax_kernel(const float* __restrict__ p0, const int* n_dev, int n_cap,
-                                SbpDevState* st) {
-    const int n = sbp_read_n(n_dev, n_cap);
+// pmax[f] = max |p0| over frame f (grid.y = frame).
+__global__ void fwd_pmax_kernel(const float* __restrict__ p0, FrameTable ft,
+                                unsigned int* __restrict__ pmax) {
+    const int f = blockIdx.y;
+    const FrameSlot fs = sbp_frame_of(ft, ft.ball_off ? ft.ball_off[f] : 0);
     float m = 0.0f;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int i = fs.off + blockIdx.x * blockDim.x + threadIdx.x; i < fs.end;
+         i += gridDim.x * blockDim.x)
         m = fmaxf(m, fabsf(p0[i]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(&st->pmax_bits, __float_as_uint(m));
+    if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(&pmax[f], __float_as_uint(m));
 }
 
 // Round a float to the nearest int64. Values below 2^31 in magnitude (nearly
@@ -91,8 +94,8 @@ __device__ __forceinline__ void fwd_add32(unsigned int* lo, int v) {
 }
 
 // Fixed-point exponent F: values are stored as round(v * 2^F).
-__device__ __forceinline__ int fwd_frac_bits(const SbpDevState* st) {
-    const float pm = __uint_as_float(st->pmax_bits);
+__device__ __forceinline__ int fwd_frac_bits(unsigned int pmax_bits) {
+    const float pm = __uint_as_float(pmax_bits);
     int e = 0;
     if (pm > 0.0f) frexpf(pm, &e);  // pm < 2^e
     int F = kFracHeadroomBits - e;
@@ -100,18 +103,20 @@ __device__ __forceinline__ int fwd_frac_bits(const SbpDevState* st) {
 }
 
 __global__ void __launch_bounds__(kGroupWarps * 32, 2)
-fwd_group_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restrict__ sens,
-                 LevelGeo g, int chunk, SbpDevState* st, unsigned long long* __restrict__ acc) {
+fwd_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, LevelGeo g,
+                 int chunk, const unsigned int* __restrict__ pmax, SbpDevState* st,
+                 unsigned long long* __restrict__ acc_all) {
     extern __shared__ unsigned int sacc[];  // [2][kWindow][32]: low words, then high words
     __shared__ float s_red[kGroupWarps * 7];
     __shared__ float s_box[7];
     __shared__ int s_jlo[32];
-    const int n = sbp_read_n(n_dev, n_cap);
     const int c0 = blockIdx.x * chunk;
-    if (c0 >= n) return;  // uniform over the block
-    const int c1 = min(n, c0 + chunk);
+    const FrameSlot fs = sbp_frame_of(ft, c0);
+    if (c0 >= fs.end) return;  // uniform over the block
+    const int c1 = min(fs.end, c0 + chunk);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int Tk = g.Tk, M = g.M;
+    unsigned long long* __restrict__ acc = acc_all + (size_t)fs.f * M * Tk;
     const int m = blockIdx.y * 32 + lane;
     const bool sv = m < M;
 
@@ -135,7 +140,7 @@ fwd_group_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restric
     const int passes = (wmax + kWindow - 1) / kWindow;  // identical in every warp
     if (warp == 0) s_jlo[lane] = jlo;
 
-    const float scale = __int_as_float((127 + fwd_frac_bits(st)) << 23);  // 2^F
+    const float scale = __int_as_float((127 + fwd_frac_bits(pmax[fs.f])) << 23);  // 2^F
     const float h = g.h_hi;
     const float d2c = -2.0f * h * h;
     unsigned int inside = 0;
@@ -257,13 +262,13 @@ fwd_group_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restric
 
 // One CTA per sensor: S = 2^-F * P(P(D)), then clear the accumulator row.
 __global__ void __launch_bounds__(kFinalizeThreads)
-fwd_finalize_kernel(unsigned long long* __restrict__ acc, int Tk, const SbpDevState* st,
-                    float* __restrict__ S) {
+fwd_finalize_kernel(unsigned long long* __restrict__ acc, int Tk,
+                    const unsigned int* __restrict__ pmax, float* __restrict__ S) {
     __shared__ long long warp_tot[32];
-    const int m = blockIdx.x;
+    const int m = blockIdx.y * gridDim.x + blockIdx.x;  // frame-major row
     unsigned long long* row = acc + (size_t)m * Tk;
     float* out = S + (size_t)m * Tk;
-    const float inv = __int_as_float((127 - fwd_frac_bits(st)) << 23);  // 2^-F
+    const float inv = __int_as_float((127 - fwd_frac_bits(pmax[blockIdx.y])) << 23);  // 2^-F
     long long carry1 = 0, carry2 = 0;
     constexpr int IPT = 4;
     const int tile = blockDim.x * IPT;
@@ -330,15 +335,53 @@ int sbp_launch_forward(sbp_array_s* a, const BallsDev& b, const int* n_dev, int 
     if (sbp_cuda_check(cudaMemsetAsync(&a->d_state->pmax_bits, 0, sizeof(unsigned int), st),
                        "forward: reset pmax"))
         return SBP_ERR_CUDA;
+    const FrameTable ft{1, nullptr, n_dev, n_cap};
     fwd_pmax_kernel<<<std::max(1, std::min(4 * a->sm_count, (n_cap + 255) / 256)), 256, 0,
-                      st>>>(b.p0, n_dev, n_cap, a->d_state);
+                      st>>>(b.p0, ft, &a->d_state->pmax_bits);
     if (sbp_cuda_check(cudaGetLastError(), "forward: pmax launch")) return SBP_ERR_CUDA;
     dim3 grid((n_cap + chunk - 1) / chunk, groups);
-    fwd_group_kernel<<<grid, kGroupWarps * 32, smem, st>>>(b, n_dev, n_cap, a->d_sens, g, chunk,
-                                                           a->d_state, a->d_acc);
+    fwd_group_kernel<<<grid, kGroupWarps * 32, smem, st>>>(
+        b, ft, a->d_sens, g, chunk, &a->d_state->pmax_bits, a->d_state, a->d_acc);
     if (sbp_cuda_check(cudaGetLastError(), "forward: accumulate launch")) return SBP_ERR_CUDA;
-    fwd_finalize_kernel<<<g.M, kFinalizeThreads, 0, st>>>(a->d_acc, g.Tk, a->d_state, S);
+    fwd_finalize_kernel<<<g.M, kFinalizeThreads, 0, st>>>(a->d_acc, g.Tk,
+                                                          &a->d_state->pmax_bits, S);
     if (sbp_cuda_check(cudaGetLastError(), "forward: finalize launch")) return SBP_ERR_CUDA;
+    sbp_count_launches(3);
+    return SBP_OK;
+}
+
+// All frames of the packed layout in one launch per kernel (sbp_forward_frames).
+int sbp_launch_forward_frames(sbp_array_s* a, const BallsDev& b, const int* n_dev, float* S,
+                              int chunk, cudaStream_t st) {
+    const LevelGeo g = sbp_level_geo(a, a->level);
+    const int F = a->frames;
+    const int total = a->h_frame_off[F];
+    const int groups = (g.M + 31) / 32;
+    if (chunk < 32 || chunk > SBP_FRAME_ALIGN || (SBP_FRAME_ALIGN % chunk)) chunk = kChunk;
+    const size_t smem = (size_t)2 * kWindow * 32 * sizeof(unsigned int);
+    if (sbp_cuda_check(cudaFuncSetAttribute(fwd_group_kernel,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem),
+                       "forward_frames: smem attribute"))
+        return SBP_ERR_CUDA;
+    // one fixed-point scale per frame, so that every frame's traces equal
+    // those of a single-cloud forward of that frame
+    if (sbp_cuda_check(cudaMemsetAsync(a->d_frame_pmax, 0, sizeof(unsigned int) * F, st),
+                       "forward_frames: reset pmax"))
+        return SBP_ERR_CUDA;
+    const FrameTable ft{F, a->d_frame_off, n_dev, total};
+    const int pmax_blocks = std::max(1, std::min(4 * a->sm_count / F, total / F / 256 + 1));
+    fwd_pmax_kernel<<<dim3(pmax_blocks, F), 256, 0, st>>>(b.p0, ft, a->d_frame_pmax);
+    if (sbp_cuda_check(cudaGetLastError(), "forward_frames: pmax launch")) return SBP_ERR_CUDA;
+    dim3 grid((total + chunk - 1) / chunk, groups);
+    fwd_group_kernel<<<grid, kGroupWarps * 32, smem, st>>>(b, ft, a->d_sens, g, chunk,
+                                                           a->d_frame_pmax, a->d_state, a->d_acc);
+    if (sbp_cuda_check(cudaGetLastError(), "forward_frames: accumulate launch"))
+        return SBP_ERR_CUDA;
+    fwd_finalize_kernel<<<dim3(g.M, F), kFinalizeThreads, 0, st>>>(a->d_acc, g.Tk,
+                                                                   a->d_frame_pmax, S);
+    if (sbp_cuda_check(cudaGetLastError(), "forward_frames: finalize launch"))
+        return SBP_ERR_CUDA;
     sbp_count_launches(3);
     return SBP_OK;
 }
@@ -452,15 +495,16 @@ extern "C" int sbp_forward_static(const float* sensors_dev, int M, double c_mm_p
                                             (int)smem),
                        "forward_static: smem attribute"))
         return SBP_ERR_CUDA;
+    const FrameTable ft{1, nullptr, n_dev, n_cap};
     fwd_pmax_kernel<<<std::max(1, std::min(4 * sms, (n_cap + 255) / 256)), 256, 0, st>>>(
-        b.p0, n_dev, n_cap, state);
+        b.p0, ft, &state->pmax_bits);
     if (sbp_cuda_check(cudaGetLastError(), "forward_static: pmax launch")) return SBP_ERR_CUDA;
     dim3 grid((n_cap + chunk - 1) / chunk, groups);
-    fwd_group_kernel<<<grid, kGroupWarps * 32, smem, st>>>(b, n_dev, n_cap, sensors_dev, g, chunk,
-                                                           state, acc);
+    fwd_group_kernel<<<grid, kGroupWarps * 32, smem, st>>>(b, ft, sensors_dev, g, chunk,
+                                                           &state->pmax_bits, state, acc);
     if (sbp_cuda_check(cudaGetLastError(), "forward_static: accumulate launch"))
         return SBP_ERR_CUDA;
-    fwd_finalize_kernel<<<M, kFinalizeThreads, 0, st>>>(acc, T_k, state, S_dev);
+    fwd_finalize_kernel<<<M, kFinalizeThreads, 0, st>>>(acc, T_k, &state->pmax_bits, S_dev);
     if (sbp_cuda_check(cudaGetLastError(), "forward_static: finalize launch")) return SBP_ERR_CUDA;
     sbp_count_launches(3);
     return SBP_OK;

@@ -52,8 +52,10 @@ __device__ __forceinline__ float3 split_dir(uint64_t seed, int i) {
     return make_float3(g[0] * inv, g[1] * inv, g[2] * inv);
 }
 
-// 0 = drop, 1 = keep, 2 = split into two, 3 = keep and duplicate.
-__device__ __forceinline__ int fg_action(const FgArrays& A, const FgRule& r, int i) {
+// 0 = drop, 1 = keep, 2 = split into two, 3 = keep and duplicate. `local`
+// is the ball's index within its frame (the rules do not depend on it).
+__device__ __forceinline__ int fg_action(const FgArrays& A, const FgRule& r, int i, int local) {
+    (void)local;
     if (r.mode != SBP_GROW) {
         const float g = A.a[9][i];
         if (r.mode == SBP_KEEP_NEG) return g < 0.0f ? 1 : 0;
@@ -119,56 +121,65 @@ __device__ __forceinline__ int fg_block_excl_scan(int v, int* warp_tot, int& tot
     return x - v + off;
 }
 
+// Every block of kFgThreads balls lies inside one frame (frame capacities are
+// multiples of SBP_FRAME_ALIGN). Counts and offsets are per frame; n_new[f]
+// receives frame f's new count, or -1 when it would exceed its capacity.
 __global__ void __launch_bounds__(kFgThreads)
-fg_count_kernel(FgArrays A, FgRule r, const int* n_dev, int n_cap, int* block_tot) {
+fg_count_kernel(FgArrays A, FgRule r, FrameTable ft, int* block_tot) {
     __shared__ int warp_tot[32];
-    const int n = sbp_read_n(n_dev, n_cap);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = i < n ? fg_out_count(fg_action(A, r, i)) : 0;
+    const FrameSlot fs = sbp_frame_of(ft, blockIdx.x * blockDim.x);
+    const int c = i < fs.end ? fg_out_count(fg_action(A, r, i, i - fs.off)) : 0;
     int tot;
     fg_block_excl_scan(c, warp_tot, tot);
     if (threadIdx.x == 0) block_tot[blockIdx.x] = tot;
 }
 
-__global__ void fg_scan_kernel(int* block_tot, int nblocks, int n_cap, SbpDevState* st) {
+// One CTA per frame: exclusive scan of the frame's block totals.
+__global__ void fg_scan_kernel(int* block_tot, FrameTable ft, int* n_new, SbpDevState* st) {
     __shared__ int warp_tot[32];
+    const int f = blockIdx.x;
+    const int off = ft.ball_off ? ft.ball_off[f] : 0;
+    const int cap = ft.ball_off ? ft.ball_off[f + 1] - off : ft.n_cap;
+    const int b0 = off / kFgThreads, nblocks = (cap + kFgThreads - 1) / kFgThreads;
     int carry = 0;
     for (int base = 0; base < nblocks; base += blockDim.x) {
         const int b = base + threadIdx.x;
-        const int v = b < nblocks ? block_tot[b] : 0;
+        const int v = b < nblocks ? block_tot[b0 + b] : 0;
         int tot;
         const int ex = fg_block_excl_scan(v, warp_tot, tot);
-        if (b < nblocks) block_tot[b] = ex + carry;
+        if (b < nblocks) block_tot[b0 + b] = ex + carry;
         carry += tot;
     }
     if (threadIdx.x == 0) {
-        if (carry > n_cap) {
-            st->n_new = -1;
+        if (carry > cap) {
+            n_new[f] = -1;
             sbp_latch(st, SBP_ERR_CAPACITY);
         } else {
-            st->n_new = carry;
+            n_new[f] = carry;
         }
     }
 }
 
 __global__ void __launch_bounds__(kFgThreads)
-fg_scatter_kernel(FgArrays A, FgRule r, const int* n_dev, int n_cap, const int* block_off,
-                  const SbpDevState* st, float* __restrict__ buf) {
+fg_scatter_kernel(FgArrays A, FgRule r, FrameTable ft, const int* block_off, const int* n_new,
+                  int total_cap, float* __restrict__ buf) {
     __shared__ int warp_tot[32];
-    if (st->n_new < 0) return;  // uniform: capacity exceeded, leave everything as is
-    const int n = sbp_read_n(n_dev, n_cap);
+    const FrameSlot fs = sbp_frame_of(ft, blockIdx.x * blockDim.x);
+    if (n_new[fs.f] < 0) return;  // uniform: capacity exceeded, leave the frame as is
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int act = i < n ? fg_action(A, r, i) : 0;
+    const int act = i < fs.end ? fg_action(A, r, i, i - fs.off) : 0;
     int tot;
-    const int pos = block_off[blockIdx.x] + fg_block_excl_scan(fg_out_count(act), warp_tot, tot);
+    const int pos =
+        fs.off + block_off[blockIdx.x] + fg_block_excl_scan(fg_out_count(act), warp_tot, tot);
     if (act == 0) return;
-    const size_t cap = (size_t)n_cap;
+    const size_t cap = (size_t)total_cap;
     if (act == 1 || act == 3) {
         for (int k = 0; k < A.count; ++k) buf[k * cap + pos] = A.a[k][i];
     }
     if (act == 2 || act == 3) {
         const float x = A.a[0][i], y = A.a[1][i], z = A.a[2][i], R = A.a[3][i], p0 = A.a[4][i];
-        const float3 v = split_dir(r.gp.seed, i);
+        const float3 v = split_dir(r.gp.seed, i - fs.off);  // index within the frame
         const float hr = 0.5f * R;
         if (act == 2) {
             const float Rc = R * 0.793700525984099737f;  // 2^(-1/3)
@@ -197,14 +208,17 @@ fg_scatter_kernel(FgArrays A, FgRule r, const int* n_dev, int n_cap, const int* 
     }
 }
 
-__global__ void fg_copy_kernel(FgArrays A, int n_cap, const float* __restrict__ buf,
-                               const SbpDevState* st, int* n_dev) {
-    const int n_new = st->n_new;
-    if (n_new < 0) return;
-    const size_t cap = (size_t)n_cap;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_new; i += gridDim.x * blockDim.x)
-        for (int k = 0; k < A.count; ++k) A.a[k][i] = buf[k * cap + i];
-    if (blockIdx.x == 0 && threadIdx.x == 0) *n_dev = n_new;
+// grid.y = frame: copies the frame's outputs back and publishes its count.
+__global__ void fg_copy_kernel(FgArrays A, FrameTable ft, int total_cap,
+                               const float* __restrict__ buf, const int* n_new, int* n_dev) {
+    const int f = blockIdx.y;
+    const int nn = n_new[f];
+    if (nn < 0) return;
+    const int off = ft.ball_off ? ft.ball_off[f] : 0;
+    const size_t cap = (size_t)total_cap;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x)
+        for (int k = 0; k < A.count; ++k) A.a[k][off + i] = buf[k * cap + off + i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) n_dev[f] = nn;
 }
 
 struct AdamArgs {
@@ -217,9 +231,11 @@ struct AdamArgs {
     unsigned mask;
 };
 
-__global__ void adam_kernel(AdamArgs a, const int* n_dev, int n_cap) {
-    const int n = sbp_read_n(n_dev, n_cap);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+// grid.y = frame
+__global__ void adam_kernel(AdamArgs a, FrameTable ft) {
+    const FrameSlot fs = sbp_frame_of(ft, ft.ball_off ? ft.ball_off[blockIdx.y] : 0);
+    for (int i = fs.off + blockIdx.x * blockDim.x + threadIdx.x; i < fs.end;
+         i += gridDim.x * blockDim.x) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             const unsigned bit = k < 3 ? SBP_MASK_XYZ : (k == 3 ? SBP_MASK_R : SBP_MASK_P0);
@@ -248,9 +264,11 @@ __global__ void adam_kernel(AdamArgs a, const int* n_dev, int n_cap) {
 
 }  // namespace
 
-int sbp_launch_filter_grow(sbp_array_s* a, sbp_balls balls, sbp_grads grads,
-                           float* const* extra, int n_extra, int* n_dev, int n_cap,
-                           const sbp_grow_params* gp, int mode, cudaStream_t st) {
+namespace {
+
+int launch_filter_grow(sbp_array_s* a, sbp_balls balls, sbp_grads grads, float* const* extra,
+                       int n_extra, const FrameTable& ft, int total_cap, int* n_dev, int* n_new,
+                       const sbp_grow_params* gp, int mode, cudaStream_t st) {
     FgArrays A;
     A.a[0] = balls.x;
     A.a[1] = balls.y;
@@ -268,24 +286,27 @@ int sbp_launch_filter_grow(sbp_array_s* a, sbp_balls balls, sbp_grads grads,
     r.mode = mode;
     if (gp) r.gp = *gp;
     else memset(&r.gp, 0, sizeof(r.gp));
-    const int blocks = (n_cap + kFgThreads - 1) / kFgThreads;
+    const int blocks = (total_cap + kFgThreads - 1) / kFgThreads;
     if (blocks > a->fg_blocks) {
-        sbp_set_error("filter_grow: n_cap exceeds the array's capacity");
+        sbp_set_error("filter_grow: capacity exceeds the array's capacity");
         return SBP_ERR_ARG;
     }
-    fg_count_kernel<<<blocks, kFgThreads, 0, st>>>(A, r, n_dev, n_cap, a->d_fg_counts);
-    fg_scan_kernel<<<1, 1024, 0, st>>>(a->d_fg_counts, blocks, n_cap, a->d_state);
-    fg_scatter_kernel<<<blocks, kFgThreads, 0, st>>>(A, r, n_dev, n_cap, a->d_fg_counts,
-                                                     a->d_state, a->d_fg_buf);
-    const int cblocks = std::max(1, std::min(4 * a->sm_count, blocks));
-    fg_copy_kernel<<<cblocks, 256, 0, st>>>(A, n_cap, a->d_fg_buf, a->d_state, n_dev);
+    fg_count_kernel<<<blocks, kFgThreads, 0, st>>>(A, r, ft, a->d_fg_counts);
+    fg_scan_kernel<<<ft.F, 1024, 0, st>>>(a->d_fg_counts, ft, n_new, a->d_state);
+    fg_scatter_kernel<<<blocks, kFgThreads, 0, st>>>(A, r, ft, a->d_fg_counts, n_new, total_cap,
+                                                     a->d_fg_buf);
+    const int per_frame = std::max(1, total_cap / ft.F);
+    const int cblocks =
+        std::max(1, std::min(std::max(1, 4 * a->sm_count / ft.F), (per_frame + 255) / 256));
+    fg_copy_kernel<<<dim3(cblocks, ft.F), 256, 0, st>>>(A, ft, total_cap, a->d_fg_buf, n_new,
+                                                        n_dev);
     sbp_count_launches(4);
     return sbp_cuda_check(cudaGetLastError(), "filter_grow launch") ? SBP_ERR_CUDA : SBP_OK;
 }
 
-int sbp_launch_adam(sbp_array_s* a, sbp_balls balls, sbp_grads grads, sbp_balls m,
-                    sbp_balls v, const int* n_dev, int n_cap, int t,
-                    const sbp_adam_params* ap, unsigned mask, cudaStream_t st) {
+int launch_adam(sbp_array_s* a, sbp_balls balls, sbp_grads grads, sbp_balls m, sbp_balls v,
+                const FrameTable& ft, int per_frame_cap, int t, const sbp_adam_params* ap,
+                unsigned mask, cudaStream_t st) {
     AdamArgs x;
     float* P[5] = {balls.x, balls.y, balls.z, balls.R, balls.p0};
     const float* Gr[5] = {grads.gx, grads.gy, grads.gz, grads.gR, grads.gp0};
@@ -304,8 +325,43 @@ int sbp_launch_adam(sbp_array_s* a, sbp_balls balls, sbp_grads grads, sbp_balls 
     x.c1 = (float)(1.0 - pow((double)ap->beta1, (double)t));
     x.c2 = (float)(1.0 - pow((double)ap->beta2, (double)t));
     x.mask = mask;
-    const int blocks = std::max(1, std::min(4 * a->sm_count, (n_cap + 255) / 256));
-    adam_kernel<<<blocks, 256, 0, st>>>(x, n_dev, n_cap);
+    const int blocks =
+        std::max(1, std::min(std::max(1, 4 * a->sm_count / ft.F), (per_frame_cap + 255) / 256));
+    adam_kernel<<<dim3(blocks, ft.F), 256, 0, st>>>(x, ft);
     sbp_count_launches(1);
     return sbp_cuda_check(cudaGetLastError(), "adam launch") ? SBP_ERR_CUDA : SBP_OK;
+}
+
+}  // namespace
+
+int sbp_launch_filter_grow(sbp_array_s* a, sbp_balls balls, sbp_grads grads,
+                           float* const* extra, int n_extra, int* n_dev, int n_cap,
+                           const sbp_grow_params* gp, int mode, cudaStream_t st) {
+    const FrameTable ft{1, nullptr, n_dev, n_cap};
+    return launch_filter_grow(a, balls, grads, extra, n_extra, ft, n_cap, n_dev,
+                              &a->d_state->n_new, gp, mode, st);
+}
+
+int sbp_launch_filter_grow_frames(sbp_array_s* a, sbp_balls balls, sbp_grads grads,
+                                  float* const* extra, int n_extra, int* n_dev,
+                                  const sbp_grow_params* gp, int mode, cudaStream_t st) {
+    const int total = a->h_frame_off[a->frames];
+    const FrameTable ft{a->frames, a->d_frame_off, n_dev, total};
+    return launch_filter_grow(a, balls, grads, extra, n_extra, ft, total, n_dev,
+                              a->d_frame_n_new, gp, mode, st);
+}
+
+int sbp_launch_adam(sbp_array_s* a, sbp_balls balls, sbp_grads grads, sbp_balls m,
+                    sbp_balls v, const int* n_dev, int n_cap, int t,
+                    const sbp_adam_params* ap, unsigned mask, cudaStream_t st) {
+    const FrameTable ft{1, nullptr, n_dev, n_cap};
+    return launch_adam(a, balls, grads, m, v, ft, n_cap, t, ap, mask, st);
+}
+
+int sbp_launch_adam_frames(sbp_array_s* a, sbp_balls balls, sbp_grads grads, sbp_balls m,
+                           sbp_balls v, const int* n_dev, int t, const sbp_adam_params* ap,
+                           unsigned mask, cudaStream_t st) {
+    const int total = a->h_frame_off[a->frames];
+    const FrameTable ft{a->frames, a->d_frame_off, n_dev, total};
+    return launch_adam(a, balls, grads, m, v, ft, total / a->frames, t, ap, mask, st);
 }

@@ -42,6 +42,52 @@ struct BallsDev {
     const float* __restrict__ p0;
 };
 
+// Multi-frame layout. Frame f owns balls [ball_off[f], ball_off[f+1]) of the
+// packed arrays (every frame's capacity is a multiple of kFrameAlign, so a
+// chunk of up to kFrameAlign balls never straddles two frames) and traces
+// [f*M*T_k, (f+1)*M*T_k); its live count is n_dev[f]. A single cloud is
+// F = 1 with ball_off = null, capacity n_cap and count n_dev (may be null).
+#define SBP_FRAME_ALIGN 1024
+#define SBP_MAX_FRAMES 1024
+
+struct FrameTable {
+    int F;
+    const int* __restrict__ ball_off;  // device, F + 1 entries, or null when F == 1
+    const int* n_dev;                  // device, F entries (null: n = capacity)
+    int n_cap;                         // capacity of the single cloud when ball_off is null
+};
+
+struct FrameSlot {
+    int f;    // frame
+    int off;  // first ball of the frame in the packed arrays
+    int end;  // one past the frame's last live ball
+};
+
+// Frame of packed ball index `ball` (binary search over the frame offsets).
+__device__ __forceinline__ FrameSlot sbp_frame_of(const FrameTable& ft, int ball) {
+    FrameSlot s;
+    if (ft.ball_off == nullptr) {
+        s.f = 0;
+        s.off = 0;
+        int n = ft.n_dev ? *ft.n_dev : ft.n_cap;
+        s.end = n < 0 ? 0 : (n > ft.n_cap ? ft.n_cap : n);
+        return s;
+    }
+    int lo = 0, hi = ft.F;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (ft.ball_off[mid] <= ball) lo = mid;
+        else hi = mid;
+    }
+    s.f = lo;
+    s.off = ft.ball_off[lo];
+    const int cap = ft.ball_off[lo + 1] - s.off;
+    int n = ft.n_dev ? ft.n_dev[lo] : cap;
+    n = n < 0 ? 0 : (n > cap ? cap : n);
+    s.end = s.off + n;
+    return s;
+}
+
 struct sbp_array_s {
     int device;
     int sm_count;
@@ -51,8 +97,16 @@ struct sbp_array_s {
     int wmode;
     // sensors on the device, structure of arrays [6][M]: sx, sy, sz, nx, ny, nz
     float* d_sens;
-    // forward: fixed-point second-difference accumulators [M][T_k] (int64)
+    // forward: fixed-point second-difference accumulators [frames][M][T_k] (int64)
     unsigned long long* d_acc;
+    size_t acc_cells;
+    // multi-frame layout (sbp_set_frames)
+    int frames;
+    int* d_frame_off;      // [frames + 1]
+    int* h_frame_off;      // host copy
+    int* d_frame_n_new;    // [frames] result counts of a frame-wise filter/grow
+    unsigned int* d_frame_pmax;  // [frames] bits of max |p0| per frame (forward scale)
+    double* d_frame_lossp; // [frames][loss blocks]
     // residual loss partials
     double* d_lossp;
     int loss_blocks;
@@ -66,6 +120,13 @@ struct sbp_array_s {
     float* d_rc_S;      // [M][T]
     float* d_rc_G;      // [M][T]
     float* d_rc_state;  // [15][n_cap]: grads (5), Adam m (5), Adam v (5)
+    // multi-frame reconstruction scratch ([frames][M][T] each)
+    float* d_fr_yk;
+    float* d_fr_S;
+    float* d_fr_G;
+    size_t fr_cells;
+    int fwd_chunk_frames;  // forward balls per CTA chosen by sbp_autotune_frames (0: default)
+    int adj_split_frames;  // adjoint CTAs per cluster chosen by sbp_autotune_frames (0: default)
 };
 
 // ----------------------------------------------------------------------------
@@ -94,6 +155,21 @@ int sbp_launch_filter_grow(sbp_array_s* a, sbp_balls balls, sbp_grads grads,
 int sbp_launch_adam(sbp_array_s* a, sbp_balls balls, sbp_grads grads, sbp_balls m,
                     sbp_balls v, const int* n_dev, int n_cap, int t,
                     const sbp_adam_params* ap, unsigned mask, cudaStream_t st);
+// the same over every frame of the packed layout of sbp_set_frames
+int sbp_launch_forward_frames(sbp_array_s* a, const BallsDev& b, const int* n_dev, float* S,
+                              int chunk, cudaStream_t st);
+int sbp_launch_residual_frames(sbp_array_s* a, const float* S, const float* y, float* G,
+                               double* loss, cudaStream_t st);
+int sbp_launch_adjoint_frames(sbp_array_s* a, const BallsDev& b, const int* n_dev,
+                              const float* G, sbp_grads out, unsigned mask, cudaStream_t st);
+int sbp_launch_filter_grow_frames(sbp_array_s* a, sbp_balls balls, sbp_grads grads,
+                                  float* const* extra, int n_extra, int* n_dev,
+                                  const sbp_grow_params* gp, int mode, cudaStream_t st);
+int sbp_launch_adam_frames(sbp_array_s* a, sbp_balls balls, sbp_grads grads, sbp_balls m,
+                           sbp_balls v, const int* n_dev, int t, const sbp_adam_params* ap,
+                           unsigned mask, cudaStream_t st);
+int sbp_launch_downsample_rows(sbp_array_s* a, int k, int rows, const float* y_full,
+                               float* y_k, cudaStream_t st);
 
 // ----------------------------------------------------------------------------
 // device helpers

@@ -98,6 +98,20 @@ _SIGS = {
     "sbp_reconstruct": (ctypes.c_int, [_P, _P, _Balls, _P, ctypes.c_int,
                                        ctypes.POINTER(_ReconParams), _P]),
     "sbp_launch_count": (ctypes.c_longlong, []),
+    "sbp_set_frames": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
+    "sbp_set_sampling_level_frames": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
+    "sbp_forward_frames": (ctypes.c_int, [_P, _Balls, _P, _P, _P]),
+    "sbp_residual_frames": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "sbp_adjoint_frames": (ctypes.c_int, [_P, _Balls, _P, _P, _Balls, ctypes.c_uint, _P]),
+    "sbp_filter_grow_frames": (ctypes.c_int, [_P, _Balls, _Balls, ctypes.POINTER(_P),
+                                              ctypes.c_int, _P, ctypes.POINTER(_GrowParams),
+                                              ctypes.c_int, _P]),
+    "sbp_adam_step_frames": (ctypes.c_int, [_P, _Balls, _Balls, _Balls, _Balls, _P, ctypes.c_int,
+                                            ctypes.POINTER(_AdamParams), ctypes.c_uint, _P]),
+    "sbp_reconstruct_frames": (ctypes.c_int, [_P, _P, _Balls, _P, ctypes.POINTER(_ReconParams),
+                                              _P]),
+    "sbp_autotune_frames": (ctypes.c_int, [_P, _Balls, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]),
     "sbp_probe_fp32_fma": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "sbp_probe_issue": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "sbp_probe_smem_atomic": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -387,6 +401,122 @@ class SensorArray:
             self.level = stages[-1].level
         elif zero_grad_mode is not None and zero_grad_mode >= 0:
             self.level = zero_grad_level
+
+    # ------------------------------------------------------------ batched frames
+    def set_frames(self, capacities) -> np.ndarray:
+        """Frame layout (sbp_set_frames): returns the F + 1 padded offsets of
+        the frames in the packed cloud."""
+        caps = np.ascontiguousarray(np.asarray(capacities, dtype=np.int32))
+        off = np.zeros(caps.size + 1, dtype=np.int32)
+        _check("sbp_set_frames", self._lib.sbp_set_frames(self._h, caps.ctypes.data, caps.size,
+                                                          off.ctypes.data))
+        self.frames = int(caps.size)
+        self.frame_off = off
+        return off
+
+    def _check_frame_traces(self, t, T):
+        shape = (self.frames, self.M, T)
+        if t.dtype != torch.float32 or not t.is_cuda or tuple(t.shape) != shape \
+                or not t.is_contiguous():
+            raise ValueError(f"expected a contiguous {shape} float32 CUDA tensor")
+
+    def set_sampling_level_frames(self, k: int, y_full=None, out=None):
+        Tk = self.level_info(k)[0]
+        if y_full is not None:
+            self._check_frame_traces(y_full, self.T)
+            if out is None:
+                out = torch.empty((self.frames, self.M, Tk), dtype=torch.float32,
+                                  device=self.device)
+            self._check_frame_traces(out, Tk)
+        _check("sbp_set_sampling_level_frames", self._lib.sbp_set_sampling_level_frames(
+            self._h, k, _dptr(y_full), _dptr(out if y_full is not None else None), _stream()))
+        self.level = k
+        return out
+
+    def forward_frames(self, balls, n_dev, out=None):
+        Tk = self.Tk
+        if out is None:
+            out = torch.empty((self.frames, self.M, Tk), dtype=torch.float32, device=self.device)
+        self._check_frame_traces(out, Tk)
+        _check("sbp_forward_frames", self._lib.sbp_forward_frames(
+            self._h, _rows(balls), _dptr(n_dev), _dptr(out), _stream()))
+        return out
+
+    def residual_frames(self, S, y_k, G=None, loss=None):
+        Tk = self.Tk
+        self._check_frame_traces(y_k, Tk)
+        if G is None:
+            G = torch.empty_like(y_k)
+        _check("sbp_residual_frames", self._lib.sbp_residual_frames(
+            self._h, _dptr(S), _dptr(y_k), _dptr(G), _dptr(loss), _stream()))
+        return G
+
+    def adjoint_frames(self, balls, n_dev, G, mask: int = MASK_ALL, out=None):
+        self._check_frame_traces(G, self.Tk)
+        if out is None:
+            out = torch.empty_like(balls)
+        _check("sbp_adjoint_frames", self._lib.sbp_adjoint_frames(
+            self._h, _rows(balls), _dptr(n_dev), _dptr(G), _rows(out), mask, _stream()))
+        return out
+
+    def filter_grow_frames(self, balls, grads, n_dev, mode: int = KEEP_NEG,
+                           grow: GrowParams | None = None, extra=()):
+        ex = []
+        for t in extra:
+            ex.extend(t[k] for k in range(t.shape[0])) if t.dim() == 2 else ex.append(t)
+        arr = (_P * max(1, len(ex)))(*[t.data_ptr() for t in ex])
+        gp = grow.c() if grow is not None else None
+        _check("sbp_filter_grow_frames", self._lib.sbp_filter_grow_frames(
+            self._h, _rows(balls), _rows(grads), arr, len(ex), _dptr(n_dev),
+            ctypes.byref(gp) if gp is not None else None, mode, _stream()))
+
+    def adam_step_frames(self, balls, grads, m, v, n_dev, t: int, ap: AdamParams,
+                         mask: int = MASK_ALL):
+        p = ap.c()
+        _check("sbp_adam_step_frames", self._lib.sbp_adam_step_frames(
+            self._h, _rows(balls), _rows(grads), _rows(m), _rows(v), _dptr(n_dev), int(t),
+            ctypes.byref(p), mask, _stream()))
+
+    def reconstruct_frames(self, y_full, balls, n_dev, stages, zero_grad_mode: int = KEEP_NEG,
+                           zero_grad_level: int = 0, adam: AdamParams | None = None,
+                           grow: GrowParams | None = None, loss_log=None, n_log=None):
+        """sbp_reconstruct_frames: all frames in lockstep; logs hold F entries
+        per iteration."""
+        self._check_frame_traces(y_full, self.T)
+        rp = _ReconParams()
+        rp.zero_grad_mode = -1 if zero_grad_mode is None else int(zero_grad_mode)
+        rp.zero_grad_level = int(zero_grad_level)
+        rp.n_stages = len(stages)
+        for i, st in enumerate(stages):
+            rp.stages[i] = _Stage(st.level, st.iterations, st.grad_mask, int(st.grow),
+                                  int(st.duplicate))
+        rp.adam = (adam or AdamParams()).c()
+        rp.grow = (grow or GrowParams()).c()
+        cap = 10 ** 9
+        if loss_log is not None:
+            rp.loss_log_dev = loss_log.data_ptr()
+            cap = min(cap, loss_log.numel() // self.frames)
+        if n_log is not None:
+            rp.n_log_dev = n_log.data_ptr()
+            cap = min(cap, n_log.numel() // self.frames)
+        rp.log_capacity = cap if (loss_log is not None or n_log is not None) else 0
+        _check("sbp_reconstruct_frames", self._lib.sbp_reconstruct_frames(
+            self._h, _dptr(y_full), _rows(balls), _dptr(n_dev), ctypes.byref(rp), _stream()))
+        if stages:
+            self.level = stages[-1].level
+
+    def autotune_frames(self, balls, n_dev):
+        """Tile autotuner of the batched path (sbp_autotune_frames); returns
+        (forward balls per CTA, adjoint CTAs per cluster)."""
+        Tk = self.Tk
+        S = torch.empty((self.frames, self.M, Tk), dtype=torch.float32, device=self.device)
+        G = torch.randn((self.frames, self.M, Tk), dtype=torch.float32, device=self.device)
+        c, sp = ctypes.c_int(), ctypes.c_int()
+        torch.cuda.synchronize()
+        _check("sbp_autotune_frames", self._lib.sbp_autotune_frames(
+            self._h, _rows(balls), _dptr(n_dev), _dptr(S), _dptr(G), ctypes.byref(c),
+            ctypes.byref(sp)))
+        return c.value, sp.value
 
     def sync_status(self) -> int:
         return int(self._lib.sbp_sync_status(self._h, _stream()))

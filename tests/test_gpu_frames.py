@@ -1,0 +1,152 @@
+"""Batched frames: every batched step equals the single-cloud step applied to
+each frame, and a frame's traces match the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sb():
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_2601_00551_gb300 import slingbag
+
+    torch.cuda.set_device(0)
+    return slingbag
+
+
+COUNTS = (1500, 300, 2000, 900)
+
+
+def frame_clouds():
+    return [workloads.uniform_balls(n, 2.0, 0.05, 0.35, 0.0, 1.0, seed=50 + f).stack()
+            for f, n in enumerate(COUNTS)]
+
+
+def setup(sb, levels=(2, 1)):
+    wl = workloads.tiny()
+    F = len(COUNTS)
+    caps = [c + 700 for c in COUNTS]  # room to grow
+    total = sum((c + 1023) // 1024 * 1024 for c in caps)
+    arr = sb.SensorArray(wl.sensors.pos, wl.sensors.normal, wl.c, wl.fs_mhz, wl.T, levels,
+                         n_cap=total)
+    off = arr.set_frames(caps)
+    packed = torch.zeros((5, total), device="cuda")
+    clouds = frame_clouds()
+    for f, b in enumerate(clouds):
+        packed[:, off[f]:off[f] + b.shape[1]] = torch.from_numpy(b)
+    n_dev = torch.tensor(COUNTS, dtype=torch.int32, device="cuda")
+    # a frame holds its padded capacity, so the single-cloud calls get the same
+    single = sb.SensorArray(wl.sensors.pos, wl.sensors.normal, wl.c, wl.fs_mhz, wl.T, levels,
+                            n_cap=max(off[f + 1] - off[f] for f in range(F)))
+    return wl, arr, single, off, packed, n_dev, clouds
+
+
+def test_forward_and_adjoint_frames_equal_single_cloud(sb):
+    wl, arr, single, off, packed, n_dev, clouds = setup(sb)
+    rng = np.random.default_rng(0)
+    for k in range(2):
+        arr.set_sampling_level(k)
+        single.set_sampling_level(k)
+        Tk = arr.Tk
+        S = arr.forward_frames(packed, n_dev)
+        G = torch.from_numpy(rng.normal(size=(len(COUNTS), wl.sensors.M, Tk))
+                             .astype(np.float32)).cuda()
+        g = arr.adjoint_frames(packed, n_dev, G)
+        for f, b in enumerate(clouds):
+            bf = torch.from_numpy(b).cuda()
+            Sf = single.forward(bf)
+            assert torch.equal(S[f], Sf)
+            gf = single.adjoint(bf, G[f].contiguous())
+            n = b.shape[1]
+            assert torch.equal(g[:, off[f]:off[f] + n], gf[:, :n])
+        # one frame against the oracle
+        ref = oracle.forward(clouds[2], wl.sensors.pos, wl.sensors.normal, wl.c,
+                             (2, 1)[k] / wl.fs_mhz, Tk)
+        got = S[2].cpu().numpy()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
+
+
+def test_filter_grow_and_adam_frames_equal_single_cloud(sb):
+    wl, arr, single, off, packed, n_dev, clouds = setup(sb)
+    rng = np.random.default_rng(1)
+    total = packed.shape[1]
+    grads = torch.from_numpy(rng.normal(size=(5, total)).astype(np.float32)).cuda()
+    grads[:, ::7] = 0.0
+    mom = torch.from_numpy(rng.normal(size=(10, total)).astype(np.float32)).cuda().abs()
+    ap = sb.AdamParams()
+    gp = sb.GrowParams(seed=9, R_max=0.3, duplicate=True, g_dup=1.5)
+    # single-cloud reference, frame by frame
+    ref = []
+    for f, b in enumerate(clouds):
+        n = b.shape[1]
+        cap = off[f + 1] - off[f]
+        B = torch.zeros((5, cap), device="cuda")
+        Gd = torch.zeros((5, cap), device="cuda")
+        Mm = torch.zeros((10, cap), device="cuda")
+        B[:, :n] = packed[:, off[f]:off[f] + n]
+        Gd[:, :n] = grads[:, off[f]:off[f] + n]
+        Mm[:, :n] = mom[:, off[f]:off[f] + n]
+        nd = torch.tensor([n], dtype=torch.int32, device="cuda")
+        single.adam_step(B, Gd, Mm[:5], Mm[5:], 3, ap, n=nd, mask=7)
+        single.filter_grow(B, Gd, nd, mode=sb.GROW, grow=gp, extra=[Mm])
+        assert single.sync_status() == 0
+        m = int(nd.item())
+        ref.append((m, B[:, :m].clone(), Gd[:, :m].clone(), Mm[:, :m].clone()))
+    arr.adam_step_frames(packed, grads, mom[:5], mom[5:], n_dev, 3, ap, mask=7)
+    arr.filter_grow_frames(packed, grads, n_dev, mode=sb.GROW, grow=gp, extra=[mom])
+    assert arr.sync_status() == 0
+    counts = n_dev.cpu().numpy()
+    for f, (m, B, Gd, Mm) in enumerate(ref):
+        assert counts[f] == m
+        assert torch.equal(packed[:, off[f]:off[f] + m], B)
+        assert torch.equal(grads[:, off[f]:off[f] + m], Gd)
+        assert torch.equal(mom[:, off[f]:off[f] + m], Mm)
+
+
+def test_reconstruct_frames_equals_per_frame_reconstruct(sb):
+    wl, arr, single, off, packed, n_dev, clouds = setup(sb)
+    F = len(COUNTS)
+    y_frames = []
+    for f in range(F):
+        truth = workloads.uniform_balls(200, 2.0, 0.05, 0.2, 0.5, 1.0, seed=70 + f).stack()
+        y = oracle.forward(truth, wl.sensors.pos, wl.sensors.normal, wl.c, 1 / wl.fs_mhz, wl.T)
+        y_frames.append(workloads.add_noise(y.astype(np.float32), seed=80 + f))
+    Y = torch.from_numpy(np.stack(y_frames)).cuda()
+    stages = [sb.Stage(0, 2, 3, True, False), sb.Stage(1, 3, 7, True, True)]
+    gp = sb.GrowParams(seed=3, R_max=0.3, g_dup=2.0)
+    loss = torch.zeros(5 * F, dtype=torch.float64, device="cuda")
+    nlog = torch.zeros(5 * F, dtype=torch.int32, device="cuda")
+    arr.reconstruct_frames(Y, packed, n_dev, stages, grow=gp, loss_log=loss, n_log=nlog)
+    assert arr.sync_status() == 0
+    loss = loss.cpu().numpy().reshape(5, F)
+    nlog = nlog.cpu().numpy().reshape(5, F)
+    for f, b in enumerate(clouds):
+        cap = off[f + 1] - off[f]
+        B = torch.zeros((5, cap), device="cuda")
+        B[:, :b.shape[1]] = torch.from_numpy(b)
+        nd = torch.tensor([b.shape[1]], dtype=torch.int32, device="cuda")
+        lf = torch.zeros(5, dtype=torch.float64, device="cuda")
+        nf = torch.zeros(5, dtype=torch.int32, device="cuda")
+        single.reconstruct(Y[f].contiguous(), B, nd, stages, grow=gp, loss_log=lf, n_log=nf)
+        assert single.sync_status() == 0
+        np.testing.assert_array_equal(nlog[:, f], nf.cpu().numpy())
+        np.testing.assert_allclose(loss[:, f], lf.cpu().numpy(), rtol=1e-12)
+        m = int(nd.item())
+        assert int(n_dev[f].item()) == m
+        assert torch.equal(packed[:, off[f]:off[f] + m], B[:, :m])
+
+
+def test_autotune_frames_keeps_results(sb):
+    wl, arr, single, off, packed, n_dev, clouds = setup(sb)
+    arr.set_sampling_level(1)
+    S0 = arr.forward_frames(packed, n_dev).clone()
+    chunk, split = arr.autotune_frames(packed, n_dev)
+    assert chunk in (256, 512, 1024) and split in (1, 2, 4, 8)
+    assert torch.equal(arr.forward_frames(packed, n_dev), S0)
