@@ -60,6 +60,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-frames", action="store_true",
+                    help="skip the batched dynamic-imaging comparison")
     ap.add_argument("--profile", action="store_true",
                     help="short run for a profiler: no clocks, e2e or CPU baseline")
     return ap.parse_args(argv)
@@ -377,6 +379,11 @@ def run_native(args, rank, world, local):
                                 pairs_per_step, dev)
     if not args.profile and args.workload == "vessel":
         result["time_to_residual"] = time_to_residual(sb, arr, wl, y_full, init, n0)
+    if not (args.profile or args.no_frames) and args.workload == "vessel":
+        try:
+            result["batched_frames"] = batched_frames(args, sb, dev)
+        except Exception as exc:  # keep the main measurement if this part fails
+            result["batched_frames"] = {"error": f"{type(exc).__name__}: {exc}"}
     if world == 1 and rank == 0 and not (args.no_cpu_baseline or args.profile):
         result["cpu_baseline"] = cpu_baseline(wl, y_host, counts, n0, seconds=15.0)
     arr.close()
@@ -531,6 +538,171 @@ def time_to_residual(sb, arr, wl, y_full, init, n0, target=0.5, seg=10, max_iter
             "speedup": (a_s / p_s) if (p_s and a_s) else None,
             "paper_context": "SlingBAG Pro vs SlingBAG, hand vessels, 2006 sensors: 3.79 h vs "
                              "8.32 h (2.2x), hardware not stated"}
+
+
+def batched_frames(args, sb, dev, steps=8, warmup=3):
+    """Batched dynamic imaging (32 frames of the moving vessel phantom, 20k-200k
+    balls per frame, 256 sensors, 10/20/40 MHz, T = 512/1024/2048): the same
+    step as the main measurement (zero-gradient filtering, then one
+    iteration per level) run over every frame, four ways:
+
+    per_frame        one sbp_reconstruct call per frame (its own launches,
+                     sized by that frame's cloud);
+    per_frame_graph  the same calls captured once in a CUDA graph;
+    batched          one sbp_reconstruct_frames call: one launch per kernel
+                     covers all frames, tiles from sbp_autotune_frames;
+    batched_graph    that call captured in a CUDA graph (one graph launch
+                     per step).
+
+    Every arm starts from the same clouds; the per-iteration ball counts of
+    all arms must agree (the batched kernels equal the single-cloud ones
+    frame by frame). L2 is flushed before every timed step; the restore of
+    the initial clouds is outside the timed region."""
+    import torch
+
+    import workloads
+
+    fw = workloads.frames()
+    F, M, nl = fw.F, fw.sensors.M, len(fw.levels)
+    counts0 = np.array([b.n for b in fw.inits], dtype=np.int64)
+    caps = 2 * counts0
+    align = 1024
+    padded = (caps + align - 1) // align * align
+    total = int(padded.sum())
+    arr = sb.SensorArray(fw.sensors.pos, fw.sensors.normal, fw.c, fw.fs_mhz, fw.T, fw.levels,
+                         n_cap=total)
+    off = arr.set_frames(caps)
+
+    # measured traces: every frame's phantom rendered at 40 MHz, plus 1% noise
+    nt = fw.truths[0].n
+    tpad = (nt + align - 1) // align * align
+    tarr = sb.SensorArray(fw.sensors.pos, fw.sensors.normal, fw.c, fw.fs_mhz, fw.T, (1,),
+                          n_cap=F * tpad)
+    toff = tarr.set_frames([nt] * F)
+    tp = torch.zeros((5, F * tpad), dtype=torch.float32, device=dev)
+    for f, b in enumerate(fw.truths):
+        tp[:, toff[f]:toff[f] + nt] = torch.from_numpy(b.stack()).to(dev)
+    tarr.set_sampling_level_frames(0)
+    Yc = tarr.forward_frames(tp, torch.full((F,), nt, dtype=torch.int32, device=dev))
+    y_host = np.stack([workloads.add_noise(Yc[f].cpu().numpy(), seed=3000 + f)
+                       for f in range(F)])
+    tarr.close()
+    del tp, Yc
+    Y = torch.from_numpy(y_host).to(dev)
+
+    init = torch.zeros((5, total), dtype=torch.float32, device=dev)
+    for f, b in enumerate(fw.inits):
+        init[:, off[f]:off[f] + b.n] = torch.from_numpy(b.stack()).to(dev)
+    n_init = torch.from_numpy(counts0.astype(np.int32)).to(dev)
+    balls = torch.empty_like(init)
+    n_dev = torch.empty_like(n_init)
+    stages = stages_for(sb, fw)
+    gp = sb.GrowParams(seed=1000, **GROW)
+    n_log = torch.zeros(nl * F, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    # per-frame buffers for the single-cloud arms
+    single = sb.SensorArray(fw.sensors.pos, fw.sensors.normal, fw.c, fw.fs_mhz, fw.T,
+                            fw.levels, n_cap=int(padded.max()))
+    Bf = [torch.empty((5, int(padded[f])), dtype=torch.float32, device=dev) for f in range(F)]
+    nf = [torch.empty(1, dtype=torch.int32, device=dev) for _ in range(F)]
+    Yf = [Y[f].contiguous() for f in range(F)]
+    logf = torch.zeros((F, nl), dtype=torch.int32, device=dev)
+
+    def restore_batched():
+        balls.copy_(init)
+        n_dev.copy_(n_init)
+
+    def restore_single():
+        for f in range(F):
+            Bf[f].copy_(init[:, off[f]:off[f] + int(padded[f])])
+            nf[f].fill_(int(counts0[f]))
+
+    def run_batched():
+        arr.reconstruct_frames(Y, balls, n_dev, stages, grow=gp, n_log=n_log)
+
+    def run_single():
+        for f in range(F):
+            single.reconstruct(Yf[f], Bf[f], nf[f], stages, grow=gp, n_log=logf[f])
+
+    # tiles for the batched kernels, tuned on the initial clouds at the finest level
+    restore_batched()
+    arr.set_sampling_level_frames(nl - 1)
+    chunk, split = arr.autotune_frames(balls, n_dev)
+
+    def capture(restore, run):
+        restore()
+        run()  # first call allocates the scratch outside the capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        restore()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            run()
+        return g
+
+    launches = {}
+    for name, restore, run in (("per_frame", restore_single, run_single),
+                               ("batched", restore_batched, run_batched)):
+        restore()
+        l0 = sb.launch_count()
+        run()
+        launches[name] = int(sb.launch_count() - l0)
+    torch.cuda.synchronize()
+    g_single = capture(restore_single, run_single)
+    g_batched = capture(restore_batched, run_batched)
+
+    arms = {
+        "per_frame": (restore_single, run_single),
+        "per_frame_graph": (restore_single, g_single.replay),
+        "batched": (restore_batched, run_batched),
+        "batched_graph": (restore_batched, g_batched.replay),
+    }
+    stream = torch.cuda.current_stream()
+    out = {}
+    counts = {}
+    for name, (restore, run) in arms.items():
+        ms = []
+        for it in range(warmup + steps):
+            restore()
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            run()
+            b.record(stream)
+            if it >= warmup:
+                ms.append((a, b))
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ms]
+        if name.startswith("batched"):
+            c = n_log.cpu().numpy().reshape(nl, F).T.astype(np.int64)
+        else:
+            c = logf.cpu().numpy().astype(np.int64)
+        counts[name] = c
+        out[name] = {"ms_per_step": statistics.mean(ms)}
+    if arr.sync_status() != 0 or single.sync_status() != 0:
+        raise RuntimeError("device status latched in the batched-frames measurement")
+    ref = counts["per_frame"]
+    same = all(np.array_equal(c, ref) for c in counts.values())
+    pairs = float(ref.sum()) * M
+    for name in out:
+        out[name]["pairs_per_s"] = pairs / (out[name]["ms_per_step"] * 1e-3)
+    arr.close()
+    single.close()
+    return {
+        "workload": fw.name,
+        "frames": F, "sensors": M, "balls_init_total": int(counts0.sum()),
+        "balls_init_range": [int(counts0.min()), int(counts0.max())],
+        "pairs_per_step": pairs, "steps": steps, "warmup": warmup,
+        "counts_identical_across_arms": bool(same),
+        "autotuned": {"forward_balls_per_cta": chunk, "adjoint_ctas_per_cluster": split},
+        "kernel_launches_per_step": launches,
+        **out,
+        "speedup_batched_graph_vs_per_frame": (out["per_frame"]["ms_per_step"] /
+                                               out["batched_graph"]["ms_per_step"]),
+        "l2": "flushed before every timed step (512 MB write)",
+    }
 
 
 def run_e2e(args, sb, arr, wl, y_host, init, n0, n_cap, stages, adam, pairs_per_step, dev):

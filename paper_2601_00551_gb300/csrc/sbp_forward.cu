@@ -49,6 +49,8 @@ constexpr int kWindow = 384;        // cells per sensor held in shared memory
 constexpr int kChunk = 512;         // largest number of balls per CTA
 constexpr int kLoBits = 20;         // 2 * kChunk * 2^kLoBits < 2^32
 static_assert(2LL * kChunk * (1LL << kLoBits) < (1LL << 32), "low word could overflow");
+// the batched launch accepts chunks up to one frame alignment unit
+static_assert(2LL * SBP_FRAME_ALIGN * (1LL << kLoBits) < (1LL << 32), "low word could overflow");
 constexpr int kFinalizeThreads = 1024;
 constexpr int kFracHeadroomBits = 34;  // F = 34 - ceil(log2 max|p0|)
 

@@ -150,3 +150,42 @@ def test_autotune_frames_keeps_results(sb):
     chunk, split = arr.autotune_frames(packed, n_dev)
     assert chunk in (256, 512, 1024) and split in (1, 2, 4, 8)
     assert torch.equal(arr.forward_frames(packed, n_dev), S0)
+
+
+def test_reconstruct_frames_replays_in_cuda_graph(sb):
+    wl, arr, single, off, packed, n_dev, clouds = setup(sb)
+    F = len(COUNTS)
+    y = np.stack([oracle.forward(workloads.uniform_balls(200, 2.0, 0.05, 0.2, 0.5, 1.0,
+                                                         seed=90 + f).stack(),
+                                 wl.sensors.pos, wl.sensors.normal, wl.c, 1 / wl.fs_mhz, wl.T)
+                  for f in range(F)]).astype(np.float32)
+    Y = torch.from_numpy(y).cuda()
+    stages = [sb.Stage(0, 1, 3, True, False), sb.Stage(1, 2, 7, True, True)]
+    gp = sb.GrowParams(seed=5, R_max=0.3, g_dup=2.0)
+    init, n0 = packed.clone(), n_dev.clone()
+    loss = torch.zeros(3 * F, dtype=torch.float64, device="cuda")
+
+    def run():
+        arr.reconstruct_frames(Y, packed, n_dev, stages, grow=gp, loss_log=loss)
+
+    run()  # eager; also allocates the scratch
+    torch.cuda.synchronize()
+    eager = (packed.clone(), n_dev.clone(), loss.clone())
+    g = torch.cuda.CUDAGraph()
+    packed.copy_(init)
+    n_dev.copy_(n0)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        run()
+    for _ in range(2):  # replays start from the restored clouds
+        packed.copy_(init)
+        n_dev.copy_(n0)
+        loss.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert arr.sync_status() == 0
+        assert torch.equal(n_dev, eager[1])
+        assert torch.equal(loss, eager[2])
+        for f in range(F):
+            m = int(n_dev[f].item())
+            assert torch.equal(packed[:, off[f]:off[f] + m], eager[0][:, off[f]:off[f] + m])

@@ -293,3 +293,53 @@ def vessel(n_init: int = 200_000, n_truth: int = 150_000, M: int = 512, T: int =
     truth = vessel_tree(n_truth, half=10.0, seed=0)
     return Workload("vessel: 200k balls x 512 sensors, 10/20/40 MHz, T=1024/2048/4096",
                     sens, init, truth, 40.0, T, (4, 2, 1), half=10.0)
+
+
+@dataclasses.dataclass
+class FrameWorkload:
+    """Dynamic imaging: one sensor array, F frames of a moving phantom, each
+    reconstructed from its own initial cloud."""
+    name: str
+    sensors: Sensors
+    inits: list           # initial cloud per frame (Balls)
+    truths: list          # ground truth per frame (Balls), the phantom shifted
+    shifts: np.ndarray    # (F, 3) displacement of frame f from frame 0, mm
+    fs_mhz: float
+    T: int
+    levels: tuple
+    c: float = C_MM_PER_US
+    half: float = 10.0
+
+    @property
+    def F(self) -> int:
+        return len(self.inits)
+
+
+def frames(n_frames: int = 32, n_lo: int = 20_000, n_hi: int = 200_000, n_truth: int = 150_000,
+           M: int = 256, T: int = 2048, max_step: float = 0.5, levels=(4, 2, 1),
+           sort: bool = True) -> FrameWorkload:
+    """The batched dynamic-imaging case: the vessel-tree phantom of `vessel`
+    moved rigidly from frame to frame (step f has length ~U(0, max_step) mm
+    along a seeded random direction, seed 4), measured by 256 sensors of the
+    same ellipsoidal cap at 40 MHz with T = 2048; frame f starts from its own
+    uniform random cloud whose size is drawn uniformly from {n_lo..n_hi}
+    (seed 4), laid out in Morton order."""
+    sens = ellipsoid_cap(M, (30.0, 30.0, 20.0), 15.0, seed=2)
+    rng = np.random.default_rng(4)
+    counts = rng.integers(n_lo, n_hi + 1, size=n_frames)
+    steps = _random_unit(rng, n_frames) * rng.uniform(0.0, max_step, size=(n_frames, 1))
+    steps[0] = 0.0
+    shifts = np.cumsum(steps, axis=0)
+    base = vessel_tree(n_truth, half=10.0, seed=0)
+    truths, inits = [], []
+    for f in range(n_frames):
+        s = shifts[f].astype(np.float32)
+        truths.append(Balls(base.x + s[0], base.y + s[1], base.z + s[2], base.R.copy(),
+                            base.p0.copy()))
+        b = uniform_balls(int(counts[f]), 10.0, 0.05, 0.2, 0.0, 1.0, seed=1000 + f)
+        if sort:
+            b = b.take(morton_order(b, 10.0))
+        inits.append(b)
+    name = (f"frames: {n_frames} frames x {n_lo // 1000}k-{n_hi // 1000}k balls x {M} sensors, "
+            f"10/20/40 MHz, T={T // levels[0]}/{T // levels[1]}/{T}")
+    return FrameWorkload(name, sens, inits, truths, shifts, 40.0, T, tuple(levels))
