@@ -7,6 +7,9 @@
  * events on a private stream, synchronises, and writes an operation rate:
  *   sbp_probe_fp32_fma:     thread-level FP32 fused multiply-adds per second
  *                           (independent chains, no memory traffic);
+ *   sbp_probe_fp32x2_fma:   the same FMAs issued as packed pairs (one
+ *                           instruction performs the FMAs of both halves of
+ *                           a float2; sm_100 and later);
  *   sbp_probe_issue:        warp instructions issued per second by a loop of
  *                           independent integer adds (ALU pipe);
  *   sbp_probe_smem_atomic:  shared-memory atomic adds per second, by kind:
@@ -24,6 +27,7 @@ extern "C" {
 #endif
 
 int sbp_probe_fp32_fma(double* fma_per_s);
+int sbp_probe_fp32x2_fma(double* fma_per_s);
 int sbp_probe_issue(double* warp_inst_per_s);
 int sbp_probe_smem_atomic(int kind, double* atomics_per_s);
 

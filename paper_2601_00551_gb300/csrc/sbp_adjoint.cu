@@ -113,8 +113,52 @@ struct GradOut {
 // P0_ONLY: only dL/dp0 is wanted (the zero-gradient pass), so the chain rule
 // for R and the centre is skipped.
 // Launched with a cluster of gridDim.y CTAs along y (cudaLaunchKernelEx).
+// Window sums of one pair against the residual row of its sensor: the first
+// cell gf = G[jL-1], the last cell gl = G[jH] (0 past the record) and, with
+// d_q = G[jL+q] - gl over the L = min(jH, Tk) - jL ramp cells,
+// E0 = sum_q d_q and E1 = sum_q q d_q. Reads the staged window when it holds
+// every needed cell, else the global row.
+__device__ __forceinline__ void adj_window_sums(const float* __restrict__ sGrow, int jlo, int len,
+                                                bool staged, const float* __restrict__ Gm,
+                                                int jL, int jH, int Tk, float& gf, float& gl,
+                                                float& E0, float& E1) {
+    const int L = min(jH, Tk) - jL;
+    E0 = 0.f;
+    E1 = 0.f;
+    // the box bound puts cells jL-1 .. min(jH, Tk-1) inside the staged
+    // window; checked anyway so that no read can leave it
+    if (staged && jL - 1 >= jlo && min(jH, Tk - 1) - jlo < len) {
+        const float* Gw = sGrow - jlo + jL;
+        gf = Gw[-1];
+        gl = jH < Tk ? Gw[jH - jL] : 0.0f;
+        // E1 = sum_q q d_q accumulated as the running sums of the tail
+        float run = 0.0f;
+        int q = L - 1;
+        for (; q >= 2; q -= 2) {
+            const float d1 = Gw[q] - gl, d0 = Gw[q - 1] - gl;
+            run += d1;
+            E1 += run;
+            run += d0;
+            E1 += run;
+        }
+        if (q == 1) {
+            run += Gw[1] - gl;
+            E1 += run;
+        }
+        E0 = L > 0 ? run + (Gw[0] - gl) : 0.0f;
+    } else {
+        gf = Gm[jL - 1];
+        gl = jH < Tk ? Gm[jH] : 0.0f;
+        for (int q = 0; q < L; ++q) {
+            const float d = Gm[jL + q] - gl;
+            E0 += d;
+            E1 = fmaf((float)q, d, E1);
+        }
+    }
+}
+
 template <bool P0_ONLY>
-__global__ void __launch_bounds__(kAdjThreads)
+__global__ void __launch_bounds__(kAdjThreads, P0_ONLY ? 8 : 6)
 adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, LevelGeo g,
                  const float* __restrict__ G_all, unsigned mask, GradOut out) {
     __shared__ float sG[kAdjGroup * kAdjWindow];  // [sensor][cell]
@@ -172,7 +216,7 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     }
     const float h = g.h_hi;
     const float hh2 = 2.0f * h * h;
-    float gx = 0.f, gy = 0.f, gz = 0.f, gR = 0.f, gp = 0.f;
+    float2 gx2 = f2(0.f), gy2 = f2(0.f), gz2 = f2(0.f), gR2 = f2(0.f), gp2 = f2(0.f);
     // this CTA's share of the sensors, whole groups
     const int part = (int)cluster.block_rank();
     const int split = (int)gridDim.y;  // one cluster spans all of y
@@ -194,6 +238,10 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
                                             __int_as_float(len));
             atomicMax(&s_lmax, len);
         }
+        if ((cnt & 1) && threadIdx.x == cnt) {  // odd group: a partner that no ball reaches
+            s_sa[cnt] = make_float4(1e6f, 1e6f, 1e6f, 0.0f);
+            s_sb[cnt] = make_float4(0.0f, 1.0f, __int_as_float(0), __int_as_float(0));
+        }
         __syncthreads();
         const bool staged = s_lmax <= kAdjWindow;  // uniform
         if (staged) {
@@ -206,70 +254,103 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
             __syncthreads();
         }
         if (!valid) continue;
+        // two sensors at a time, evaluated side by side in the halves of float2
 #pragma unroll 1
-        for (int s = 0; s < cnt; ++s) {
-            const float4 sa = s_sa[s], sb = s_sb[s];
-            const PairDist pd = sbp_pair_distance(cx, cy, cz, sa.x, sa.y, sa.z);
-            PairWindow win;
-            if (!sbp_window(pd, R, g, win)) continue;
-            const float ux = pd.dx * pd.rd, uy = pd.dy * pd.rd, uz = pd.dz * pd.rd;
-            const float nx = sa.w, ny = sb.x, nz = sb.y;
-            const float cosv = nx * ux + ny * uy + nz * uz;
-            float act;
-            const float w = sbp_weight(g.wmode, cosv, act);
-            if (w == 0.0f && act == 0.0f) continue;
-            const int jL = win.jL, jH = win.jH;
-            const float b0 = win.b0;
-            const int L = min(jH, Tk) - jL;  // ramp cells inside the record
-            float gf, gl, E0 = 0.f, E1 = 0.f;
-            const int jlo = __float_as_int(sb.z), len = __float_as_int(sb.w);
-            // the box bound puts cells jL-1 .. min(jH, Tk-1) inside the staged
-            // window; checked anyway so that no read can leave it
-            if (staged && jL - 1 >= jlo && min(jH, Tk - 1) - jlo < len) {
-                const float* Gw = sG + s * kAdjWindow - jlo + jL;
-                gf = Gw[-1];
-                gl = jH < Tk ? Gw[jH - jL] : 0.0f;
-                // E1 = sum_q q d_q accumulated as the running sums of the tail
-                float run = 0.0f;
-                int q = L - 1;
+        for (int s = 0; s < cnt; s += 2) {
+            const float4 saA = s_sa[s], sbA = s_sb[s], saB = s_sa[s + 1], sbB = s_sb[s + 1];
+            const PairDist2 pd =
+                sbp_pair_distance2(f2(cx), f2(cy), f2(cz), make_float2(saA.x, saB.x),
+                                   make_float2(saA.y, saB.y), make_float2(saA.z, saB.z));
+            PairWindow wa, wb;
+            bool okA = sbp_window_ff(pd.dh.x, pd.dl.x, R, g, wa);
+            bool okB = sbp_window_ff(pd.dh.y, pd.dl.y, R, g, wb);
+            if (!(okA || okB)) continue;
+            const float2 ux = f2mul(pd.dx, pd.rd), uy = f2mul(pd.dy, pd.rd),
+                         uz = f2mul(pd.dz, pd.rd);
+            const float2 nx = make_float2(saA.w, saB.w), ny = make_float2(sbA.x, sbB.x),
+                         nz = make_float2(sbA.y, sbB.y);
+            const float2 cosv = f2fma(nx, ux, f2fma(ny, uy, f2mul(nz, uz)));
+            float actA, actB;
+            float wA = sbp_weight(g.wmode, cosv.x, actA), wB = sbp_weight(g.wmode, cosv.y, actB);
+            okA = okA && !(wA == 0.0f && actA == 0.0f);
+            okB = okB && !(wB == 0.0f && actB == 0.0f);
+            if (!(okA || okB)) continue;
+            // window sums; a pair that does not count gets zeros, so that its
+            // half contributes exactly nothing below
+            const int jloA = __float_as_int(sbA.z), lenA = __float_as_int(sbA.w);
+            const int jloB = __float_as_int(sbB.z), lenB = __float_as_int(sbB.w);
+            float2 gf = f2(0.f), gl = f2(0.f), E0 = f2(0.f), E1 = f2(0.f);
+            const int LA = min(wa.jH, Tk) - wa.jL, LB = min(wb.jH, Tk) - wb.jL;
+            // side by side when both windows are staged and differ by at most
+            // one ramp cell: the shorter one then reads one cell further, its
+            // own last cell G[jH] (inside the record), which adds d = 0
+            const bool inA = okA && staged && wa.jL - 1 >= jloA && min(wa.jH, Tk - 1) - jloA < lenA;
+            const bool inB = okB && staged && wb.jL - 1 >= jloB && min(wb.jH, Tk - 1) - jloB < lenB;
+            if (inA && inB && abs(LA - LB) <= 1 && (LA >= LB || wa.jH < Tk) &&
+                (LB >= LA || wb.jH < Tk)) {
+                const float* GwA = sG + s * kAdjWindow - jloA + wa.jL;
+                const float* GwB = sG + (s + 1) * kAdjWindow - jloB + wb.jL;
+                gf = make_float2(GwA[-1], GwB[-1]);
+                gl = make_float2(wa.jH < Tk ? GwA[wa.jH - wa.jL] : 0.0f,
+                                 wb.jH < Tk ? GwB[wb.jH - wb.jL] : 0.0f);
+                const float2 ngl = f2neg(gl);
+                const int Lm = max(LA, LB);
+                float2 run = f2(0.f);
+                int q = Lm - 1;
                 for (; q >= 2; q -= 2) {
-                    const float d1 = Gw[q] - gl, d0 = Gw[q - 1] - gl;
-                    run += d1;
-                    E1 += run;
-                    run += d0;
-                    E1 += run;
+                    const float2 d1 = f2add(make_float2(GwA[q], GwB[q]), ngl);
+                    const float2 d0 = f2add(make_float2(GwA[q - 1], GwB[q - 1]), ngl);
+                    run = f2add(run, d1);
+                    E1 = f2add(E1, run);
+                    run = f2add(run, d0);
+                    E1 = f2add(E1, run);
                 }
                 if (q == 1) {
-                    run += Gw[1] - gl;
-                    E1 += run;
+                    run = f2add(run, f2add(make_float2(GwA[1], GwB[1]), ngl));
+                    E1 = f2add(E1, run);
                 }
-                E0 = L > 0 ? run + (Gw[0] - gl) : 0.0f;
+                if (Lm > 0) E0 = f2add(run, f2add(make_float2(GwA[0], GwB[0]), ngl));
             } else {
-                const float* Gm = G + (size_t)(m0 + s) * Tk;
-                gf = Gm[jL - 1];
-                gl = jH < Tk ? Gm[jH] : 0.0f;
-                for (int q = 0; q < L; ++q) {
-                    const float d = Gm[jL + q] - gl;
-                    E0 += d;
-                    E1 = fmaf((float)q, d, E1);
-                }
+                if (okA)
+                    adj_window_sums(sG + s * kAdjWindow, jloA, lenA, staged,
+                                    G + (size_t)(m0 + s) * Tk, wa.jL, wa.jH, Tk, gf.x, gl.x, E0.x,
+                                    E1.x);
+                if (okB)
+                    adj_window_sums(sG + (s + 1) * kAdjWindow, jloB, lenB, staged,
+                                    G + (size_t)(m0 + s + 1) * Tk, wb.jL, wb.jH, Tk, gf.y, gl.y,
+                                    E0.y, E1.y);
             }
-            const float Df = gf - gl;
-            const float A = Df * fmaxf(R - b0, 0.0f) * (R + b0) + E0 * h * (2.0f * b0 - h) -
-                            hh2 * E1;
-            const float qd = g.inv_4h * pd.rd;  // 1 / (4 d h)
-            const float K0 = w * qd;
-            gp += K0 * A;
+            if (!okA) {
+                wA = 0.0f;
+                actA = 0.0f;
+            }
+            if (!okB) {
+                wB = 0.0f;
+                actB = 0.0f;
+            }
+            const float2 b0 = make_float2(okA ? wa.b0 : 0.0f, okB ? wb.b0 : 0.0f);
+            const float2 Df = f2sub(gf, gl);
+            const float2 ra = make_float2(fmaxf(R - b0.x, 0.0f), fmaxf(R - b0.y, 0.0f));
+            const float2 A = f2fma(f2mul(Df, ra), f2add(f2(R), b0),
+                                   f2fma(f2mul(E0, f2(h)), f2fma(f2(2.0f), b0, f2(-h)),
+                                         f2mul(f2(-hh2), E1)));
+            const float2 qd = f2mul(f2(g.inv_4h), pd.rd);  // 1 / (4 d h)
+            const float2 K0 = f2mul(make_float2(wA, wB), qd);
+            gp2 = f2fma(K0, A, gp2);
             if (P0_ONLY) continue;
-            const float Bh = h * E0 - b0 * Df;
-            gR += 2.0f * p0 * K0 * R * Df;
-            const float gd = p0 * K0 * (2.0f * Bh - A * pd.rd);
-            const float gw = p0 * A * qd * act;
-            gx += gd * ux + gw * (nx - cosv * ux) * pd.rd;
-            gy += gd * uy + gw * (ny - cosv * uy) * pd.rd;
-            gz += gd * uz + gw * (nz - cosv * uz) * pd.rd;
+            const float2 Bh = f2fma(f2(h), E0, f2neg(f2mul(b0, Df)));
+            const float2 pK = f2mul(f2(p0), K0);
+            gR2 = f2fma(f2mul(pK, f2(2.0f * R)), Df, gR2);
+            const float2 gd = f2mul(pK, f2fma(f2(2.0f), Bh, f2neg(f2mul(A, pd.rd))));
+            const float2 gw = f2mul(f2mul(f2mul(f2(p0), A), qd), make_float2(actA, actB));
+            const float2 gwr = f2mul(gw, pd.rd);
+            gx2 = f2fma(gd, ux, f2fma(gwr, f2fma(f2neg(cosv), ux, nx), gx2));
+            gy2 = f2fma(gd, uy, f2fma(gwr, f2fma(f2neg(cosv), uy, ny), gy2));
+            gz2 = f2fma(gd, uz, f2fma(gwr, f2fma(f2neg(cosv), uz, nz), gz2));
         }
     }
+    const float gx = gx2.x + gx2.y, gy = gy2.x + gy2.y, gz = gz2.x + gz2.y;
+    const float gR = gR2.x + gR2.y, gp = gp2.x + gp2.y;
     if (valid) {  // stored under the ball's chunk-local index
         s_part[li * 5 + 0] = gx;
         s_part[li * 5 + 1] = gy;

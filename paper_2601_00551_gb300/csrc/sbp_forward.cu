@@ -95,6 +95,63 @@ __device__ __forceinline__ void fwd_add32(unsigned int* lo, int v) {
     atomicAdd(lo + kWindow * 32, (unsigned int)(v >> kLoBits));
 }
 
+// Adds one pair's six second-difference impulses to the lane's column of the
+// split accumulator: three at cells ra .. ra+2 (relative to this pass) from
+// the first-cell, ramp and slope coefficients fa, f1, f2, three at rb .. rb+2
+// from the last-cell coefficient fe, with L = jH - jL ramp cells. Cells
+// outside [0, lim] belong to another pass or lie past the record.
+__device__ __forceinline__ void fwd_emit(unsigned int* col, int ra, int rb, int L, int lim,
+                                         float fa, float fe, float f1, float f2) {
+    const bool fast_a = ra >= 0 && ra + 2 <= lim, fast_b = rb >= 0 && rb + 2 <= lim;
+    // impulses are sums of at most four coefficient terms; below 2^28 each
+    // they fit in 32 bits (the usual case)
+    const float big = fmaxf(fmaxf(fabsf(fa), fabsf(fe)), fmaxf(fabsf(f1), fabsf(f2) * (float)(L + 2)));
+    if (big < 268435456.0f && fast_a && fast_b) {
+        const int qa = __float2int_rn(fa), qe = __float2int_rn(fe);
+        const int q1 = __float2int_rn(f1), q2 = __float2int_rn(f2);
+        const int Lq2 = L * q2;
+        unsigned int* a = col + ra * 32;
+        fwd_add32(a, qa);
+        fwd_add32(a + 32, q1 - 2 * qa);
+        fwd_add32(a + 64, qa - q1 + q2);
+        unsigned int* c = col + rb * 32;
+        fwd_add32(c, qe - q1 - Lq2);
+        fwd_add32(c + 32, q1 + Lq2 - q2 - 2 * qe);
+        fwd_add32(c + 64, qe);
+        return;
+    }
+    const long long qa = fwd_f2ll(fa), qe = fwd_f2ll(fe);
+    const long long q1 = fwd_f2ll(f1), q2 = fwd_f2ll(f2);
+    const long long Lq2 = (long long)L * q2;
+    // second difference of the pair's cell values: three impulses at
+    // jL-1 .. jL+1 and three at jH .. jH+2 (valid for every jH >= jL; when
+    // the two triples overlap the impulses add up)
+    const long long ia0 = qa, ia1 = q1 - 2 * qa, ia2 = qa - q1 + q2;
+    const long long ib0 = qe - q1 - Lq2, ib1 = q1 + Lq2 - q2 - 2 * qe, ib2 = qe;
+    if (fast_a) {
+        unsigned int* a = col + ra * 32;
+        fwd_add(a, ia0);
+        fwd_add(a + 32, ia1);
+        fwd_add(a + 64, ia2);
+    } else {
+        const long long v[3] = {ia0, ia1, ia2};
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (ra + q >= 0 && ra + q <= lim) fwd_add(col + (ra + q) * 32, v[q]);
+    }
+    if (fast_b) {
+        unsigned int* c = col + rb * 32;
+        fwd_add(c, ib0);
+        fwd_add(c + 32, ib1);
+        fwd_add(c + 64, ib2);
+    } else {
+        const long long v[3] = {ib0, ib1, ib2};
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (rb + q >= 0 && rb + q <= lim) fwd_add(col + (rb + q) * 32, v[q]);
+    }
+}
+
 // Fixed-point exponent F: values are stored as round(v * 2^F).
 __device__ __forceinline__ int fwd_frac_bits(unsigned int pmax_bits) {
     const float pm = __uint_as_float(pmax_bits);
@@ -122,8 +179,7 @@ fwd_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     const int m = blockIdx.y * 32 + lane;
     const bool sv = m < M;
 
-    for (int t = threadIdx.x; t < 2 * kWindow * 32; t += blockDim.x) sacc[t] = 0u;
-    sbp_chunk_box(b, c0, c1, s_red, s_box);  // also orders the clearing above
+    sbp_chunk_box(b, c0, c1, s_red, s_box);
 
     float sx = 0.f, sy = 0.f, sz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
     int jlo = 0, jhi = -1;
@@ -141,6 +197,13 @@ fwd_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
     const int passes = (wmax + kWindow - 1) / kWindow;  // identical in every warp
     if (warp == 0) s_jlo[lane] = jlo;
+    // only the cells some lane can touch are cleared (and later flushed)
+    const int used0 = min(wmax, kWindow) * 32;
+    for (int t = threadIdx.x; t < used0; t += blockDim.x) {
+        sacc[t] = 0u;
+        sacc[kWindow * 32 + t] = 0u;
+    }
+    __syncthreads();
 
     const float scale = __int_as_float((127 + fwd_frac_bits(pmax[fs.f])) << 23);  // 2^F
     const float h = g.h_hi;
@@ -150,102 +213,62 @@ fwd_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
         const int base = jlo + p * kWindow;  // this lane's first cell in this pass
         // last cell of this pass that may be stored: inside the record and the buffer
         const int lim = min(jhi - base, kWindow - 1);
-        int i = c0 + warp;
-        // the next ball is loaded while the current one is processed
-        float nx_ = 0.f, ny_ = 0.f, nz_ = 0.f, nR = 0.f, np0 = 0.f;
-        if (i < c1) {
-            nx_ = b.x[i];
-            ny_ = b.y[i];
-            nz_ = b.z[i];
-            nR = b.R[i];
-            np0 = b.p0[i];
-        }
-        for (; i < c1; i += kGroupWarps) {
-            const float cx = nx_, cy = ny_, cz = nz_, R = nR, p0 = np0;
-            const int inext = i + kGroupWarps;
-            if (inext < c1) {
-                nx_ = b.x[inext];
-                ny_ = b.y[inext];
-                nz_ = b.z[inext];
-                nR = b.R[inext];
-                np0 = b.p0[inext];
-            }
-            if (p0 == 0.0f || !sv) continue;
-            const PairDist pd = sbp_pair_distance(cx, cy, cz, sx, sy, sz);
-            if (!(pd.dh + pd.dl > R)) {
+        unsigned int* col = sacc + lane;
+        // The warp takes its balls two at a time (i and i + kGroupWarps) and
+        // evaluates both pairs of its lane's sensor side by side; an odd last
+        // ball is paired with an empty one. Every ball goes through the same
+        // instructions, so its impulses do not depend on its partner.
+        for (int i = c0 + warp; i < c1; i += 2 * kGroupWarps) {
+            const int iB = i + kGroupWarps;
+            const bool hasB = iB < c1;
+            const float2 cx = make_float2(b.x[i], hasB ? b.x[iB] : 0.0f);
+            const float2 cy = make_float2(b.y[i], hasB ? b.y[iB] : 0.0f);
+            const float2 cz = make_float2(b.z[i], hasB ? b.z[iB] : 0.0f);
+            const float2 R2 = make_float2(b.R[i], hasB ? b.R[iB] : 0.0f);
+            const float2 P2 = make_float2(b.p0[i], hasB ? b.p0[iB] : 0.0f);
+            if ((P2.x == 0.0f && P2.y == 0.0f) || !sv) continue;
+            const PairDist2 pd = sbp_pair_distance2(cx, cy, cz, f2(sx), f2(sy), f2(sz));
+            // inside test and window, per pair
+            bool okA = P2.x != 0.0f, okB = P2.y != 0.0f;
+            if (okA && !(pd.dh.x + pd.dl.x > R2.x)) {
                 if (p == 0) ++inside;
-                continue;
+                okA = false;
             }
-            PairWindow win;
-            if (!sbp_window(pd, R, g, win)) continue;
-            const int jL = win.jL, jH = win.jH;
-            const float cosv = (nx * pd.dx + ny * pd.dy + nz * pd.dz) * pd.rd;
-            float act;
-            const float w = sbp_weight(g.wmode, cosv, act);
-            if (w == 0.0f) continue;
-            const float b0 = win.b0, bL = win.bL;
-            const float Ks = p0 * w * g.inv_4h * pd.rd * scale;  // K 2^F
-            const float fa = Ks * fmaxf(R - b0, 0.0f) * (R + b0);
-            const float fe = -(Ks * fmaxf(R + bL, 0.0f) * (R - bL));
-            const float f1 = Ks * h * (2.0f * b0 - h);
-            const float f2 = Ks * d2c;
-            const int L = jH - jL;
-            unsigned int* col = sacc + lane;
-            const int ra = jL - 1 - base, rb = jH - base;
-            const bool fast_a = ra >= 0 && ra + 2 <= lim, fast_b = rb >= 0 && rb + 2 <= lim;
-            // impulses are sums of at most four coefficient terms; below 2^28
-            // each they fit in 32 bits (the usual case)
-            const float big = fmaxf(fmaxf(fabsf(fa), fabsf(fe)),
-                                    fmaxf(fabsf(f1), fabsf(f2) * (float)(L + 2)));
-            if (big < 268435456.0f && fast_a && fast_b) {
-                const int qa = __float2int_rn(fa), qe = __float2int_rn(fe);
-                const int q1 = __float2int_rn(f1), q2 = __float2int_rn(f2);
-                const int Lq2 = L * q2;
-                unsigned int* a = col + ra * 32;
-                fwd_add32(a, qa);
-                fwd_add32(a + 32, q1 - 2 * qa);
-                fwd_add32(a + 64, qa - q1 + q2);
-                unsigned int* c = col + rb * 32;
-                fwd_add32(c, qe - q1 - Lq2);
-                fwd_add32(c + 32, q1 + Lq2 - q2 - 2 * qe);
-                fwd_add32(c + 64, qe);
-                continue;
+            if (okB && !(pd.dh.y + pd.dl.y > R2.y)) {
+                if (p == 0) ++inside;
+                okB = false;
             }
-            const long long qa = fwd_f2ll(fa), qe = fwd_f2ll(fe);
-            const long long q1 = fwd_f2ll(f1), q2 = fwd_f2ll(f2);
-            const long long Lq2 = (long long)L * q2;
-            // second difference of the pair's cell values: three impulses at
-            // jL-1.. jL+1 and three at jH..jH+2 (valid for every jH >= jL; when
-            // the two triples overlap the impulses add up)
-            const long long ia0 = qa, ia1 = q1 - 2 * qa, ia2 = qa - q1 + q2;
-            const long long ib0 = qe - q1 - Lq2, ib1 = q1 + Lq2 - q2 - 2 * qe, ib2 = qe;
-            if (fast_a) {
-                unsigned int* a = col + ra * 32;
-                fwd_add(a, ia0);
-                fwd_add(a + 32, ia1);
-                fwd_add(a + 64, ia2);
-            } else {
-                const long long v[3] = {ia0, ia1, ia2};
-#pragma unroll
-                for (int q = 0; q < 3; ++q)
-                    if (ra + q >= 0 && ra + q <= lim) fwd_add(col + (ra + q) * 32, v[q]);
-            }
-            if (fast_b) {
-                unsigned int* c = col + rb * 32;
-                fwd_add(c, ib0);
-                fwd_add(c + 32, ib1);
-                fwd_add(c + 64, ib2);
-            } else {
-                const long long v[3] = {ib0, ib1, ib2};
-#pragma unroll
-                for (int q = 0; q < 3; ++q)
-                    if (rb + q >= 0 && rb + q <= lim) fwd_add(col + (rb + q) * 32, v[q]);
-            }
+            PairWindow wa, wb;
+            okA = okA && sbp_window_ff(pd.dh.x, pd.dl.x, R2.x, g, wa);
+            okB = okB && sbp_window_ff(pd.dh.y, pd.dl.y, R2.y, g, wb);
+            if (!(okA || okB)) continue;
+            const float2 cosv = f2mul(
+                f2fma(f2(nx), pd.dx, f2fma(f2(ny), pd.dy, f2mul(f2(nz), pd.dz))), pd.rd);
+            float actA, actB;
+            const float2 w = make_float2(sbp_weight(g.wmode, cosv.x, actA),
+                                         sbp_weight(g.wmode, cosv.y, actB));
+            okA = okA && w.x != 0.0f;
+            okB = okB && w.y != 0.0f;
+            if (!(okA || okB)) continue;
+            const float2 b0 = make_float2(wa.b0, wb.b0), bL = make_float2(wa.bL, wb.bL);
+            // K 2^F = p0 w 2^F / (4 d h)
+            const float2 Ks = f2mul(f2mul(f2mul(P2, w), f2(g.inv_4h * scale)), pd.rd);
+            const float2 ra = make_float2(fmaxf(R2.x - b0.x, 0.0f), fmaxf(R2.y - b0.y, 0.0f));
+            const float2 re = make_float2(fmaxf(R2.x + bL.x, 0.0f), fmaxf(R2.y + bL.y, 0.0f));
+            const float2 fa = f2mul(f2mul(Ks, ra), f2add(R2, b0));
+            const float2 fe = f2neg(f2mul(f2mul(Ks, re), f2sub(R2, bL)));
+            const float2 f1 = f2mul(f2mul(Ks, f2(h)), f2fma(f2(2.0f), b0, f2(-h)));
+            const float2 fq = f2mul(Ks, f2(d2c));
+            if (okA) fwd_emit(col, wa.jL - 1 - base, wa.jH - base, wa.jH - wa.jL, lim, fa.x, fe.x,
+                              f1.x, fq.x);
+            if (okB) fwd_emit(col, wb.jL - 1 - base, wb.jH - base, wb.jH - wb.jL, lim, fa.y, fe.y,
+                              f1.y, fq.y);
         }
         __syncthreads();
         // flush this pass: lanes of a warp read 32 consecutive words (one cell
         // of all 32 sensors), recombine the two halves and clear them
-        for (int t = threadIdx.x; t < kWindow * 32; t += blockDim.x) {
+        const int used = min(wmax - p * kWindow, kWindow) * 32;
+        for (int t = threadIdx.x; t < used; t += blockDim.x) {
             const unsigned int lo = sacc[t];
             const int hi = (int)sacc[kWindow * 32 + t];
             if (lo | (unsigned)hi) {

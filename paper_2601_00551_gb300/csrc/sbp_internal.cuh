@@ -232,6 +232,68 @@ __device__ __forceinline__ PairDist sbp_pair_distance(float cx, float cy, float 
     return p;
 }
 
+// ----------------------------------------------------------------------------
+// Two pairs at once. Blackwell issues the FP32 add, multiply and fused
+// multiply-add of both halves of a float2 as one instruction, so a thread
+// that evaluates two pairs side by side spends half the issue slots on their
+// floating-point arithmetic. Every operation below rounds each half exactly
+// as its scalar counterpart does, so a pair's result does not depend on
+// which half it was evaluated in.
+// ----------------------------------------------------------------------------
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b: b * (-1) + a rounds once, to the same value as the subtraction
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {
+    return __ffma2_rn(a, b, c);
+}
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ void ff2_two_sum(float2 a, float2 b, float2& s, float2& e) {
+    s = f2add(a, b);
+    const float2 bb = f2sub(s, a);
+    e = f2add(f2sub(a, f2sub(s, bb)), f2sub(b, bb));
+}
+
+struct PairDist2 {
+    float2 dh, dl;      // d = dh + dl, per half
+    float2 dx, dy, dz;  // c - s rounded to float
+    float2 rd;          // ~1/dh
+};
+
+// sbp_pair_distance for two (ball, sensor) pairs; every half equals the
+// scalar result bit for bit.
+__device__ __forceinline__ PairDist2 sbp_pair_distance2(float2 cx, float2 cy, float2 cz,
+                                                        float2 sx, float2 sy, float2 sz) {
+    PairDist2 p;
+    float2 ex, ey, ez;
+    ff2_two_sum(cx, f2neg(sx), p.dx, ex);
+    ff2_two_sum(cy, f2neg(sy), p.dy, ey);
+    ff2_two_sum(cz, f2neg(sz), p.dz, ez);
+    const float2 qx = f2mul(p.dx, p.dx), rx = f2fma(p.dx, p.dx, f2neg(qx));
+    const float2 qy = f2mul(p.dy, p.dy), ry = f2fma(p.dy, p.dy, f2neg(qy));
+    const float2 qz = f2mul(p.dz, p.dz), rz = f2fma(p.dz, p.dz, f2neg(qz));
+    float2 s1, e1, s2, e2;
+    ff2_two_sum(qx, qy, s1, e1);
+    ff2_two_sum(s1, qz, s2, e2);
+    float2 lo = f2add(f2add(rx, ry), f2add(rz, f2add(e1, e2)));
+    lo = f2fma(f2add(p.dx, p.dx), ex, lo);
+    lo = f2fma(f2add(p.dy, p.dy), ey, lo);
+    lo = f2fma(f2add(p.dz, p.dz), ez, lo);
+    const float2 Sh = f2add(s2, lo);
+    const float2 Sl = f2sub(lo, f2sub(Sh, s2));
+    const float2 rs = make_float2(rsqrtf(Sh.x), rsqrtf(Sh.y));
+    p.dh = f2mul(Sh, rs);
+    const float2 res = f2add(f2fma(f2neg(p.dh), p.dh, Sh), Sl);
+    p.rd = rs;
+    p.dl = f2mul(f2mul(res, f2(0.5f)), rs);
+    return p;
+}
+
 // Offset of cell boundary j from the wave front: b_j = d - j h, evaluated as
 // (dh - j h_hi) + (dl - err(j h_hi) - j h_lo); the first difference is exact
 // when j h_hi lies within a factor of two of dh.
@@ -258,13 +320,13 @@ struct PairWindow {
     float b0, bL;
 };
 
-__device__ __forceinline__ bool sbp_window(const PairDist& pd, float R, const LevelGeo& g,
-                                           PairWindow& w) {
+__device__ __forceinline__ bool sbp_window_ff(float dh, float dl, float R, const LevelGeo& g,
+                                              PairWindow& w) {
     const float h = g.h_hi;
-    const float xr = pd.dh * g.inv_h;
-    if (!(xr < (float)g.Tk + 4096.0f) || !(pd.dh + pd.dl > R)) return false;  // also NaN
+    const float xr = dh * g.inv_h;
+    if (!(xr < (float)g.Tk + 4096.0f) || !(dh + dl > R)) return false;  // also NaN
     const int jr = (int)floorf(xr);
-    const float e = sbp_boundary(pd.dh, pd.dl, jr, g.h_hi, g.h_lo);  // b_jr
+    const float e = sbp_boundary(dh, dl, jr, g.h_hi, g.h_lo);  // b_jr
     const float tL = fminf(fmaxf((e - R) * g.inv_h, -1e6f), 1e6f);
     const float tH = fminf(fmaxf((e + R) * g.inv_h, -1e6f), 1e6f);
     int kL = (int)floorf(tL) + 1;
@@ -290,6 +352,11 @@ __device__ __forceinline__ bool sbp_window(const PairDist& pd, float R, const Le
     w.b0 = b0;
     w.bL = bL;
     return w.jH >= w.jL && w.jL >= 1 && w.jL - 1 < g.Tk;
+}
+
+__device__ __forceinline__ bool sbp_window(const PairDist& pd, float R, const LevelGeo& g,
+                                           PairWindow& w) {
+    return sbp_window_ff(pd.dh, pd.dl, R, g, w);
 }
 
 // Orientation weight and its switch (1 where d w / d c is non-zero).

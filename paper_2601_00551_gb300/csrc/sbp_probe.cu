@@ -28,6 +28,25 @@ __global__ void __launch_bounds__(kProbeThreads) probe_fma_kernel(float* out, fl
     if (s == 12345.678f) out[blockIdx.x] = s;  // practically never taken
 }
 
+// The same chains as packed pairs: one instruction performs two FP32 fused
+// multiply-adds on the two halves of a float2.
+__global__ void __launch_bounds__(kProbeThreads) probe_fma2_kernel(float* out, float a, float b) {
+    float2 v[kChains / 2];
+#pragma unroll
+    for (int c = 0; c < kChains / 2; ++c)
+        v[c] = make_float2((float)(threadIdx.x + 2 * c), (float)(threadIdx.x + 2 * c + 1));
+    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+#pragma unroll 4
+    for (int it = 0; it < kFmaIters; ++it) {
+#pragma unroll
+        for (int c = 0; c < kChains / 2; ++c) v[c] = __ffma2_rn(v[c], a2, b2);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < kChains / 2; ++c) s += v[c].x + v[c].y;
+    if (s == 12345.678f) out[blockIdx.x] = s;  // practically never taken
+}
+
 __global__ void __launch_bounds__(kProbeThreads) probe_issue_kernel(unsigned* out, unsigned a) {
     unsigned v[kChains];
 #pragma unroll
@@ -113,6 +132,25 @@ extern "C" int sbp_probe_fp32_fma(double* fma_per_s) {
             &ms))
         return e;
     sbp_count_launches(4);
+    *fma_per_s = (double)g_blocks * kProbeThreads * kFmaIters * kChains / (ms * 1e-3);
+    return SBP_OK;
+}
+
+extern "C" int sbp_probe_fp32x2_fma(double* fma_per_s) {
+    if (!fma_per_s) {
+        sbp_set_error("probe_fp32x2_fma: null pointer");
+        return SBP_ERR_ARG;
+    }
+    if (int e = probe_setup()) return e;
+    double ms = 0;
+    if (int e = time_launch(
+            [](cudaStream_t s) {
+                probe_fma2_kernel<<<g_blocks, kProbeThreads, 0, s>>>((float*)g_out, 0.999f, 1e-3f);
+            },
+            &ms))
+        return e;
+    sbp_count_launches(4);
+    // kChains / 2 packed instructions per iteration, two FMAs each
     *fma_per_s = (double)g_blocks * kProbeThreads * kFmaIters * kChains / (ms * 1e-3);
     return SBP_OK;
 }

@@ -113,6 +113,7 @@ _SIGS = {
     "sbp_autotune_frames": (ctypes.c_int, [_P, _Balls, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int)]),
     "sbp_probe_fp32_fma": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
+    "sbp_probe_fp32x2_fma": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "sbp_probe_issue": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "sbp_probe_smem_atomic": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "sbp_sync_status": (ctypes.c_int, [_P, _P]),
@@ -205,13 +206,16 @@ def launch_count() -> int:
 
 def probe_rates() -> dict:
     """Measured throughput of the units that bound the hot kernels
-    (include/slingbag_probe.h): FP32 FMA/s, warp instructions issued/s and
+    (include/slingbag_probe.h): FP32 FMA/s (single and packed-pair
+    instructions), warp instructions issued/s and
     shared-memory atomic adds/s (u32, u64, f32), on the current device."""
     lib = load_library()
     out = {}
     v = ctypes.c_double()
     _check("sbp_probe_fp32_fma", lib.sbp_probe_fp32_fma(ctypes.byref(v)))
     out["fp32_fma_per_s"] = v.value
+    _check("sbp_probe_fp32x2_fma", lib.sbp_probe_fp32x2_fma(ctypes.byref(v)))
+    out["fp32x2_fma_per_s"] = v.value
     _check("sbp_probe_issue", lib.sbp_probe_issue(ctypes.byref(v)))
     out["warp_inst_per_s"] = v.value
     for kind, name in enumerate(("u32", "u64", "f32")):
