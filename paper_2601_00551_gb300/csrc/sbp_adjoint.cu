@@ -262,8 +262,8 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
                 sbp_pair_distance2(f2(cx), f2(cy), f2(cz), make_float2(saA.x, saB.x),
                                    make_float2(saA.y, saB.y), make_float2(saA.z, saB.z));
             PairWindow wa, wb;
-            bool okA = sbp_window_ff(pd.dh.x, pd.dl.x, R, g, wa);
-            bool okB = sbp_window_ff(pd.dh.y, pd.dl.y, R, g, wb);
+            bool okA, okB;
+            sbp_window2(pd.dh, pd.dl, f2(R), g, wa, wb, okA, okB);
             if (!(okA || okB)) continue;
             const float2 ux = f2mul(pd.dx, pd.rd), uy = f2mul(pd.dy, pd.rd),
                          uz = f2mul(pd.dz, pd.rd);

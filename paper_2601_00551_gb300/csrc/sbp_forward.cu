@@ -239,8 +239,10 @@ fwd_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
                 okB = false;
             }
             PairWindow wa, wb;
-            okA = okA && sbp_window_ff(pd.dh.x, pd.dl.x, R2.x, g, wa);
-            okB = okB && sbp_window_ff(pd.dh.y, pd.dl.y, R2.y, g, wb);
+            bool wA, wB;
+            sbp_window2(pd.dh, pd.dl, R2, g, wa, wb, wA, wB);
+            okA = okA && wA;
+            okB = okB && wB;
             if (!(okA || okB)) continue;
             const float2 cosv = f2mul(
                 f2fma(f2(nx), pd.dx, f2fma(f2(ny), pd.dy, f2mul(f2(nz), pd.dz))), pd.rd);

@@ -359,6 +359,75 @@ __device__ __forceinline__ bool sbp_window(const PairDist& pd, float R, const Le
     return sbp_window_ff(pd.dh, pd.dl, R, g, w);
 }
 
+// sbp_window for two pairs. The arithmetic is that of sbp_window_ff, with
+// the cell indices carried as exact small integers in float (below 2^24) and
+// converted once at the end; the fix-ups of the two ends are selects. Pairs
+// whose window is not valid (ok = false) may carry any values.
+__device__ __forceinline__ void sbp_window2(float2 dh, float2 dl, float2 R, const LevelGeo& g,
+                                            PairWindow& wa, PairWindow& wb, bool& okA,
+                                            bool& okB) {
+    const float h = g.h_hi;
+    const float2 xr = f2mul(dh, f2(g.inv_h));
+    const float2 dd = f2add(dh, dl);
+    const float lim = (float)g.Tk + 4096.0f;
+    okA = xr.x < lim && dd.x > R.x;  // also false for NaN
+    okB = xr.y < lim && dd.y > R.y;
+    const float2 jr = make_float2(floorf(xr.x), floorf(xr.y));
+    // b_jr = (dh - jr h_hi) + (dl - err(jr h_hi) - jr h_lo)
+    const float2 p = f2mul(jr, f2(g.h_hi));
+    const float2 pe = f2fma(jr, f2(g.h_hi), f2neg(p));
+    const float2 e = f2add(f2sub(dh, p), f2sub(f2sub(dl, pe), f2mul(jr, f2(g.h_lo))));
+    const float2 tL = f2mul(f2sub(e, R), f2(g.inv_h));
+    const float2 tH = f2mul(f2add(e, R), f2(g.inv_h));
+    float2 kL = f2add(make_float2(floorf(tL.x), floorf(tL.y)), f2(1.0f));
+    float2 kH = f2add(make_float2(ceilf(tH.x), ceilf(tH.y)), f2(-1.0f));
+    float2 b0 = f2fma(kL, f2(-h), e);
+    float2 bL = f2fma(kH, f2(-h), e);
+    // exact fix-ups: b0 must satisfy b0 < R <= b0 + h, bL must satisfy bL - h <= -R < bL
+    const float2 b0p = f2add(b0, f2(h)), b0m = f2add(b0, f2(-h));
+    const float2 bLp = f2add(bL, f2(h)), bLm = f2add(bL, f2(-h));
+    const float2 nR = f2neg(R);
+    if (b0.x >= R.x) {
+        kL.x += 1.0f;
+        b0.x = b0m.x;
+    } else if (b0p.x < R.x) {
+        kL.x -= 1.0f;
+        b0.x = b0p.x;
+    }
+    if (b0.y >= R.y) {
+        kL.y += 1.0f;
+        b0.y = b0m.y;
+    } else if (b0p.y < R.y) {
+        kL.y -= 1.0f;
+        b0.y = b0p.y;
+    }
+    if (bL.x <= nR.x) {
+        kH.x -= 1.0f;
+        bL.x = bLp.x;
+    } else if (bLm.x > nR.x) {
+        kH.x += 1.0f;
+        bL.x = bLm.x;
+    }
+    if (bL.y <= nR.y) {
+        kH.y -= 1.0f;
+        bL.y = bLp.y;
+    } else if (bLm.y > nR.y) {
+        kH.y += 1.0f;
+        bL.y = bLm.y;
+    }
+    const float2 jL = f2add(jr, kL), jH = f2add(jr, kH);
+    okA = okA && jH.x >= jL.x && jL.x >= 1.0f && jL.x <= (float)g.Tk;
+    okB = okB && jH.y >= jL.y && jL.y >= 1.0f && jL.y <= (float)g.Tk;
+    wa.jL = __float2int_rz(jL.x);
+    wa.jH = __float2int_rz(jH.x);
+    wb.jL = __float2int_rz(jL.y);
+    wb.jH = __float2int_rz(jH.y);
+    wa.b0 = b0.x;
+    wa.bL = bL.x;
+    wb.b0 = b0.y;
+    wb.bL = bL.y;
+}
+
 // Orientation weight and its switch (1 where d w / d c is non-zero).
 __device__ __forceinline__ float sbp_weight(int wmode, float cosv, float& active) {
     if (wmode == SBP_W_NONE) {
