@@ -30,10 +30,12 @@
 //                 the shared buffer are covered in several passes.
 //                 A 64-bit shared atomic add costs several times a 32-bit one
 //                 on this GPU, so each int64 impulse v is added as two 32-bit
-//                 words: its low kLoBits bits (unsigned) and v >> kLoBits
-//                 (signed). Neither word can overflow within a CTA (at most
-//                 2 impulses per ball and cell, kChunk balls), and the flush
-//                 recombines them exactly.
+//                 words: v mod 2^32 and v >> kLoBits (signed). The high word
+//                 cannot overflow within a CTA, and the sum of the low
+//                 kLoBits-bit parts (at most 2 impulses per ball and cell,
+//                 kChunk balls) stays below 2^32, so the flush recovers it
+//                 from the first word and the high word and recombines the
+//                 sum exactly.
 //   fwd_finalize  CTA = one sensor; two block scans turn impulses into the
 //                 float32 trace and clear the accumulator row
 #include <algorithm>
@@ -84,14 +86,14 @@ __device__ __forceinline__ long long fwd_f2ll(float x) {
 // Adds the int64 impulse v to the split accumulator word pair at `lo` (the
 // high word sits kWindow * 32 words further on).
 __device__ __forceinline__ void fwd_add(unsigned int* lo, long long v) {
-    atomicAdd(lo, (unsigned int)v & ((1u << kLoBits) - 1u));
+    atomicAdd(lo, (unsigned int)v);
     atomicAdd(lo + kWindow * 32, (unsigned int)(int)(v >> kLoBits));
 }
 
 // The same for an impulse that fits in 32 bits (its arithmetic shift gives
 // the same high word as the 64-bit one).
 __device__ __forceinline__ void fwd_add32(unsigned int* lo, int v) {
-    atomicAdd(lo, (unsigned int)v & ((1u << kLoBits) - 1u));
+    atomicAdd(lo, (unsigned int)v);
     atomicAdd(lo + kWindow * 32, (unsigned int)(v >> kLoBits));
 }
 
@@ -271,9 +273,13 @@ fwd_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
         // of all 32 sensors), recombine the two halves and clear them
         const int used = min(wmax - p * kWindow, kWindow) * 32;
         for (int t = threadIdx.x; t < used; t += blockDim.x) {
-            const unsigned int lo = sacc[t];
+            const unsigned int wa = sacc[t];
             const int hi = (int)sacc[kWindow * 32 + t];
-            if (lo | (unsigned)hi) {
+            if (wa | (unsigned)hi) {
+                // the low word holds the whole sum mod 2^32; the sum of the
+                // low kLoBits-bit parts lies in [0, 2^32), so it is that word
+                // minus hi * 2^kLoBits, mod 2^32
+                const unsigned int lo = wa - ((unsigned int)hi << kLoBits);
                 const long long v = (long long)hi * (1LL << kLoBits) + (long long)lo;
                 const int ln = t & 31, rel = t >> 5;
                 const int j = s_jlo[ln] + p * kWindow + rel;
