@@ -411,11 +411,17 @@ def adj_ops_per_pair(mean_R, h):
 # the hot kernels at the 40 MHz level of the vessel workload, from one ncu
 # capture, valid while the kernel source is the one that was measured (its
 # SHA-256 prefix below); otherwise reported as null.
+# DRAM bytes (read + write) of one launch at the finest level, from one ncu
+# capture of the kernel (dram__bytes_read.sum + dram__bytes_write.sum). A
+# record holds only while the kernel's sources hash to the value it was
+# taken with; after any change the traffic is reported as null.
 NCU_TRAFFIC = {
-    "forward": {"source": "paper_2601_00551_gb300/csrc/sbp_forward.cu",
-                "sha256": "65a7f405b22e31ac", "bytes": 5.261056e6},
-    "adjoint": {"source": "paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
-                "sha256": "b1b496a7abf96ddb", "bytes": 3.729920e6},
+    "forward": {"sources": ["paper_2601_00551_gb300/csrc/sbp_forward.cu",
+                            "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
+                "sha256": "9a4cd47f3defc5b6", "bytes": 5.260800e6},
+    "adjoint": {"sources": ["paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
+                            "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
+                "sha256": "8a3f5b3bff1a9855", "bytes": 3.748864e6},
 }
 
 
@@ -425,12 +431,14 @@ def _traffic(name):
     rec = NCU_TRAFFIC[name]
     if not rec["sha256"] or rec["bytes"] is None:
         return None
+    m = hashlib.sha256()
     try:
-        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                m.update(f.read())
     except OSError:
         return None
-    return rec["bytes"] if sha == rec["sha256"] else None
+    return rec["bytes"] if m.hexdigest()[:16] == rec["sha256"] else None
 
 
 def roofline(fwd_ms, adj_ms, counts, M, clk, mean_R, h_fine, probes):
