@@ -25,21 +25,25 @@
 //   residual     G = 2 (S - y), L = sum (S - y)^2 (fixed-order last-block reduction)
 //   adj_group    A cluster of kAdjSplit CTAs shares one chunk of consecutive
 //                balls (one thread per ball) and splits the sensors between
-//                its CTAs. Each CTA walks its sensors in groups; for each
-//                group it stages, per
-//                sensor, the window of G that the chunk's bounding box can
-//                reach into shared memory ([sensor][cell], coalesced loads),
-//                and every thread loops over the group's sensors reading its
-//                pair's cells from there. A ball's five gradient components
-//                stay in its thread's registers across the CTA's sensors; the
-//                first CTA of the cluster then adds the other CTAs' partial
-//                sums through distributed shared memory, in rank order, and
-//                writes every ball's gradients exactly once. No atomics.
-//                Windows that do not fit (an unsorted cloud) are read from
-//                global memory instead.
+//                its CTAs. Each CTA walks its sensors in groups of 16. For
+//                each group it stages, per sensor, the window of G that the
+//                chunk's bounding box can reach into shared memory
+//                ([sensor][cell]) with asynchronous copies into one of two
+//                buffers, the next group's copies in flight while the
+//                current group is evaluated. Every thread takes the group's
+//                sensors two at a time, evaluating both pairs side by side
+//                in packed float2 arithmetic. A ball's five gradient
+//                components stay in its thread's registers across the CTA's
+//                sensors. The first CTA of the cluster then adds the other
+//                CTAs' partial sums through distributed shared memory, in
+//                rank order, and writes every ball's gradients exactly once.
+//                No atomics. Windows that do not fit (an unsorted cloud) are
+//                read from global memory instead.
 #include <cooperative_groups.h>
 
 #include <algorithm>
+
+#include <cuda_pipeline.h>
 
 #include "sbp_internal.cuh"
 
@@ -50,7 +54,9 @@ namespace {
 constexpr int kAdjThreads = 128;  // balls (threads) per adjoint CTA
 constexpr int kAdjSplit = 4;      // default CTAs per cluster, each taking 1/split of the sensors
 constexpr int kAdjGroup = 16;     // sensors staged per round
-constexpr int kAdjWindow = 256;   // cells per sensor staged in shared memory
+constexpr int kAdjWindow = 224;   // cells per sensor staged in shared memory
+constexpr int kAdjWindowP0 = 128; // the same for the p0-only adjoint, which keeps more CTAs per SM
+constexpr int kAdjMeta = 128;     // sensors whose set-up is held in shared memory at once
 
 __global__ void downsample_kernel(const float* __restrict__ y, int M, int T, int f, int Tk,
                                   float* __restrict__ yk) {
@@ -110,9 +116,6 @@ struct GradOut {
     float* o[5];  // x, y, z, R, p0
 };
 
-// P0_ONLY: only dL/dp0 is wanted (the zero-gradient pass), so the chain rule
-// for R and the centre is skipped.
-// Launched with a cluster of gridDim.y CTAs along y (cudaLaunchKernelEx).
 // Window sums of one pair against the residual row of its sensor: the first
 // cell gf = G[jL-1], the last cell gl = G[jH] (0 past the record) and, with
 // d_q = G[jL+q] - gl over the L = min(jH, Tk) - jL ramp cells,
@@ -157,17 +160,24 @@ __device__ __forceinline__ void adj_window_sums(const float* __restrict__ sGrow,
     }
 }
 
+// P0_ONLY: only dL/dp0 is wanted (the zero-gradient pass), so the chain rule
+// for R and the centre is skipped.
+// Launched with a cluster of gridDim.y CTAs along y (cudaLaunchKernelEx).
 template <bool P0_ONLY>
 __global__ void __launch_bounds__(kAdjThreads, P0_ONLY ? 8 : 6)
 adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, LevelGeo g,
                  const float* __restrict__ G_all, unsigned mask, GradOut out) {
-    __shared__ float sG[kAdjGroup * kAdjWindow];  // [sensor][cell]
-    __shared__ float4 s_sa[kAdjGroup];            // sx, sy, sz, nx
-    __shared__ float4 s_sb[kAdjGroup];            // ny, nz, jlo, len (as int bits)
+    // two staging buffers [sensor][cell]; after the last group the first one
+    // holds this CTA's partial sums
+    constexpr int kWin = P0_ONLY ? kAdjWindowP0 : kAdjWindow;
+    __shared__ __align__(16) float sG[2][kAdjGroup * kWin];
+    __shared__ float4 s_sa[kAdjMeta + 1];  // sx, sy, sz, nx (+1: partner of an odd last sensor)
+    __shared__ float4 s_sb[kAdjMeta + 1];  // ny, nz, jlo, len (as int bits)
+    __shared__ int s_glen[kAdjMeta / kAdjGroup];  // longest window of each group
     __shared__ float s_red[(kAdjThreads / 32) * 7];
     __shared__ float s_box[7];
-    __shared__ int s_lmax;
-    __shared__ float s_part[kAdjThreads * 5];  // this CTA's partial sums
+    float* const s_part = sG[0];  // this CTA's partial sums, [ball][5]
+    static_assert(kAdjThreads * 5 <= kAdjGroup * kWin, "partials do not fit");
     cg::cluster_group cluster = cg::this_cluster();
     const int c0 = blockIdx.x * kAdjThreads;
     const FrameSlot fs = sbp_frame_of(ft, c0);
@@ -222,135 +232,164 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     const int split = (int)gridDim.y;  // one cluster spans all of y
     const int per = ((M + split - 1) / split + kAdjGroup - 1) / kAdjGroup * kAdjGroup;
     const int m_begin = min(M, part * per), m_end = min(M, m_begin + per);
-    for (int m0 = m_begin; m0 < m_end; m0 += kAdjGroup) {
-        const int cnt = min(kAdjGroup, m_end - m0);
-        __syncthreads();  // the previous group is done with the shared buffers
-        if (threadIdx.x == 0) s_lmax = 0;
+    // The share is walked in blocks of up to kAdjMeta sensors whose positions,
+    // normals and cell ranges are set up once, and within a block in groups of
+    // kAdjGroup sensors. The residual windows of group q + 1 are copied into
+    // the other staging buffer asynchronously while group q is evaluated, so
+    // one barrier per group both publishes a group and frees the buffer of
+    // the group before.
+    for (int mb = m_begin; mb < m_end; mb += kAdjMeta) {
+        const int nsens = min(kAdjMeta, m_end - mb);
+        const int ng = (nsens + kAdjGroup - 1) / kAdjGroup;
+        __syncthreads();  // the previous block is done with every shared buffer
+        for (int t = threadIdx.x; t < ng; t += blockDim.x) s_glen[t] = 0;
         __syncthreads();
-        if (threadIdx.x < cnt) {
-            const int m = m0 + threadIdx.x;
+        for (int t = threadIdx.x; t < nsens; t += blockDim.x) {
+            const int m = mb + t;
             const float sx = sens[m], sy = sens[M + m], sz = sens[2 * M + m];
             int jlo, jhi;
             sbp_box_cells(sx, sy, sz, s_box, g, jlo, jhi);
             const int len = max(0, jhi - jlo + 1);
-            s_sa[threadIdx.x] = make_float4(sx, sy, sz, sens[3 * M + m]);
-            s_sb[threadIdx.x] = make_float4(sens[4 * M + m], sens[5 * M + m], __int_as_float(jlo),
-                                            __int_as_float(len));
-            atomicMax(&s_lmax, len);
+            s_sa[t] = make_float4(sx, sy, sz, sens[3 * M + m]);
+            s_sb[t] = make_float4(sens[4 * M + m], sens[5 * M + m], __int_as_float(jlo),
+                                  __int_as_float(len));
+            atomicMax(&s_glen[t / kAdjGroup], len);
         }
-        if ((cnt & 1) && threadIdx.x == cnt) {  // odd group: a partner that no ball reaches
-            s_sa[cnt] = make_float4(1e6f, 1e6f, 1e6f, 0.0f);
-            s_sb[cnt] = make_float4(0.0f, 1.0f, __int_as_float(0), __int_as_float(0));
+        if ((nsens & 1) && threadIdx.x == 0) {  // odd count: a partner that no ball reaches
+            s_sa[nsens] = make_float4(1e6f, 1e6f, 1e6f, 0.0f);
+            s_sb[nsens] = make_float4(0.0f, 1.0f, __int_as_float(0), __int_as_float(0));
         }
         __syncthreads();
-        const bool staged = s_lmax <= kAdjWindow;  // uniform
-        if (staged) {
-            for (int s = 0; s < cnt; ++s) {
-                const float4 sb = s_sb[s];
+        // asynchronous copy of group q's windows into buffer q & 1 (skipped
+        // for a group whose longest window does not fit: it reads L2 instead)
+        auto stage = [&](int q) {
+            if (s_glen[q] > kWin) return;
+            const int gb = q * kAdjGroup, cntq = min(kAdjGroup, nsens - gb);
+            float* dst = sG[q & 1];
+            for (int s = 0; s < cntq; ++s) {
+                const float4 sb = s_sb[gb + s];
                 const int jlo = __float_as_int(sb.z), len = __float_as_int(sb.w);
-                const float* row = G + (size_t)(m0 + s) * Tk + jlo;
-                for (int r = threadIdx.x; r < len; r += blockDim.x) sG[s * kAdjWindow + r] = row[r];
+                const float* row = G + (size_t)(mb + gb + s) * Tk + jlo;
+                for (int r = threadIdx.x; r < len; r += blockDim.x)
+                    __pipeline_memcpy_async(dst + s * kWin + r, row + r, sizeof(float));
             }
-            __syncthreads();
-        }
-        if (!valid) continue;
-        // two sensors at a time, evaluated side by side in the halves of float2
+        };
+        stage(0);
+        __pipeline_commit();
+        for (int q = 0; q < ng; ++q) {
+            __pipeline_wait_prior(0);  // this thread's copies of group q have landed
+            __syncthreads();  // ... everyone's; and group q - 1 is no longer read
+            if (q + 1 < ng) {
+                stage(q + 1);
+                __pipeline_commit();
+            }
+            const int gbase = q * kAdjGroup;
+            const int cnt = min(kAdjGroup, nsens - gbase);
+            const int m0 = mb + gbase;
+            const bool staged = s_glen[q] <= kWin;  // uniform
+            const float4* __restrict__ sa_g = s_sa + gbase;
+            const float4* __restrict__ sb_g = s_sb + gbase;
+            const float* __restrict__ sGb = sG[q & 1];
+            if (!valid) continue;
+            // two sensors at a time, evaluated side by side in the halves of float2
 #pragma unroll 1
-        for (int s = 0; s < cnt; s += 2) {
-            const float4 saA = s_sa[s], sbA = s_sb[s], saB = s_sa[s + 1], sbB = s_sb[s + 1];
-            const PairDist2 pd =
-                sbp_pair_distance2(f2(cx), f2(cy), f2(cz), make_float2(saA.x, saB.x),
-                                   make_float2(saA.y, saB.y), make_float2(saA.z, saB.z));
-            PairWindow wa, wb;
-            bool okA, okB;
-            sbp_window2(pd.dh, pd.dl, f2(R), g, wa, wb, okA, okB);
-            if (!(okA || okB)) continue;
-            const float2 ux = f2mul(pd.dx, pd.rd), uy = f2mul(pd.dy, pd.rd),
-                         uz = f2mul(pd.dz, pd.rd);
-            const float2 nx = make_float2(saA.w, saB.w), ny = make_float2(sbA.x, sbB.x),
-                         nz = make_float2(sbA.y, sbB.y);
-            const float2 cosv = f2fma(nx, ux, f2fma(ny, uy, f2mul(nz, uz)));
-            float actA, actB;
-            float wA = sbp_weight(g.wmode, cosv.x, actA), wB = sbp_weight(g.wmode, cosv.y, actB);
-            okA = okA && !(wA == 0.0f && actA == 0.0f);
-            okB = okB && !(wB == 0.0f && actB == 0.0f);
-            if (!(okA || okB)) continue;
-            // window sums; a pair that does not count gets zeros, so that its
-            // half contributes exactly nothing below
-            const int jloA = __float_as_int(sbA.z), lenA = __float_as_int(sbA.w);
-            const int jloB = __float_as_int(sbB.z), lenB = __float_as_int(sbB.w);
-            float2 gf = f2(0.f), gl = f2(0.f), E0 = f2(0.f), E1 = f2(0.f);
-            const int LA = min(wa.jH, Tk) - wa.jL, LB = min(wb.jH, Tk) - wb.jL;
-            // side by side when both windows are staged and differ by at most
-            // one ramp cell: the shorter one then reads one cell further, its
-            // own last cell G[jH] (inside the record), which adds d = 0
-            const bool inA = okA && staged && wa.jL - 1 >= jloA && min(wa.jH, Tk - 1) - jloA < lenA;
-            const bool inB = okB && staged && wb.jL - 1 >= jloB && min(wb.jH, Tk - 1) - jloB < lenB;
-            if (inA && inB && abs(LA - LB) <= 1 && (LA >= LB || wa.jH < Tk) &&
-                (LB >= LA || wb.jH < Tk)) {
-                const float* GwA = sG + s * kAdjWindow - jloA + wa.jL;
-                const float* GwB = sG + (s + 1) * kAdjWindow - jloB + wb.jL;
-                gf = make_float2(GwA[-1], GwB[-1]);
-                gl = make_float2(wa.jH < Tk ? GwA[wa.jH - wa.jL] : 0.0f,
-                                 wb.jH < Tk ? GwB[wb.jH - wb.jL] : 0.0f);
-                const float2 ngl = f2neg(gl);
-                const int Lm = max(LA, LB);
-                float2 run = f2(0.f);
-                int q = Lm - 1;
-                for (; q >= 2; q -= 2) {
-                    const float2 d1 = f2add(make_float2(GwA[q], GwB[q]), ngl);
-                    const float2 d0 = f2add(make_float2(GwA[q - 1], GwB[q - 1]), ngl);
-                    run = f2add(run, d1);
-                    E1 = f2add(E1, run);
-                    run = f2add(run, d0);
-                    E1 = f2add(E1, run);
+            for (int s = 0; s < cnt; s += 2) {
+                const float4 saA = sa_g[s], sbA = sb_g[s], saB = sa_g[s + 1], sbB = sb_g[s + 1];
+                const PairDist2 pd =
+                    sbp_pair_distance2(f2(cx), f2(cy), f2(cz), make_float2(saA.x, saB.x),
+                                       make_float2(saA.y, saB.y), make_float2(saA.z, saB.z));
+                PairWindow wa, wb;
+                bool okA, okB;
+                sbp_window2(pd.dh, pd.dl, f2(R), g, wa, wb, okA, okB);
+                if (!(okA || okB)) continue;
+                const float2 ux = f2mul(pd.dx, pd.rd), uy = f2mul(pd.dy, pd.rd),
+                             uz = f2mul(pd.dz, pd.rd);
+                const float2 nx = make_float2(saA.w, saB.w), ny = make_float2(sbA.x, sbB.x),
+                             nz = make_float2(sbA.y, sbB.y);
+                const float2 cosv = f2fma(nx, ux, f2fma(ny, uy, f2mul(nz, uz)));
+                float actA, actB;
+                float wA = sbp_weight(g.wmode, cosv.x, actA), wB = sbp_weight(g.wmode, cosv.y, actB);
+                okA = okA && !(wA == 0.0f && actA == 0.0f);
+                okB = okB && !(wB == 0.0f && actB == 0.0f);
+                if (!(okA || okB)) continue;
+                // window sums; a pair that does not count gets zeros, so that its
+                // half contributes exactly nothing below
+                const int jloA = __float_as_int(sbA.z), lenA = __float_as_int(sbA.w);
+                const int jloB = __float_as_int(sbB.z), lenB = __float_as_int(sbB.w);
+                float2 gf = f2(0.f), gl = f2(0.f), E0 = f2(0.f), E1 = f2(0.f);
+                const int LA = min(wa.jH, Tk) - wa.jL, LB = min(wb.jH, Tk) - wb.jL;
+                // side by side when both windows are staged and differ by at most
+                // one ramp cell: the shorter one then reads one cell further, its
+                // own last cell G[jH] (inside the record), which adds d = 0
+                const bool inA = okA && staged && wa.jL - 1 >= jloA && min(wa.jH, Tk - 1) - jloA < lenA;
+                const bool inB = okB && staged && wb.jL - 1 >= jloB && min(wb.jH, Tk - 1) - jloB < lenB;
+                if (inA && inB && abs(LA - LB) <= 1 && (LA >= LB || wa.jH < Tk) &&
+                    (LB >= LA || wb.jH < Tk)) {
+                    const float* GwA = sGb + s * kWin - jloA + wa.jL;
+                    const float* GwB = sGb + (s + 1) * kWin - jloB + wb.jL;
+                    gf = make_float2(GwA[-1], GwB[-1]);
+                    gl = make_float2(wa.jH < Tk ? GwA[wa.jH - wa.jL] : 0.0f,
+                                     wb.jH < Tk ? GwB[wb.jH - wb.jL] : 0.0f);
+                    const float2 ngl = f2neg(gl);
+                    const int Lm = max(LA, LB);
+                    float2 run = f2(0.f);
+                    int q = Lm - 1;
+                    for (; q >= 2; q -= 2) {
+                        const float2 d1 = f2add(make_float2(GwA[q], GwB[q]), ngl);
+                        const float2 d0 = f2add(make_float2(GwA[q - 1], GwB[q - 1]), ngl);
+                        run = f2add(run, d1);
+                        E1 = f2add(E1, run);
+                        run = f2add(run, d0);
+                        E1 = f2add(E1, run);
+                    }
+                    if (q == 1) {
+                        run = f2add(run, f2add(make_float2(GwA[1], GwB[1]), ngl));
+                        E1 = f2add(E1, run);
+                    }
+                    if (Lm > 0) E0 = f2add(run, f2add(make_float2(GwA[0], GwB[0]), ngl));
+                } else {
+                    if (okA)
+                        adj_window_sums(sGb + s * kWin, jloA, lenA, staged,
+                                        G + (size_t)(m0 + s) * Tk, wa.jL, wa.jH, Tk, gf.x, gl.x, E0.x,
+                                        E1.x);
+                    if (okB)
+                        adj_window_sums(sGb + (s + 1) * kWin, jloB, lenB, staged,
+                                        G + (size_t)(m0 + s + 1) * Tk, wb.jL, wb.jH, Tk, gf.y, gl.y,
+                                        E0.y, E1.y);
                 }
-                if (q == 1) {
-                    run = f2add(run, f2add(make_float2(GwA[1], GwB[1]), ngl));
-                    E1 = f2add(E1, run);
+                if (!okA) {
+                    wA = 0.0f;
+                    actA = 0.0f;
                 }
-                if (Lm > 0) E0 = f2add(run, f2add(make_float2(GwA[0], GwB[0]), ngl));
-            } else {
-                if (okA)
-                    adj_window_sums(sG + s * kAdjWindow, jloA, lenA, staged,
-                                    G + (size_t)(m0 + s) * Tk, wa.jL, wa.jH, Tk, gf.x, gl.x, E0.x,
-                                    E1.x);
-                if (okB)
-                    adj_window_sums(sG + (s + 1) * kAdjWindow, jloB, lenB, staged,
-                                    G + (size_t)(m0 + s + 1) * Tk, wb.jL, wb.jH, Tk, gf.y, gl.y,
-                                    E0.y, E1.y);
+                if (!okB) {
+                    wB = 0.0f;
+                    actB = 0.0f;
+                }
+                const float2 b0 = make_float2(okA ? wa.b0 : 0.0f, okB ? wb.b0 : 0.0f);
+                const float2 Df = f2sub(gf, gl);
+                const float2 ra = make_float2(fmaxf(R - b0.x, 0.0f), fmaxf(R - b0.y, 0.0f));
+                const float2 A = f2fma(f2mul(Df, ra), f2add(f2(R), b0),
+                                       f2fma(f2mul(E0, f2(h)), f2fma(f2(2.0f), b0, f2(-h)),
+                                             f2mul(f2(-hh2), E1)));
+                const float2 qd = f2mul(f2(g.inv_4h), pd.rd);  // 1 / (4 d h)
+                const float2 K0 = f2mul(make_float2(wA, wB), qd);
+                gp2 = f2fma(K0, A, gp2);
+                if (P0_ONLY) continue;
+                const float2 Bh = f2fma(f2(h), E0, f2neg(f2mul(b0, Df)));
+                const float2 pK = f2mul(f2(p0), K0);
+                gR2 = f2fma(f2mul(pK, f2(2.0f * R)), Df, gR2);
+                const float2 gd = f2mul(pK, f2fma(f2(2.0f), Bh, f2neg(f2mul(A, pd.rd))));
+                const float2 gw = f2mul(f2mul(f2mul(f2(p0), A), qd), make_float2(actA, actB));
+                const float2 gwr = f2mul(gw, pd.rd);
+                gx2 = f2fma(gd, ux, f2fma(gwr, f2fma(f2neg(cosv), ux, nx), gx2));
+                gy2 = f2fma(gd, uy, f2fma(gwr, f2fma(f2neg(cosv), uy, ny), gy2));
+                gz2 = f2fma(gd, uz, f2fma(gwr, f2fma(f2neg(cosv), uz, nz), gz2));
             }
-            if (!okA) {
-                wA = 0.0f;
-                actA = 0.0f;
-            }
-            if (!okB) {
-                wB = 0.0f;
-                actB = 0.0f;
-            }
-            const float2 b0 = make_float2(okA ? wa.b0 : 0.0f, okB ? wb.b0 : 0.0f);
-            const float2 Df = f2sub(gf, gl);
-            const float2 ra = make_float2(fmaxf(R - b0.x, 0.0f), fmaxf(R - b0.y, 0.0f));
-            const float2 A = f2fma(f2mul(Df, ra), f2add(f2(R), b0),
-                                   f2fma(f2mul(E0, f2(h)), f2fma(f2(2.0f), b0, f2(-h)),
-                                         f2mul(f2(-hh2), E1)));
-            const float2 qd = f2mul(f2(g.inv_4h), pd.rd);  // 1 / (4 d h)
-            const float2 K0 = f2mul(make_float2(wA, wB), qd);
-            gp2 = f2fma(K0, A, gp2);
-            if (P0_ONLY) continue;
-            const float2 Bh = f2fma(f2(h), E0, f2neg(f2mul(b0, Df)));
-            const float2 pK = f2mul(f2(p0), K0);
-            gR2 = f2fma(f2mul(pK, f2(2.0f * R)), Df, gR2);
-            const float2 gd = f2mul(pK, f2fma(f2(2.0f), Bh, f2neg(f2mul(A, pd.rd))));
-            const float2 gw = f2mul(f2mul(f2mul(f2(p0), A), qd), make_float2(actA, actB));
-            const float2 gwr = f2mul(gw, pd.rd);
-            gx2 = f2fma(gd, ux, f2fma(gwr, f2fma(f2neg(cosv), ux, nx), gx2));
-            gy2 = f2fma(gd, uy, f2fma(gwr, f2fma(f2neg(cosv), uy, ny), gy2));
-            gz2 = f2fma(gd, uz, f2fma(gwr, f2fma(f2neg(cosv), uz, nz), gz2));
         }
     }
     const float gx = gx2.x + gx2.y, gy = gy2.x + gy2.y, gz = gz2.x + gz2.y;
     const float gR = gR2.x + gR2.y, gp = gp2.x + gp2.y;
+    __syncthreads();  // every group is done with the staging buffers
     if (valid) {  // stored under the ball's chunk-local index
         s_part[li * 5 + 0] = gx;
         s_part[li * 5 + 1] = gy;
