@@ -16,7 +16,10 @@ with T = 1024 / 2048 / 4096):
 The pairs of a step are sum over the three iterations of n_k x M, with n_k
 the live ball count entering iteration k (the zero-gradient pass is extra
 work and is not counted). L2 is flushed (a 512 MB write) before every timed
-step. `value` times the step with inputs resident in device memory;
+step. `value` times the step with inputs resident in device memory, the
+step's launches replayed from a CUDA graph captured once (the same kernels
+in the same order; `eager` gives the same step launched call by call, and
+the per-kernel times and the roofline come from that eager pass);
 `e2e` times the same step through sbp_reconstruct with the cloud and the
 measured traces copied from pinned host memory and the result copied back
 inside the timed region.
@@ -324,7 +327,6 @@ def run_native(args, rank, world, local):
     torch.cuda.synchronize()
     barrier()
     launches = sb.launch_count() - launches0
-    clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in times]
     total_s = sum(step_ms) / 1e3
     if not np.array_equal(n_log.cpu().numpy(), counts):
@@ -333,6 +335,42 @@ def run_native(args, rank, world, local):
         raise RuntimeError("device status latched during the timed steps")
     max_s, all_pairs = aggregate(total_s, pairs_per_step * args.steps)
     value = all_pairs / max_s
+
+    # the same step replayed from a CUDA graph (one launch per step from the
+    # host; the kernels and their order are unchanged)
+    graph = None
+    if not args.profile:
+        try:
+            g = torch.cuda.CUDAGraph()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g):
+                step(False)
+            gt = []
+            for it in range(max(3, args.warmup) + args.steps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                g.replay()
+                b.record(stream)
+                if it >= max(3, args.warmup):
+                    gt.append((a, b))
+            torch.cuda.synchronize()
+            if not np.array_equal(n_log.cpu().numpy(), counts) or arr.sync_status() != 0:
+                raise RuntimeError("graph replay changed the step's ball counts")
+            g_ms = statistics.mean(a.elapsed_time(b) for a, b in gt)
+            g_max_s, _ = aggregate(g_ms * 1e-3 * args.steps, pairs_per_step * args.steps)
+            graph = {"ms_per_step": g_max_s * 1e3 / args.steps,
+                     "value": all_pairs / g_max_s}
+            del g
+        except Exception as exc:  # the eager measurement stands on its own
+            graph = {"error": f"{type(exc).__name__}: {exc}"}
+    clk = clocks.stop()
+    eager = {"ms_per_step": max_s * 1e3 / args.steps, "value": value}
+    launch_mode = "eager"
+    if graph is not None and "value" in graph:
+        value, max_s, launch_mode = graph["value"], graph["ms_per_step"] * 1e-3 * args.steps, \
+            "cuda_graph"
 
     # per-call device times of the hot kernels, over the timed region
     def per_level(name):
@@ -355,6 +393,7 @@ def run_native(args, rank, world, local):
             "pairs_per_step": pairs_per_step,
             "l2": "flushed before every timed step (512 MB write)",
             "parallelism": f"replicas x{world}",
+            "launch": launch_mode,
         },
         "gpu_launches": int(launches),
         "kernel_ms": {"forward": {str(k): v for k, v in fwd_ms.items()},
@@ -363,6 +402,9 @@ def run_native(args, rank, world, local):
     }
     if clk is not None:
         result["clocks"] = clk
+    result["eager"] = eager
+    if graph is not None:
+        result["graph_replay"] = graph
     probes = None
     if not args.profile:
         try:

@@ -42,6 +42,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cstdint>
 
 #include <cuda_pipeline.h>
 
@@ -74,29 +75,73 @@ __global__ void downsample_kernel(const float* __restrict__ y, int M, int T, int
     }
 }
 
+// Sum of squares in float-float: hi + lo carries sum r^2 with the rounding
+// error of every product and addition (relative error ~n 2^-48), so the
+// per-thread sums need no double-precision arithmetic per element.
+__device__ __forceinline__ void sq_acc(float r, float& hi, float& lo) {
+    const float p = r * r;
+    const float pe = fmaf(r, r, -p);
+    float s, e;
+    ff_two_sum(hi, p, s, e);
+    hi = s;
+    lo += e + pe;
+}
+
+// G = 2 (S - y) (S may be null: S = 0) and this thread's share of
+// sum (S - y)^2 over [0, n), four elements per load when vec is set (then
+// n is a multiple of 4 and the three arrays 16-byte aligned).
+__device__ __forceinline__ void residual_span(const float* __restrict__ S,
+                                              const float* __restrict__ y, float* __restrict__ G,
+                                              long long n, bool vec, long long t0,
+                                              long long stride, float& hi, float& lo) {
+    if (vec) {
+        const float4* y4 = reinterpret_cast<const float4*>(y);
+        const float4* S4 = reinterpret_cast<const float4*>(S);
+        float4* G4 = reinterpret_cast<float4*>(G);
+        for (long long t = t0; t < n / 4; t += stride) {
+            const float4 yv = y4[t];
+            const float4 sv = S ? S4[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 r = make_float4(sv.x - yv.x, sv.y - yv.y, sv.z - yv.z, sv.w - yv.w);
+            if (G) G4[t] = make_float4(2.0f * r.x, 2.0f * r.y, 2.0f * r.z, 2.0f * r.w);
+            sq_acc(r.x, hi, lo);
+            sq_acc(r.y, hi, lo);
+            sq_acc(r.z, hi, lo);
+            sq_acc(r.w, hi, lo);
+        }
+        return;
+    }
+    for (long long t = t0; t < n; t += stride) {
+        const float r = (S ? S[t] : 0.0f) - y[t];
+        if (G) G[t] = 2.0f * r;
+        sq_acc(r, hi, lo);
+    }
+}
+
+__device__ __forceinline__ double block_sum(double v, double* warp_sum) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double b = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (blockDim.x + 31) / 32; ++w) b += warp_sum[w];
+    return b;  // valid in thread 0
+}
+
 // G = 2 (S - y); per-block sums of (S - y)^2 in double; the last block to
 // finish adds the block sums in index order.
 __global__ void residual_kernel(const float* __restrict__ S, const float* __restrict__ y,
-                                float* __restrict__ G, long long total,
+                                float* __restrict__ G, long long total, bool vec,
                                 double* __restrict__ partials, SbpDevState* st,
                                 double* loss) {
     __shared__ double warp_sum[32];
     __shared__ bool is_last;
-    double acc = 0.0;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const float r = (S ? S[t] : 0.0f) - y[t];
-        G[t] = 2.0f * r;
-        acc += (double)r * (double)r;
-    }
+    float hi = 0.f, lo = 0.f;
+    residual_span(S, y, G, total, vec, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                  (long long)gridDim.x * blockDim.x, hi, lo);
     if (!loss) return;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = acc;
-    __syncthreads();
+    const double b = block_sum((double)hi + (double)lo, warp_sum);
     if (threadIdx.x == 0) {
-        double b = 0.0;
-        for (int w = 0; w < (blockDim.x + 31) / 32; ++w) b += warp_sum[w];
         partials[blockIdx.x] = b;
         __threadfence();
         const unsigned int tk = atomicAdd(&st->loss_ticket, 1u);
@@ -443,13 +488,24 @@ int sbp_launch_downsample_rows(sbp_array_s* a, int k, int rows, const float* y_f
     return sbp_cuda_check(cudaGetLastError(), "downsample launch") ? SBP_ERR_CUDA : SBP_OK;
 }
 
+namespace {
+
+// The four-wide path needs n % 4 == 0 and 16-byte aligned arrays.
+bool residual_vec(const float* S, const float* y, const float* G, long long n) {
+    auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    return n % 4 == 0 && al(y) && (!S || al(S)) && (!G || al(G));
+}
+
+}  // namespace
+
 int sbp_launch_residual(sbp_array_s* a, const float* S, const float* y, float* G,
                         double* loss, cudaStream_t st) {
     const int Tk = sbp_level_T(a, a->level);
     const long long total = (long long)a->M * Tk;
+    const bool vec = residual_vec(S, y, G, total);
     const int blocks = (int)std::max<long long>(
-        1, std::min<long long>(a->loss_blocks, (total + 255) / 256));
-    residual_kernel<<<blocks, 256, 0, st>>>(S, y, G, total, a->d_lossp, a->d_state, loss);
+        1, std::min<long long>(a->loss_blocks, (total / (vec ? 4 : 1) + 255) / 256));
+    residual_kernel<<<blocks, 256, 0, st>>>(S, y, G, total, vec, a->d_lossp, a->d_state, loss);
     sbp_count_launches(1);
     return sbp_cuda_check(cudaGetLastError(), "residual launch") ? SBP_ERR_CUDA : SBP_OK;
 }
@@ -516,27 +572,21 @@ namespace {
 
 // Per-frame sums of (S - y)^2: block partials, then one thread per frame adds
 // them in block order (reproducible).
+// Frame f = blockIdx.y: G = 2 (S - y) over the frame and, when partials is
+// set, this block's sum of (S - y)^2 into partials[f][blockIdx.x].
 __global__ void frame_loss_partial_kernel(const float* __restrict__ S, const float* __restrict__ y,
-                                          long long per_frame, double* __restrict__ partials) {
+                                          float* __restrict__ G, long long per_frame, bool vec,
+                                          double* __restrict__ partials) {
     __shared__ double warp_sum[32];
     const int f = blockIdx.y;
-    const float* Sf = S + (size_t)f * per_frame;
-    const float* yf = y + (size_t)f * per_frame;
-    double acc = 0.0;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < per_frame;
-         t += (long long)gridDim.x * blockDim.x) {
-        const float r = (Sf ? Sf[t] : 0.0f) - yf[t];
-        acc += (double)r * (double)r;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double bsum = 0.0;
-        for (int w = 0; w < (blockDim.x + 31) / 32; ++w) bsum += warp_sum[w];
-        partials[(size_t)f * gridDim.x + blockIdx.x] = bsum;
-    }
+    const size_t o = (size_t)f * per_frame;
+    float hi = 0.f, lo = 0.f;
+    residual_span(S ? S + o : nullptr, y + o, G ? G + o : nullptr, per_frame, vec,
+                  blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                  (long long)gridDim.x * blockDim.x, hi, lo);
+    if (!partials) return;
+    const double b = block_sum((double)hi + (double)lo, warp_sum);
+    if (threadIdx.x == 0) partials[(size_t)f * gridDim.x + blockIdx.x] = b;
 }
 
 __global__ void frame_loss_final_kernel(const double* __restrict__ partials, int blocks, int F,
@@ -555,18 +605,19 @@ int sbp_launch_residual_frames(sbp_array_s* a, const float* S, const float* y, f
                                double* loss, cudaStream_t st) {
     const int Tk = sbp_level_T(a, a->level);
     const long long per = (long long)a->M * Tk;
-    const long long total = per * a->frames;
-    const int blocks = (int)std::max<long long>(
-        1, std::min<long long>(a->loss_blocks, (total + 255) / 256));
-    residual_kernel<<<blocks, 256, 0, st>>>(S, y, G, total, a->d_lossp, a->d_state, nullptr);
+    const bool vec = residual_vec(S, y, G, per);  // per % 4 == 0 keeps every frame aligned
+    // blocks per frame: enough to fill the GPU, at most the 16 partials a frame has room for
+    const int fb = (int)std::max<long long>(
+        1, std::min<long long>(
+               {16LL, (4LL * a->sm_count + a->frames - 1) / a->frames,
+                (per / (vec ? 4 : 1) + 255) / 256}));
+    frame_loss_partial_kernel<<<dim3(fb, a->frames), 256, 0, st>>>(
+        S, y, G, per, vec, loss ? a->d_frame_lossp : nullptr);
     int launched = 1;
     if (loss) {
-        const int fb = 16;
-        frame_loss_partial_kernel<<<dim3(fb, a->frames), 256, 0, st>>>(S, y, per,
-                                                                       a->d_frame_lossp);
         frame_loss_final_kernel<<<(a->frames + 127) / 128, 128, 0, st>>>(a->d_frame_lossp, fb,
                                                                           a->frames, loss);
-        launched += 2;
+        launched += 1;
     }
     sbp_count_launches(launched);
     return sbp_cuda_check(cudaGetLastError(), "residual_frames launch") ? SBP_ERR_CUDA : SBP_OK;
