@@ -435,13 +435,13 @@ def run_native(args, rank, world, local):
 # Thread-level arithmetic operations per pair of the two hot kernels, counted
 # from the per-pair code of the algorithm (FP32 and integer arithmetic,
 # compares and conversions; loads, stores, branches and loop control are not
-# counted). Forward: exact distance 52, inside test 2, window 45, weight 6,
-# K 4, coefficients 15, range test 11, conversions 4, impulses 11, 32-bit
-# split 12, bounds and addresses 8, shared atomics 12. Adjoint: distance 52,
-# window 45, direction and weight 8, tests and bounds 11, chain rule 40, plus
-# the window sums: 3 operations per ramp cell beyond the first and 2 more,
-# with L = 2 R / h cells on average.
-FWD_OPS_PER_PAIR = 182
+# counted; a packed two-pair instruction counts once per pair). Forward: exact
+# distance 55, inside test 2, window 42, weight 6, K 3, coefficients 15, range
+# test 11, conversions 4, impulses 11, high words 6, bounds and addresses 8,
+# shared atomics 12. Adjoint: distance 55, window 42, direction and weight 8,
+# tests and bounds 11, chain rule 40, plus the window sums: 3 operations per
+# ramp cell beyond the first and 2 more, with L = 2 R / h cells on average.
+FWD_OPS_PER_PAIR = 175
 
 
 def adj_ops_per_pair(mean_R, h):
