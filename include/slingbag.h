@@ -326,6 +326,66 @@ int sbp_reconstruct_frames(sbp_array arr, const float* y_full_dev, sbp_balls pac
 int sbp_autotune_frames(sbp_array arr, sbp_balls packed, const int* n_dev, float* S_dev,
                         float* G_dev, int* fwd_chunk_out, int* adj_split_out);
 
+/* ------------------------------------------------------------------------
+ * Envelope, initialisation and voxel grid: the steps of Algorithm 1 before
+ * and after the iteration (Section 4.1; Algorithm 1, envelope mesh
+ * generation, ray-casting initialisation, point cloud to voxel grid).
+ * ---------------------------------------------------------------------- */
+
+typedef struct sbp_envelope_s* sbp_envelope; /* opaque; owned by the library */
+
+/* Envelope mesh from the array coordinates: the convex hull of the M sensor
+ * positions (pos_host: HOST memory, [M][3] float32, mm), a closed triangle
+ * mesh with outward orientation, built on the host in double precision.
+ * The paper names no construction: the convex hull is this library's
+ * reading. Copies the mesh to the current device. Returns SBP_ERR_ARG for
+ * M < 4 or a flat array (a line or plane of sensors), SBP_ERR_NUMERIC for a
+ * non-finite coordinate. */
+int sbp_envelope_create(const float* pos_host, int M, sbp_envelope* out);
+int sbp_envelope_destroy(sbp_envelope env); /* synchronises the device */
+
+/* Face count, enclosed volume (mm^3) and the sensors' bounding box
+ * (bbox6 = {xmin, ymin, zmin, xmax, ymax, zmax}); any pointer may be NULL. */
+int sbp_envelope_info(sbp_envelope env, int* n_faces, double* volume, double* bbox6);
+
+/* The triangles as sensor indices, [n_faces][3], into host memory. */
+int sbp_envelope_faces(sbp_envelope env, int* tri_host);
+
+/* Region test of n points (device SoA x, y, z): inside_dev[i] = 1 when the
+ * point is inside the envelope (ray casting: odd number of crossings of a
+ * fixed ray, double precision) and at least `inset` mm from its surface (the
+ * reconstruction region pulled inward along the normals), else 0. */
+int sbp_envelope_classify(sbp_envelope env, const float* x_dev, const float* y_dev,
+                          const float* z_dev, long long n, double inset,
+                          unsigned char* inside_dev, sbp_stream stream);
+
+/* Random initialisation of the point cloud inside the region. Candidate k
+ * takes x, y, z uniform over the sensors' bounding box and R, p0 uniform in
+ * [R_lo, R_hi], [p_lo, p_hi], from SplitMix64 outputs 5k .. 5k+4 of the
+ * stream seeded with `seed` (each a double lo + (hi - lo) u, u = top 53 bits
+ * x 2^-53, rounded to float). Candidates first .. first + n_cand - 1 are
+ * tested in order; the first n_want inside the region (see classify) are
+ * written to out[0 .. ) and their number to *n_dev (device int). The
+ * result depends only on the seed and the candidate range. Allocates its
+ * scratch on first use (and when n_cand grows, synchronising then). */
+int sbp_envelope_sample(sbp_envelope env, uint64_t seed, long long first, long long n_cand,
+                        double inset, double R_lo, double R_hi, double p_lo, double p_hi,
+                        sbp_balls out, int n_want, int* n_dev, sbp_stream stream);
+
+/* Point cloud to voxel grid. Voxel (i, j, k) has centre origin + (index +
+ * 1/2) spacing and takes the sum of value_dev[b] (NULL: the balls' p0) over
+ * the live balls b with |centre - c_b| < R_b; the test is evaluated in
+ * double as (dx^2 + dy^2) + dz^2 < R^2. The paper's voxel shader is not
+ * specified: this is the uniform-sphere reading. Sums are accumulated in
+ * fixed point (2^-F units, F = 40 - ceil(log2 max|value|)), so the grid is
+ * independent of ball order. vol_dev: [nz][ny][nx] float32, overwritten.
+ * scratch_dev: nx*ny*nz + 1 uint64 words of device memory that must be zero
+ * before the first call; every call leaves them zero. n_dev may be NULL
+ * (all n_cap balls). */
+int sbp_voxelize(sbp_balls balls, const float* value_dev, const int* n_dev, int n_cap,
+                 const double* origin3, double spacing, int nx, int ny, int nz,
+                 unsigned long long* scratch_dev, float* vol_dev, sbp_stream stream);
+
 /* Number of CUDA kernels this library has launched in this process. */
 long long sbp_launch_count(void);
 

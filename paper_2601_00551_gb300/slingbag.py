@@ -116,6 +116,19 @@ _SIGS = {
     "sbp_probe_fp32x2_fma": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "sbp_probe_issue": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "sbp_probe_smem_atomic": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "sbp_envelope_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "sbp_envelope_destroy": (ctypes.c_int, [_P]),
+    "sbp_envelope_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_double), _P]),
+    "sbp_envelope_faces": (ctypes.c_int, [_P, _P]),
+    "sbp_envelope_classify": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_longlong, ctypes.c_double,
+                                             _P, _P]),
+    "sbp_envelope_sample": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_longlong,
+                                           ctypes.c_longlong, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           _Balls, ctypes.c_int, _P, _P]),
+    "sbp_voxelize": (ctypes.c_int, [_Balls, _P, _P, ctypes.c_int, _P, ctypes.c_double,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
     "sbp_sync_status": (ctypes.c_int, [_P, _P]),
     "sbp_get_inside_pairs": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_longlong)]),
 }
@@ -560,3 +573,97 @@ def radiate(array: SensorArray, x, y, z, R, p0, level: int = 0) -> torch.Tensor:
     centres (x, y, z), radii R and pressures p0 (float32 CUDA vectors) at
     sampling level `level` of `array`."""
     return _Radiator.apply(x, y, z, R, p0, array, level)
+
+
+# --------------------------------------------------------------------------
+# envelope, initialisation and voxel grid (include/slingbag.h)
+# --------------------------------------------------------------------------
+
+class Envelope:
+    """The array's envelope mesh (sbp_envelope_create): the convex hull of the
+    sensor positions, with the ray-casting region test and the seeded
+    initialisation of a point cloud inside it."""
+
+    def __init__(self, pos, device=None):
+        self._lib = load_library()
+        if device is not None:
+            torch.cuda.set_device(device)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        P = np.ascontiguousarray(np.asarray(pos, dtype=np.float32).reshape(-1, 3))
+        h = _P()
+        _check("sbp_envelope_create", self._lib.sbp_envelope_create(P.ctypes.data, P.shape[0],
+                                                                    ctypes.byref(h)))
+        self._h = h
+        nf, vol = ctypes.c_int(), ctypes.c_double()
+        box = np.zeros(6, dtype=np.float64)
+        _check("sbp_envelope_info", self._lib.sbp_envelope_info(
+            self._h, ctypes.byref(nf), ctypes.byref(vol), box.ctypes.data))
+        self.n_faces, self.volume = nf.value, vol.value
+        self.bbox = (box[:3].copy(), box[3:].copy())
+
+    def faces(self) -> np.ndarray:
+        tri = np.zeros((self.n_faces, 3), dtype=np.int32)
+        _check("sbp_envelope_faces", self._lib.sbp_envelope_faces(self._h, tri.ctypes.data))
+        return tri
+
+    def classify(self, pts: torch.Tensor, inset: float = 0.0) -> torch.Tensor:
+        """pts: (3, n) or (>=3, n) float32 CUDA rows x, y, z -> uint8 flags."""
+        if pts.dtype != torch.float32 or not pts.is_cuda or pts.dim() != 2 or pts.shape[0] < 3 \
+                or not pts.is_contiguous():
+            raise ValueError("expected a contiguous (3+, n) float32 CUDA tensor")
+        n = pts.shape[1]
+        out = torch.empty(n, dtype=torch.uint8, device=pts.device)
+        _check("sbp_envelope_classify", self._lib.sbp_envelope_classify(
+            self._h, _dptr(pts[0]), _dptr(pts[1]), _dptr(pts[2]), n, float(inset), _dptr(out),
+            _stream()))
+        return out
+
+    def sample(self, n_want: int, n_candidates: int, seed: int, inset: float = 0.0,
+               R_range=(0.05, 0.2), p_range=(0.0, 1.0), first: int = 0, out=None, n_dev=None):
+        """Seeded ray-casting initialisation (sbp_envelope_sample): returns the
+        (5, cap) cloud tensor and its device count."""
+        if out is None:
+            out = torch.zeros((5, max(1, n_want)), dtype=torch.float32, device=self.device)
+        if n_dev is None:
+            n_dev = torch.zeros(1, dtype=torch.int32, device=self.device)
+        if out.shape[1] < n_want:
+            raise ValueError("out holds fewer than n_want balls")
+        _check("sbp_envelope_sample", self._lib.sbp_envelope_sample(
+            self._h, int(seed) & 0xFFFFFFFFFFFFFFFF, int(first), int(n_candidates), float(inset),
+            float(R_range[0]), float(R_range[1]), float(p_range[0]), float(p_range[1]),
+            _rows(out), int(n_want), _dptr(n_dev), _stream()))
+        return out, n_dev
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sbp_envelope_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def voxelize(balls: torch.Tensor, origin, spacing: float, dims, n_dev=None, values=None,
+             out=None, scratch=None) -> torch.Tensor:
+    """Point cloud -> voxel grid (sbp_voxelize): float32 [nz][ny][nx] of the
+    summed values (default p0) of the balls containing each voxel centre."""
+    lib = load_library()
+    nx, ny, nz = (int(v) for v in dims)
+    total = nx * ny * nz
+    if out is None:
+        out = torch.empty((nz, ny, nx), dtype=torch.float32, device=balls.device)
+    if scratch is None:
+        scratch = torch.zeros(total + 1, dtype=torch.int64, device=balls.device)
+    if scratch.numel() < total + 1 or scratch.dtype != torch.int64:
+        raise ValueError("scratch needs nx*ny*nz + 1 int64 words")
+    if values is not None and (values.dtype != torch.float32 or not values.is_cuda):
+        raise ValueError("values must be a float32 CUDA tensor")
+    org = (ctypes.c_double * 3)(*[float(v) for v in origin])
+    _check("sbp_voxelize", lib.sbp_voxelize(
+        _rows(balls), _dptr(values), _dptr(n_dev), balls.shape[1], org, float(spacing), nx, ny, nz,
+        _dptr(scratch), _dptr(out), _stream()))
+    return out
+
