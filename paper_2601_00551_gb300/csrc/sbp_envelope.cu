@@ -719,6 +719,8 @@ int sbp_voxelize(sbp_balls balls, const float* value_dev, const int* n_dev, int 
     }
     const int fb = (int)std::max<long long>(1, std::min<long long>(4096, (total + 255) / 256));
     vox_finalize_kernel<<<fb, 256, 0, st>>>(scratch_dev, total, bits, vol_dev);
+    if (sbp_cuda_check(cudaMemsetAsync(bits, 0, sizeof(unsigned int), st), "voxelize: clear"))
+        return SBP_ERR_CUDA;
     sbp_count_launches(launched + 1);
     return sbp_cuda_check(cudaGetLastError(), "voxelize launch") ? SBP_ERR_CUDA : SBP_OK;
 }

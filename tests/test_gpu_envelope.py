@@ -92,7 +92,7 @@ def test_sample_matches_oracle(sb):
     assert n == ref.shape[1] == n_want
     np.testing.assert_array_equal(out[:, :n].cpu().numpy(), ref)
     # a shorter candidate range stops early; a later range continues the stream
-    out2, n2 = env.sample(10 ** 6, 200, seed, inset=inset, out=torch.zeros((5, 200)).cuda())
+    out2, n2 = env.sample(200, 200, seed, inset=inset, out=torch.zeros((5, 200)).cuda())
     ref2, _ = E.sample_cloud(V, T, 10 ** 6, seed, inset, 0, 200)
     assert int(n2.item()) == ref2.shape[1]
     np.testing.assert_array_equal(out2[:, :ref2.shape[1]].cpu().numpy(), ref2)
