@@ -65,6 +65,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-frames", action="store_true",
                     help="skip the batched dynamic-imaging comparison")
+    ap.add_argument("--no-envelope", action="store_true",
+                    help="skip the envelope / initialisation / voxel grid timing")
     ap.add_argument("--profile", action="store_true",
                     help="short run for a profiler: no clocks, e2e or CPU baseline")
     return ap.parse_args(argv)
@@ -426,6 +428,11 @@ def run_native(args, rank, world, local):
             result["batched_frames"] = batched_frames(args, sb, dev)
         except Exception as exc:  # keep the main measurement if this part fails
             result["batched_frames"] = {"error": f"{type(exc).__name__}: {exc}"}
+    if not (args.profile or args.no_envelope) and args.workload == "vessel":
+        try:
+            result["envelope_init_voxel"] = envelope_init_voxel(sb, dev)
+        except Exception as exc:  # keep the main measurement if this part fails
+            result["envelope_init_voxel"] = {"error": f"{type(exc).__name__}: {exc}"}
     if world == 1 and rank == 0 and not (args.no_cpu_baseline or args.profile):
         result["cpu_baseline"] = cpu_baseline(wl, y_host, counts, n0, seconds=15.0)
     arr.close()
@@ -753,6 +760,63 @@ def batched_frames(args, sb, dev, steps=8, warmup=3):
                                                out["batched_graph"]["ms_per_step"]),
         "l2": "flushed before every timed step (512 MB write)",
     }
+
+
+def envelope_init_voxel(sb, dev, reps=3):
+    """Entry and exit of Algorithm 1 on a closed irregular array (2006 sensors
+    on a closed ellipsoid around an 80 x 104 x 40 mm region): the envelope
+    mesh (host convex hull), the seeded ray-casting initialisation of
+    200,000 balls inside the envelope pulled 2 mm inward, and the point cloud
+    -> voxel grid conversion of that cloud at 0.2 mm (41.6M voxels). Device
+    times from CUDA events (one warm-up call, then the mean of `reps`)."""
+    import torch
+
+    import workloads
+
+    ew = workloads.envelope()
+    t0 = time.perf_counter()
+    env = sb.Envelope(ew.sensors.pos)
+    hull_ms = (time.perf_counter() - t0) * 1e3
+    lo, hi = env.bbox
+    box_vol = float(np.prod(hi - lo))
+    n = ew.n_init
+    n_cand = int(1.6 * n * box_vol / env.volume) + 4096
+    out = torch.zeros((5, n), dtype=torch.float32, device=dev)
+    n_dev = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    sample_ms = timed(lambda: env.sample(n, n_cand, ew.seed, inset=ew.inset, R_range=ew.R_range,
+                                         p_range=ew.p_range, out=out, n_dev=n_dev))
+    got = int(n_dev.item())
+    nx, ny, nz = ew.dims
+    scratch = torch.zeros(nx * ny * nz + 1, dtype=torch.int64, device=dev)
+    vol = torch.empty((nz, ny, nx), dtype=torch.float32, device=dev)
+    vox_ms = timed(lambda: sb.voxelize(out, ew.origin, ew.spacing, ew.dims, n_dev=n_dev,
+                                       out=vol, scratch=scratch))
+    filled = int((vol != 0).sum().item())
+    res = {
+        "workload": ew.name,
+        "envelope": {"faces": env.n_faces, "volume_mm3": env.volume, "host_ms": hull_ms},
+        "init": {"balls": got, "candidates": n_cand, "ms": sample_ms,
+                 "candidates_per_s": n_cand / (sample_ms * 1e-3),
+                 "ray_triangle_tests_per_s": n_cand * env.n_faces / (sample_ms * 1e-3)},
+        "voxel_grid": {"voxels": nx * ny * nz, "filled": filled, "ms": vox_ms,
+                       "voxels_per_s": nx * ny * nz / (vox_ms * 1e-3)},
+    }
+    env.close()
+    return res
 
 
 def run_e2e(args, sb, arr, wl, y_host, init, n0, n_cap, stages, adam, pairs_per_step, dev):

@@ -33,6 +33,9 @@ struct sbp_envelope_s {
     double volume = 0;
     std::vector<int> tri;       // [F][3] sensor indices, outward orientation
     double* d_tri = nullptr;    // [F][13]: v0, e1 = v1 - v0, e2 = v2 - v0, unit normal, offset
+    float* d_ftri = nullptr;    // [F][20]: the same triangle seen along the ray (see FTri)
+    double frame[6] = {0, 0, 0, 0, 0, 0};  // the two unit axes across the ray
+    double lmax = 0;            // largest coordinate magnitude of the sensors
     unsigned char* d_flags = nullptr;  // sampling scratch: one flag per candidate
     long long flags_cap = 0;
     long long* d_block = nullptr;      // per-block accepted counts, then offsets; [blocks + 1]
@@ -42,6 +45,7 @@ struct sbp_envelope_s {
 namespace {
 
 constexpr int kTriWords = 13;
+constexpr int kFWords = 26;  // float record per triangle (see fast_cross)
 constexpr int kEnvThreads = 256;
 constexpr int kTriTile = 128;  // triangles staged in shared memory at a time
 constexpr int kVoxFracHeadroom = 40;  // voxel sums kept as round(v 2^F), |v| 2^F < 2^40
@@ -50,6 +54,7 @@ constexpr int kVoxFracHeadroom = 40;  // voxel sums kept as round(v 2^F), |v| 2^
 // coordinate plane)
 __device__ __constant__ double kRayDir[3] = {0.8017837257372732, 0.5345224838248488,
                                              0.2672612419124244};
+constexpr double kRayDirHost[3] = {0.8017837257372732, 0.5345224838248488, 0.2672612419124244};
 
 // ---------------------------------------------------------------------------
 // host: incremental convex hull
@@ -239,83 +244,155 @@ __device__ __forceinline__ bool ray_hits(const double* T, double x, double y, do
 
 // Squared distance from p to the closed triangle (closest point by the
 // Voronoi regions of its vertices, edges and face).
-__device__ __forceinline__ double tri_dist2(const double* T, double px, double py, double pz) {
-    const double ax = T[0], ay = T[1], az = T[2];
-    const double abx = T[3], aby = T[4], abz = T[5], acx = T[6], acy = T[7], acz = T[8];
-    const double apx = px - ax, apy = py - ay, apz = pz - az;
-    const double d1 = abx * apx + aby * apy + abz * apz, d2 = acx * apx + acy * apy + acz * apz;
-    double qx, qy, qz;
-    if (d1 <= 0.0 && d2 <= 0.0) {
+template <typename R>
+__device__ __forceinline__ R tri_dist2(const R* T, R px, R py, R pz) {
+    const R ax = T[0], ay = T[1], az = T[2];
+    const R abx = T[3], aby = T[4], abz = T[5], acx = T[6], acy = T[7], acz = T[8];
+    const R apx = px - ax, apy = py - ay, apz = pz - az;
+    const R d1 = abx * apx + aby * apy + abz * apz, d2 = acx * apx + acy * apy + acz * apz;
+    R qx, qy, qz;
+    if (d1 <= R(0) && d2 <= R(0)) {
         qx = ax, qy = ay, qz = az;
     } else {
-        const double bpx = apx - abx, bpy = apy - aby, bpz = apz - abz;
-        const double d3 = abx * bpx + aby * bpy + abz * bpz, d4 = acx * bpx + acy * bpy + acz * bpz;
-        const double cpx = apx - acx, cpy = apy - acy, cpz = apz - acz;
-        const double d5 = abx * cpx + aby * cpy + abz * cpz, d6 = acx * cpx + acy * cpy + acz * cpz;
-        const double vc = d1 * d4 - d3 * d2, vb = d5 * d2 - d1 * d6, va = d3 * d6 - d5 * d4;
-        if (d3 >= 0.0 && d4 <= d3) {
+        const R bpx = apx - abx, bpy = apy - aby, bpz = apz - abz;
+        const R d3 = abx * bpx + aby * bpy + abz * bpz, d4 = acx * bpx + acy * bpy + acz * bpz;
+        const R cpx = apx - acx, cpy = apy - acy, cpz = apz - acz;
+        const R d5 = abx * cpx + aby * cpy + abz * cpz, d6 = acx * cpx + acy * cpy + acz * cpz;
+        const R vc = d1 * d4 - d3 * d2, vb = d5 * d2 - d1 * d6, va = d3 * d6 - d5 * d4;
+        if (d3 >= R(0) && d4 <= d3) {
             qx = ax + abx, qy = ay + aby, qz = az + abz;
-        } else if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) {
-            const double s = d1 / (d1 - d3);
+        } else if (vc <= R(0) && d1 >= R(0) && d3 <= R(0)) {
+            const R s = d1 / (d1 - d3);
             qx = ax + s * abx, qy = ay + s * aby, qz = az + s * abz;
-        } else if (d6 >= 0.0 && d5 <= d6) {
+        } else if (d6 >= R(0) && d5 <= d6) {
             qx = ax + acx, qy = ay + acy, qz = az + acz;
-        } else if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {
-            const double s = d2 / (d2 - d6);
+        } else if (vb <= R(0) && d2 >= R(0) && d6 <= R(0)) {
+            const R s = d2 / (d2 - d6);
             qx = ax + s * acx, qy = ay + s * acy, qz = az + s * acz;
-        } else if (va <= 0.0 && (d4 - d3) >= 0.0 && (d5 - d6) >= 0.0) {
-            const double s = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+        } else if (va <= R(0) && (d4 - d3) >= R(0) && (d5 - d6) >= R(0)) {
+            const R s = (d4 - d3) / ((d4 - d3) + (d5 - d6));
             qx = ax + abx + s * (acx - abx), qy = ay + aby + s * (acy - aby),
             qz = az + abz + s * (acz - abz);
         } else {
-            const double den = 1.0 / (va + vb + vc);
-            const double v = vb * den, w = vc * den;
+            const R den = R(1) / (va + vb + vc);
+            const R v = vb * den, w = vc * den;
             qx = ax + abx * v + acx * w, qy = ay + aby * v + acy * w, qz = az + abz * v + acz * w;
         }
     }
-    const double ex = px - qx, ey = py - qy, ez = pz - qz;
+    const R ex = px - qx, ey = py - qy, ez = pz - qz;
     return ex * ex + ey * ey + ez * ez;
 }
 
+// Float record of a triangle seen along the ray. With the ray direction d
+// and two unit axes e_u, e_v across it, the ray from p crosses the triangle
+// exactly when p's projection (p.e_u, p.e_v) lies inside the projected
+// triangle and the triangle's plane lies ahead of p along d. Words:
+//   0..5   projected vertices a, b, c (u, v)
+//   6..11  projected edge vectors b - a, c - b, a - c (from the double vertices)
+//   12..15 projected bounding box (umin, umax, vmin, vmax)
+//   16..18 L1 lengths of the three edge vectors
+//   19..21 unit normal n, 22..24 vertex a, 25 sign of n.d
+struct RayFrame {
+    double e[6];  // e_u, e_v
+    double lmax;  // largest sensor coordinate magnitude
+};
+
+// One pair of projected edge functions' error bands: an edge function
+// (b - a) x (p - a) evaluated in float with coordinates below L in magnitude
+// is within 16 eps L |b - a|_1 of its exact value (eps = 2^-24), which
+// includes the rounding of the projected coordinates themselves.
+constexpr float kEps = 5.9604645e-8f;
+
+// Ray-crossing test of one triangle: 1 = crossed, 0 = not crossed, -1 = too
+// close to an edge or to the triangle's plane to decide in float.
+__device__ __forceinline__ int fast_cross(const float* T, float pu, float pv, float px, float py,
+                                          float pz, float kp) {
+    const float m = kp * 4.0f;
+    if (pu < T[12] - m || pu > T[13] + m || pv < T[14] - m || pv > T[15] + m) return 0;
+    // edge functions (b - a) x (p - a); with edge vectors and vertices each
+    // rounded once from double, each is within kp |edge|_1 of its exact value
+    const float s0 = T[6] * (pv - T[1]) - T[7] * (pu - T[0]);
+    const float s1 = T[8] * (pv - T[3]) - T[9] * (pu - T[2]);
+    const float s2 = T[10] * (pv - T[5]) - T[11] * (pu - T[4]);
+    const float b0 = kp * T[16], b1 = kp * T[17], b2 = kp * T[18];
+    const int pos = (s0 > b0) + (s1 > b1) + (s2 > b2);
+    const int neg = (s0 < -b0) + (s1 < -b1) + (s2 < -b2);
+    if (pos > 0 && neg > 0) return 0;  // outside the projection
+    if (pos + neg < 3) return -1;      // on an edge within the error band
+    // inside the projection: crossed when the plane is ahead along d
+    const float sd = T[19] * (T[22] - px) + T[20] * (T[23] - py) + T[21] * (T[24] - pz);
+    if (fabsf(sd) <= kp) return -1;
+    return ((sd > 0.0f) == (T[25] > 0.0f)) ? 1 : 0;
+}
+
 // Region test of the calling thread's point against every triangle, staged
-// through shared memory in tiles. Every thread of the block must call it
-// (it contains barriers); `active` = false threads only help staging.
-__device__ bool env_in_region(const double* __restrict__ tri, int F, double inset, bool active,
-                              double x, double y, double z, double* s_tri) {
+// through shared memory in tiles. Each triangle is first decided in float;
+// undecidable ones (a ray through an edge's error band, a point on a plane)
+// and distances that may fall below the inset are evaluated in double. Every
+// thread of the block must call it (it contains barriers); `active` = false
+// threads only help staging.
+__device__ bool env_in_region(const double* __restrict__ tri, const float* __restrict__ ftri,
+                              int F, double inset, const double* frame, double lmax, bool active,
+                              double x, double y, double z, float* s_tri) {
+    const float pu = (float)(x * frame[0] + y * frame[1] + z * frame[2]);
+    const float pv = (float)(x * frame[3] + y * frame[4] + z * frame[5]);
+    const float px = (float)x, py = (float)y, pz = (float)z;
+    const double L = fmax(lmax, fmax(fabs(x), fmax(fabs(y), fabs(z)))) * 1.7320508075688772;
+    const float kp = (float)(16.0 * (double)kEps * L);
+    // sweep 1: crossings of the ray
     int hits = 0;
-    double best2 = inset > 0.0 ? inset * inset : 0.0;  // only distances below the inset matter
+    for (int t0 = 0; t0 < F; t0 += kTriTile) {
+        const int cnt = min(kTriTile, F - t0);
+        __syncthreads();
+        for (int w = threadIdx.x; w < cnt * kFWords; w += blockDim.x)
+            s_tri[w] = ftri[(size_t)t0 * kFWords + w];
+        __syncthreads();
+        if (!active) continue;
+        for (int t = 0; t < cnt; ++t) {
+            const int c = fast_cross(s_tri + t * kFWords, pu, pv, px, py, pz, kp);
+            hits += c > 0 ? 1 : (c < 0 && ray_hits(tri + (size_t)(t0 + t) * kTriWords, x, y, z)
+                                     ? 1 : 0);
+        }
+    }
+    const bool inside = active && (hits & 1);
+    if (!(inset > 0.0) || !__syncthreads_or(inside)) return inside;
+    // sweep 2, for points inside: is any triangle closer than the inset? A
+    // triangle is screened by its plane distance and its float distance
+    // (each within ~1e-5 mm of exact here) before the double evaluation.
+    const double best2 = inset * inset;
+    const float cull = (float)(inset + 1e-3 + 16.0 * (double)kEps * L);
+    const float cull2 = cull * cull;
     bool near = false;
     for (int t0 = 0; t0 < F; t0 += kTriTile) {
         const int cnt = min(kTriTile, F - t0);
         __syncthreads();
         for (int w = threadIdx.x; w < cnt * kTriWords; w += blockDim.x)
-            s_tri[w] = tri[(size_t)t0 * kTriWords + w];
+            reinterpret_cast<float*>(s_tri)[w] = (float)tri[(size_t)t0 * kTriWords + w];
         __syncthreads();
-        if (!active) continue;
-        for (int t = 0; t < cnt; ++t) {
-            const double* T = s_tri + t * kTriWords;
-            hits += ray_hits(T, x, y, z) ? 1 : 0;
-            if (inset > 0.0 && !near) {
-                // the plane distance bounds the triangle distance from below
-                const double pd = T[9] * x + T[10] * y + T[11] * z - T[12];
-                if (pd * pd < best2 && tri_dist2(T, x, y, z) < best2) near = true;
-            }
+        if (!inside || near) continue;
+        for (int t = 0; t < cnt && !near; ++t) {
+            const float* T = s_tri + t * kTriWords;
+            const float pd = T[9] * px + T[10] * py + T[11] * pz - T[12];
+            if (fabsf(pd) < cull && tri_dist2<float>(T, px, py, pz) < cull2 &&
+                tri_dist2<double>(tri + (size_t)(t0 + t) * kTriWords, x, y, z) < best2)
+                near = true;
         }
     }
-    return active && (hits & 1) && !near;
+    return inside && !near;
 }
 
 __global__ void __launch_bounds__(kEnvThreads)
-env_classify_kernel(const double* __restrict__ tri, int F, double inset,
-                    const float* __restrict__ px, const float* __restrict__ py,
-                    const float* __restrict__ pz, long long n, unsigned char* __restrict__ flags) {
-    __shared__ double s_tri[kTriTile * kTriWords];
+env_classify_kernel(const double* __restrict__ tri, const float* __restrict__ ftri, int F,
+                    double inset, RayFrame fr, const float* __restrict__ px,
+                    const float* __restrict__ py, const float* __restrict__ pz, long long n,
+                    unsigned char* __restrict__ flags) {
+    __shared__ float s_tri[kTriTile * kFWords];
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < n;
     const double x = active ? (double)px[i] : 0.0;
     const double y = active ? (double)py[i] : 0.0;
     const double z = active ? (double)pz[i] : 0.0;
-    const bool in = env_in_region(tri, F, inset, active, x, y, z, s_tri);
+    const bool in = env_in_region(tri, ftri, F, inset, fr.e, fr.lmax, active, x, y, z, s_tri);
     if (active) flags[i] = in ? 1 : 0;
 }
 
@@ -364,16 +441,17 @@ __device__ __forceinline__ Candidate env_candidate(uint64_t seed, long long k,
 
 // flags[j] for candidate first + j, and the block's accepted count
 __global__ void __launch_bounds__(kEnvThreads)
-env_sample_classify_kernel(const double* __restrict__ tri, int F, double inset, uint64_t seed,
-                           long long first, long long n_cand, SampleBox bx,
-                           unsigned char* __restrict__ flags, long long* __restrict__ block_cnt) {
-    __shared__ double s_tri[kTriTile * kTriWords];
+env_sample_classify_kernel(const double* __restrict__ tri, const float* __restrict__ ftri, int F,
+                           double inset, RayFrame fr, uint64_t seed, long long first,
+                           long long n_cand, SampleBox bx, unsigned char* __restrict__ flags,
+                           long long* __restrict__ block_cnt) {
+    __shared__ float s_tri[kTriTile * kFWords];
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = j < n_cand;
     Candidate c{0, 0, 0, 0, 0};
     if (active) c = env_candidate(seed, first + j, bx);
-    const bool in = env_in_region(tri, F, inset, active, (double)c.x, (double)c.y, (double)c.z,
-                                  s_tri);
+    const bool in = env_in_region(tri, ftri, F, inset, fr.e, fr.lmax, active, (double)c.x,
+                                  (double)c.y, (double)c.z, s_tri);
     if (active) flags[j] = in ? 1 : 0;
     const int cnt = __syncthreads_count(in);
     if (threadIdx.x == 0) block_cnt[blockIdx.x] = cnt;
@@ -505,6 +583,13 @@ __global__ void vox_finalize_kernel(unsigned long long* __restrict__ acc, long l
     }
 }
 
+RayFrame env_frame(sbp_envelope env) {
+    RayFrame f;
+    for (int k = 0; k < 6; ++k) f.e[k] = env->frame[k];
+    f.lmax = env->lmax;
+    return f;
+}
+
 int env_check_device(sbp_envelope env, const char* what) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != env->device) {
@@ -576,13 +661,63 @@ int sbp_envelope_create(const float* pos_host, int M, sbp_envelope* out) {
                 a[2] * (b[0] * c[1] - b[1] * c[0])) / 6.0;
     }
     e->volume = vol;
+    // the frame across the ray: e_u = normalise(z x d), e_v = d x e_u
+    const double* d = kRayDirHost;
+    double eu[3] = {-d[1], d[0], 0.0};
+    const double nu = std::sqrt(eu[0] * eu[0] + eu[1] * eu[1]);
+    eu[0] /= nu;
+    eu[1] /= nu;
+    const double ev[3] = {d[1] * eu[2] - d[2] * eu[1], d[2] * eu[0] - d[0] * eu[2],
+                          d[0] * eu[1] - d[1] * eu[0]};
+    for (int k = 0; k < 3; ++k) {
+        e->frame[k] = eu[k];
+        e->frame[3 + k] = ev[k];
+        e->lmax = std::max(e->lmax, std::max(std::fabs(e->lo[k]), std::fabs(e->hi[k])));
+    }
+    std::vector<float> fw((size_t)e->F * kFWords);
+    for (int f = 0; f < e->F; ++f) {
+        const double* w = &words[(size_t)f * kTriWords];
+        double uv[3][2];
+        for (int q = 0; q < 3; ++q) {
+            double v[3];
+            for (int k = 0; k < 3; ++k) v[k] = w[k] + (q == 1 ? w[3 + k] : q == 2 ? w[6 + k] : 0.0);
+            uv[q][0] = v[0] * eu[0] + v[1] * eu[1] + v[2] * eu[2];
+            uv[q][1] = v[0] * ev[0] + v[1] * ev[1] + v[2] * ev[2];
+        }
+        float* o = &fw[(size_t)f * kFWords];
+        for (int q = 0; q < 3; ++q) {
+            const int r = (q + 1) % 3;
+            const double du = uv[r][0] - uv[q][0], dv = uv[r][1] - uv[q][1];
+            o[2 * q] = (float)uv[q][0];
+            o[2 * q + 1] = (float)uv[q][1];
+            o[6 + 2 * q] = (float)du;
+            o[7 + 2 * q] = (float)dv;
+            o[16 + q] = (float)((std::fabs(du) + std::fabs(dv)) * (1.0 + 1e-6));
+        }
+        o[12] = (float)std::min({uv[0][0], uv[1][0], uv[2][0]});
+        o[13] = (float)std::max({uv[0][0], uv[1][0], uv[2][0]});
+        o[14] = (float)std::min({uv[0][1], uv[1][1], uv[2][1]});
+        o[15] = (float)std::max({uv[0][1], uv[1][1], uv[2][1]});
+        for (int k = 0; k < 3; ++k) {
+            o[19 + k] = (float)w[9 + k];
+            o[22 + k] = (float)w[k];
+        }
+        const double nd = w[9] * d[0] + w[10] * d[1] + w[11] * d[2];
+        o[25] = nd > 0.0 ? 1.0f : -1.0f;
+    }
     bool ok = !sbp_cuda_check(cudaMalloc(&e->d_tri, sizeof(double) * words.size()),
                               "envelope_create: alloc") &&
               !sbp_cuda_check(cudaMemcpy(e->d_tri, words.data(), sizeof(double) * words.size(),
                                          cudaMemcpyHostToDevice),
+                              "envelope_create: copy") &&
+              !sbp_cuda_check(cudaMalloc(&e->d_ftri, sizeof(float) * fw.size()),
+                              "envelope_create: alloc") &&
+              !sbp_cuda_check(cudaMemcpy(e->d_ftri, fw.data(), sizeof(float) * fw.size(),
+                                         cudaMemcpyHostToDevice),
                               "envelope_create: copy");
     if (!ok) {
         cudaFree(e->d_tri);
+        cudaFree(e->d_ftri);
         delete e;
         return SBP_ERR_CUDA;
     }
@@ -594,6 +729,7 @@ int sbp_envelope_destroy(sbp_envelope env) {
     if (!env) return SBP_OK;
     cudaDeviceSynchronize();
     cudaFree(env->d_tri);
+    cudaFree(env->d_ftri);
     cudaFree(env->d_flags);
     cudaFree(env->d_block);
     delete env;
@@ -635,9 +771,9 @@ int sbp_envelope_classify(sbp_envelope env, const float* x_dev, const float* y_d
     if (n == 0) return SBP_OK;
     const long long blocks = (n + kEnvThreads - 1) / kEnvThreads;
     env_classify_kernel<<<(unsigned)blocks, kEnvThreads, 0,
-                          reinterpret_cast<cudaStream_t>(stream)>>>(env->d_tri, env->F, inset,
-                                                                    x_dev, y_dev, z_dev, n,
-                                                                    inside_dev);
+                          reinterpret_cast<cudaStream_t>(stream)>>>(
+        env->d_tri, env->d_ftri, env->F, inset, env_frame(env), x_dev, y_dev, z_dev, n,
+        inside_dev);
     sbp_count_launches(1);
     return sbp_cuda_check(cudaGetLastError(), "envelope_classify launch") ? SBP_ERR_CUDA : SBP_OK;
 }
@@ -679,7 +815,8 @@ int sbp_envelope_sample(sbp_envelope env, uint64_t seed, long long first, long l
     bx.p_lo = p_lo;
     bx.p_hi = p_hi;
     env_sample_classify_kernel<<<(unsigned)nb, kEnvThreads, 0, st>>>(
-        env->d_tri, env->F, inset, seed, first, n_cand, bx, env->d_flags, env->d_block);
+        env->d_tri, env->d_ftri, env->F, inset, env_frame(env), seed, first, n_cand, bx,
+        env->d_flags, env->d_block);
     env_scan_kernel<<<1, 1024, 0, st>>>(env->d_block, (int)nb);
     env_sample_scatter_kernel<<<(unsigned)nb, kEnvThreads, 0, st>>>(
         seed, first, n_cand, bx, env->d_flags, env->d_block, n_want, out, n_dev);

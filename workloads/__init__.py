@@ -343,3 +343,35 @@ def frames(n_frames: int = 32, n_lo: int = 20_000, n_hi: int = 200_000, n_truth:
     name = (f"frames: {n_frames} frames x {n_lo // 1000}k-{n_hi // 1000}k balls x {M} sensors, "
             f"10/20/40 MHz, T={T // levels[0]}/{T // levels[1]}/{T}")
     return FrameWorkload(name, sens, inits, truths, shifts, 40.0, T, tuple(levels))
+
+
+@dataclasses.dataclass
+class EnvelopeWorkload:
+    """A closed irregular array around an imaging region, the initial cloud
+    size and inset, and the voxel grid of the region."""
+    name: str
+    sensors: Sensors
+    n_init: int
+    inset: float
+    R_range: tuple
+    p_range: tuple
+    seed: int
+    origin: tuple
+    spacing: float
+    dims: tuple
+
+
+def envelope(M: int = 2006, axes=(48.0, 60.0, 26.0), n_init: int = 200_000,
+             inset: float = 2.0) -> EnvelopeWorkload:
+    """Stand-in for the hand-vessel setup (Section 2.1): M sensors drawn
+    uniformly by area on a closed ellipsoid (semi-axes 48 / 60 / 26 mm, around
+    an 80 x 104 x 40 mm imaging region), normals inward jittered by up to
+    15 deg; 200,000 initial balls inside the envelope pulled 2 mm inward
+    (R ~ U(0.05, 0.2) mm, p0 ~ U(0, 1), seed 1); the region voxelised at
+    0.2 mm (400 x 520 x 200 voxels)."""
+    sens = ellipsoid_cap(M, axes, 15.0, seed=2, z_min=-axes[2])
+    return EnvelopeWorkload(
+        f"envelope: {M} sensors on a closed {axes[0]:g}/{axes[1]:g}/{axes[2]:g} mm ellipsoid, "
+        f"{n_init // 1000}k balls, 0.2 mm voxels over 80 x 104 x 40 mm",
+        sens, n_init, inset, (0.05, 0.2), (0.0, 1.0), 1, (-40.0, -52.0, -20.0), 0.2,
+        (400, 520, 200))
