@@ -386,6 +386,31 @@ int sbp_voxelize(sbp_balls balls, const float* value_dev, const int* n_dev, int 
                  const double* origin3, double spacing, int nx, int ny, int nz,
                  unsigned long long* scratch_dev, float* vol_dev, sbp_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Learned initial proposal: the small volume CNN (no counterpart in the
+ * paper, which initialises at random and filters by zero gradients; the
+ * learned proposal is this library's extension of that step).
+ * ---------------------------------------------------------------------- */
+
+/* 3x3x3 convolution with zero padding on a channels-last bf16 volume, on the
+ * tensor cores (tcgen05, BF16 x BF16 -> FP32 in tensor memory).
+ * in_dev:  bf16 [nz][ny][nx][cin] (device, 16-byte aligned);
+ * w_dev:   bf16 [cout][kp], row n holding the weights of output channel n at
+ *          k = tap * cin + c, tap = (dz+1)*9 + (dy+1)*3 + (dx+1), zero for
+ *          27*cin <= k < kp; kp a multiple of 64;
+ * bias_dev: float [cout] or NULL; relu: apply max(., 0) after the bias;
+ * out_dev: [nz][ny][nx][cout], bf16 (out_f32 = 0) or float (out_f32 = 1).
+ * Supported (cin, cout): (1,16) (16,16) (16,32) (32,32) (32,64) (64,64)
+ * (64,32) (32,16). A bounded wait that gives up (a device fault elsewhere)
+ * sets the status read by sbp_cnn_status. */
+int sbp_conv3d_bf16(const void* in_dev, int nx, int ny, int nz, int cin, const void* w_dev,
+                    int kp, const float* bias_dev, int cout, int relu, void* out_dev, int out_f32,
+                    sbp_stream stream);
+
+/* Synchronise `stream` and return (then clear) the convolution status:
+ * 0 = fine, 1 = a bounded wait gave up. */
+int sbp_cnn_status(sbp_stream stream, int* status);
+
 /* Number of CUDA kernels this library has launched in this process. */
 long long sbp_launch_count(void);
 

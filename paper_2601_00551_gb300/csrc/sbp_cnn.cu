@@ -1,0 +1,372 @@
+// 3D convolution (3x3x3 taps, zero padding, stride 1) as an implicit GEMM on
+// the fifth-generation tensor cores (tcgen05), for the small volume CNN of
+// the learned initial proposal.
+//
+// GEMM view: D[m][n] = sum_k A[m][k] B[n][k], m = voxel (x fastest),
+// n = output channel, k = tap * Cin + c with tap = (dz+1)*9 + (dy+1)*3 +
+// (dx+1). A is the im2col of the channels-last bf16 input gathered on the
+// fly; B is the bf16 weight matrix [Cout][Kp] (K padded with zeros to a
+// multiple of 64). D accumulates in FP32 in tensor memory.
+//
+// One CTA = 128 voxels x Cout (Cout in {16, 32, 64}); 4 warps, one thread
+// per voxel row.
+//   * K is walked in steps of 64 (one 128-byte row chunk per voxel) through
+//     two shared-memory stages in the canonical K-major, non-swizzled layout:
+//     8 x 16-byte core matrices, 128 bytes each, adjacent along K (leading
+//     byte offset 128) and 8-row groups 1024 bytes apart (stride byte
+//     offset).
+//   * Every thread gathers its voxel's 64 im2col values of the step (16-byte
+//     loads when Cin is a multiple of 8), the CTA loads the step's weights,
+//     and after a proxy fence and a barrier one thread issues four
+//     tcgen05.mma (M = 128, N = Cout, K = 16 each) and commits them to the
+//     stage's mbarrier, which the stage's next overwrite waits on.
+//   * Epilogue: each warp reads its 32 accumulator lanes with tcgen05.ld,
+//     adds the bias, applies ReLU if asked and stores the voxel's channels
+//     (bf16 or fp32, channels-last).
+// Every mbarrier wait is bounded; a wait that gives up sets a status word
+// (sbp_cnn_status) and the CTA skips to its clean-up.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "sbp_internal.cuh"
+
+namespace {
+
+constexpr int kTcRows = 128;     // voxels per CTA (the MMA's M)
+constexpr int kTcBK = 64;        // K per stage
+constexpr int kTcThreads = 128;
+constexpr int kTcCols = 64;      // TMEM columns allocated (>= Cout, power of two >= 32)
+constexpr long long kWaitLimit = 1LL << 24;
+
+__device__ int g_cnn_status;  // 0, or 1 when a bounded wait gave up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// UMMA shared-memory descriptor: start >> 4 in bits 0-13, leading byte
+// offset >> 4 in 16-29, stride byte offset >> 4 in 32-45, version 1 in
+// 46-47, no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9 and 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in
+// bits 24-28.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Waits for the phase with the given parity to complete; false after the
+// iteration limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+// 16 consecutive fp32 columns of this thread's lane
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct ConvArgs {
+    const __nv_bfloat16* in;  // [V][Cin]
+    const __nv_bfloat16* w;   // [Cout][Kp]
+    const float* bias;        // [Cout] or null
+    void* out;                // [V][Cout], bf16 or fp32
+    int nx, ny, nz;
+    int Kp;
+};
+
+template <int CIN, int COUT, bool RELU, bool OUT_F32>
+__global__ void __launch_bounds__(kTcThreads) conv3d_tc_kernel(ConvArgs a) {
+    static_assert(COUT % 16 == 0 && COUT >= 16 && COUT <= kTcCols, "Cout must be 16, 32 or 64");
+    // two stages of A (128 rows x 64) then two of B (COUT rows x 64), bf16
+    extern __shared__ __align__(1024) uint8_t s_dyn[];
+    constexpr int kABytes = kTcRows * kTcBK * 2, kBBytes = COUT * kTcBK * 2;
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t s_tmem;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const long long V = (long long)a.nx * a.ny * a.nz;
+    const long long m = (long long)blockIdx.x * kTcRows + tid;  // this thread's voxel
+    const bool mv = m < V;
+    int x = 0, y = 0, z = 0;
+    if (mv) {
+        x = (int)(m % a.nx);
+        y = (int)((m / a.nx) % a.ny);
+        z = (int)(m / ((long long)a.nx * a.ny));
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    constexpr uint32_t idesc = umma_idesc_bf16(kTcRows, COUT);
+    const int nk = a.Kp / kTcBK;
+    constexpr int K = 27 * CIN;
+    uint32_t phase[2] = {0u, 0u};
+    bool ok = true;
+
+    for (int kt = 0; kt < nk; ++kt) {
+        const int st = kt & 1;
+        if (kt >= 2) {  // the MMAs that read this stage two steps ago must be done
+            if (!mbar_wait(&bar[st], phase[st])) ok = false;
+            phase[st] ^= 1u;
+        }
+        if (!__syncthreads_and(ok)) break;
+        // this thread's row: 8 chunks of 8 K-values (16 bytes each)
+        uint8_t* rowA = s_dyn + st * kABytes + ((tid >> 3) * 8) * 128 + (tid & 7) * 16;
+#pragma unroll
+        for (int kc = 0; kc < 8; ++kc) {
+            const int k0 = kt * kTcBK + kc * 8;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (mv && k0 < K) {
+                if constexpr (CIN % 8 == 0) {
+                    const int tap = k0 / CIN, c0 = k0 % CIN;
+                    const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
+                    const int xx = x + dx, yy = y + dy, zz = z + dz;
+                    if (xx >= 0 && xx < a.nx && yy >= 0 && yy < a.ny && zz >= 0 && zz < a.nz) {
+                        const long long q = ((long long)zz * a.ny + yy) * a.nx + xx;
+                        v = *reinterpret_cast<const uint4*>(a.in + q * CIN + c0);
+                    }
+                } else {
+                    union {
+                        uint4 u;
+                        __nv_bfloat16 h[8];
+                    } e;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int k = k0 + j;
+                        e.h[j] = __float2bfloat16(0.0f);
+                        if (k < K) {
+                            const int tap = k / CIN, c = k % CIN;
+                            const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
+                            const int xx = x + dx, yy = y + dy, zz = z + dz;
+                            if (xx >= 0 && xx < a.nx && yy >= 0 && yy < a.ny && zz >= 0 &&
+                                zz < a.nz)
+                                e.h[j] = a.in[(((long long)zz * a.ny + yy) * a.nx + xx) * CIN + c];
+                        }
+                    }
+                    v = e.u;
+                }
+            }
+            *reinterpret_cast<uint4*>(rowA + kc * 128) = v;
+        }
+        // weights of the step: COUT rows x 8 chunks
+        for (int t = tid; t < COUT * 8; t += kTcThreads) {
+            const int n = t >> 3, kc = t & 7;
+            const uint4 v =
+                *reinterpret_cast<const uint4*>(a.w + (size_t)n * a.Kp + kt * kTcBK + kc * 8);
+            *reinterpret_cast<uint4*>(s_dyn + 2 * kABytes + st * kBBytes + ((n >> 3) * 8 + kc) * 128 +
+                                      (n & 7) * 16) = v;
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(s_dyn + st * kABytes);
+            const uint32_t b0 = smem_u32(s_dyn + 2 * kABytes + st * kBBytes);
+#pragma unroll
+            for (int ks = 0; ks < kTcBK / 16; ++ks)  // K = 16 per MMA: two core matrices
+                tc_mma(tmem, umma_desc(a0 + ks * 256, 128, 1024), umma_desc(b0 + ks * 256, 128, 1024),
+                       idesc, (kt > 0 || ks > 0) ? 1u : 0u);
+            tc_commit(&bar[st]);
+        }
+    }
+    // wait for the last commit of each stage still outstanding
+    if (ok) {
+        for (int s = 0; s < 2; ++s) {
+            const int uses = nk > s ? (nk - 1 - s) / 2 + 1 : 0;  // commits made on stage s
+            const int waited = uses > 0 ? uses - 1 : 0;          // of them already waited on
+            if (uses > waited && !mbar_wait(&bar[s], phase[s])) ok = false;
+        }
+    }
+    tc_fence_after();
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicExch(&g_cnn_status, 1);
+    } else {
+        // epilogue: lane = voxel row, columns = output channels (every lane
+        // takes part in the warp-wide tcgen05.ld)
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
+            float v[16];
+            tc_ld16(taddr + c0, v);
+            if (mv) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float r = v[j] + (a.bias ? a.bias[c0 + j] : 0.0f);
+                    if (RELU) r = fmaxf(r, 0.0f);
+                    v[j] = r;
+                }
+                if constexpr (OUT_F32) {
+                    float4* o = reinterpret_cast<float4*>(static_cast<float*>(a.out) + m * COUT + c0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                } else {
+                    __nv_bfloat162 h[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                    uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.out) + m * COUT + c0);
+                    o[0] = *reinterpret_cast<uint4*>(&h[0]);
+                    o[1] = *reinterpret_cast<uint4*>(&h[4]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTcCols)
+                     : "memory");
+}
+
+template <int CIN, int COUT, bool RELU, bool OUT_F32>
+int launch_conv_t(const ConvArgs& a, unsigned blocks, cudaStream_t st) {
+    constexpr int smem = 2 * (kTcRows + COUT) * kTcBK * 2;
+    auto k = conv3d_tc_kernel<CIN, COUT, RELU, OUT_F32>;
+    if (sbp_cuda_check(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                       "conv3d_bf16: smem attribute"))
+        return SBP_ERR_CUDA;
+    k<<<blocks, kTcThreads, smem, st>>>(a);
+    return SBP_OK;
+}
+
+template <int CIN, int COUT>
+int launch_conv(const ConvArgs& a, bool relu, bool out_f32, long long V, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((V + kTcRows - 1) / kTcRows);
+    if (relu && out_f32) return launch_conv_t<CIN, COUT, true, true>(a, blocks, st);
+    if (relu) return launch_conv_t<CIN, COUT, true, false>(a, blocks, st);
+    if (out_f32) return launch_conv_t<CIN, COUT, false, true>(a, blocks, st);
+    return launch_conv_t<CIN, COUT, false, false>(a, blocks, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbp_conv3d_bf16(const void* in_dev, int nx, int ny, int nz, int cin, const void* w_dev,
+                    int kp, const float* bias_dev, int cout, int relu, void* out_dev, int out_f32,
+                    sbp_stream stream) {
+    const long long V = (long long)nx * ny * nz;
+    if (!in_dev || !w_dev || !out_dev || nx < 1 || ny < 1 || nz < 1 || kp < 27 * cin ||
+        kp % kTcBK != 0 || V > (1LL << 31) * kTcRows) {
+        sbp_set_error("conv3d_bf16: invalid argument");
+        return SBP_ERR_ARG;
+    }
+    if ((reinterpret_cast<uintptr_t>(in_dev) | reinterpret_cast<uintptr_t>(w_dev) |
+         reinterpret_cast<uintptr_t>(out_dev)) & 15u) {
+        sbp_set_error("conv3d_bf16: arrays must be 16-byte aligned");
+        return SBP_ERR_ARG;
+    }
+    ConvArgs a{static_cast<const __nv_bfloat16*>(in_dev), static_cast<const __nv_bfloat16*>(w_dev),
+               bias_dev, out_dev, nx, ny, nz, kp};
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int rc = SBP_ERR_ARG + 100;  // "no case matched" until a case launches
+#define SBP_CONV_CASE(CI, CO) \
+    if (cin == CI && cout == CO) rc = launch_conv<CI, CO>(a, relu != 0, out_f32 != 0, V, st);
+    SBP_CONV_CASE(1, 16)
+    SBP_CONV_CASE(16, 16)
+    SBP_CONV_CASE(16, 32)
+    SBP_CONV_CASE(32, 32)
+    SBP_CONV_CASE(32, 64)
+    SBP_CONV_CASE(64, 64)
+    SBP_CONV_CASE(64, 32)
+    SBP_CONV_CASE(32, 16)
+#undef SBP_CONV_CASE
+    if (rc == SBP_ERR_ARG + 100) {
+        sbp_set_error("conv3d_bf16: unsupported (cin, cout); supported: (1,16) (16,16) (16,32) "
+                      "(32,32) (32,64) (64,64) (64,32) (32,16)");
+        return SBP_ERR_ARG;
+    }
+    if (rc != SBP_OK) return rc;
+    sbp_count_launches(1);
+    return sbp_cuda_check(cudaGetLastError(), "conv3d_bf16 launch") ? SBP_ERR_CUDA : SBP_OK;
+}
+
+int sbp_cnn_status(sbp_stream stream, int* status) {
+    if (!status) {
+        sbp_set_error("cnn_status: null pointer");
+        return SBP_ERR_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (sbp_cuda_check(cudaStreamSynchronize(st), "cnn_status: synchronise")) return SBP_ERR_CUDA;
+    int v = 0, zero = 0;
+    if (sbp_cuda_check(cudaMemcpyFromSymbol(&v, g_cnn_status, sizeof(int)), "cnn_status: read") ||
+        sbp_cuda_check(cudaMemcpyToSymbol(g_cnn_status, &zero, sizeof(int)), "cnn_status: clear"))
+        return SBP_ERR_CUDA;
+    *status = v;
+    return SBP_OK;
+}
+
+}  // extern "C"

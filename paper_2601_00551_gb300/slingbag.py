@@ -129,6 +129,10 @@ _SIGS = {
                                            _Balls, ctypes.c_int, _P, _P]),
     "sbp_voxelize": (ctypes.c_int, [_Balls, _P, _P, ctypes.c_int, _P, ctypes.c_double,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+    "sbp_conv3d_bf16": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P,
+                                       ctypes.c_int, _P]),
+    "sbp_cnn_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "sbp_sync_status": (ctypes.c_int, [_P, _P]),
     "sbp_get_inside_pairs": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_longlong)]),
 }
@@ -665,5 +669,50 @@ def voxelize(balls: torch.Tensor, origin, spacing: float, dims, n_dev=None, valu
     _check("sbp_voxelize", lib.sbp_voxelize(
         _rows(balls), _dptr(values), _dptr(n_dev), balls.shape[1], org, float(spacing), nx, ny, nz,
         _dptr(scratch), _dptr(out), _stream()))
+    return out
+
+
+# --------------------------------------------------------------------------
+# volume CNN (include/slingbag.h)
+# --------------------------------------------------------------------------
+
+def conv3d(x: torch.Tensor, dims, w: torch.Tensor, bias=None, relu: bool = False,
+           out_f32: bool = False, out=None) -> torch.Tensor:
+    """3x3x3 convolution on the tensor cores (sbp_conv3d_bf16). x: bf16
+    (V, cin) channels-last for dims = (nx, ny, nz); w: bf16 (cout, kp)."""
+    lib = load_library()
+    nx, ny, nz = (int(v) for v in dims)
+    V = nx * ny * nz
+    if x.dtype != torch.bfloat16 or x.dim() != 2 or x.shape[0] != V or not x.is_contiguous():
+        raise ValueError("x must be a contiguous (V, cin) bfloat16 tensor")
+    if w.dtype != torch.bfloat16 or w.dim() != 2 or not w.is_contiguous():
+        raise ValueError("w must be a contiguous (cout, kp) bfloat16 tensor")
+    cin, (cout, kp) = x.shape[1], w.shape
+    if out is None:
+        out = torch.empty((V, cout), dtype=torch.float32 if out_f32 else torch.bfloat16,
+                          device=x.device)
+    if bias is not None and (bias.dtype != torch.float32 or bias.numel() != cout):
+        raise ValueError("bias must be float32 with cout entries")
+    _check("sbp_conv3d_bf16", lib.sbp_conv3d_bf16(
+        _dptr(x), nx, ny, nz, cin, _dptr(w), kp, _dptr(bias), cout, int(relu), _dptr(out),
+        int(out_f32), _stream()))
+    return out
+
+
+def cnn_status() -> int:
+    lib = load_library()
+    v = ctypes.c_int()
+    _check("sbp_cnn_status", lib.sbp_cnn_status(_stream(), ctypes.byref(v)))
+    return v.value
+
+
+def pack_conv_weights(w: torch.Tensor) -> torch.Tensor:
+    """(cout, 27, cin) float -> bf16 (cout, kp) with k = tap * cin + c, zero
+    padded to kp = a multiple of 64."""
+    cout, taps, cin = w.shape
+    k = taps * cin
+    kp = (k + 63) // 64 * 64
+    out = torch.zeros((cout, kp), dtype=torch.bfloat16, device=w.device)
+    out[:, :k] = w.reshape(cout, k).to(torch.bfloat16)
     return out
 
