@@ -45,3 +45,36 @@ def conv3d(x, w, bias=None) -> np.ndarray:
     if bias is not None:
         out += np.asarray(bias, dtype=np.float64)
     return out
+
+
+def das_volume(y, pos, normal, c: float, dt: float, origin, spacing: float, dims,
+               wmode: str = "clamp") -> np.ndarray:
+    """Delay-and-sum volume: voxel v (centre x_v = origin + (index + 1/2)
+    spacing) takes sum_m w_m(v) y_m(tau), tau = |x_v - s_m| / c, with y_m
+    linearly interpolated between cell centres (sample j stands for the cell
+    [j dt, (j+1) dt), centre (j + 1/2) dt; zero outside the record) and
+    w = max(0, n_m . u), u = (x_v - s_m) / d (the radiator's orientation
+    weight; wmode "none" gives w = 1). dims = (nx, ny, nz); returns float64
+    [nz][ny][nx]."""
+    y = np.asarray(y, dtype=np.float64)
+    M, T = y.shape
+    nx, ny, nz = (int(v) for v in dims)
+    cx = float(origin[0]) + (np.arange(nx) + 0.5) * spacing
+    cy = float(origin[1]) + (np.arange(ny) + 0.5) * spacing
+    cz = float(origin[2]) + (np.arange(nz) + 0.5) * spacing
+    Z, Y, X = np.meshgrid(cz, cy, cx, indexing="ij")
+    vol = np.zeros((nz, ny, nx))
+    P = np.asarray(pos, dtype=np.float64)
+    N = np.asarray(normal, dtype=np.float64)
+    for m in range(M):
+        dx, dy, dz = X - P[m, 0], Y - P[m, 1], Z - P[m, 2]
+        d = np.sqrt(dx * dx + dy * dy + dz * dz)
+        w = np.ones_like(d) if wmode == "none" else np.maximum(
+            (N[m, 0] * dx + N[m, 1] * dy + N[m, 2] * dz) / d, 0.0)
+        q = d / (c * dt) - 0.5
+        j = np.floor(q).astype(np.int64)
+        f = q - j
+        y0 = np.where((j >= 0) & (j < T), y[m, np.clip(j, 0, T - 1)], 0.0)
+        y1 = np.where((j + 1 >= 0) & (j + 1 < T), y[m, np.clip(j + 1, 0, T - 1)], 0.0)
+        vol += w * ((1.0 - f) * y0 + f * y1)
+    return vol

@@ -42,3 +42,38 @@ def test_bf16_round_matches_torch():
     a = (rng.normal(size=10000) * 10.0 ** rng.integers(-5, 5, size=10000)).astype(np.float32)
     ref = torch.from_numpy(a).to(torch.bfloat16).to(torch.float32).numpy()
     np.testing.assert_array_equal(cnn.bf16_round(a), ref)
+
+
+def test_das_single_sensor_impulse_closed_form():
+    # one sensor at the origin looking along +z, a unit value in cell j: the
+    # volume is w times the hat function of |tau/dt - 1/2 - j| on the shell
+    pos = np.array([[0.0, 0.0, 0.0]])
+    nrm = np.array([[0.0, 0.0, 1.0]])
+    c, dt, T, j = 1.5, 0.1, 64, 20
+    y = np.zeros((1, T))
+    y[0, j] = 1.0
+    origin, h, dims = (-1.6, -1.6, 0.2), 0.2, (16, 16, 16)
+    vol = cnn.das_volume(y, pos, nrm, c, dt, origin, h, dims)
+    cx = origin[0] + (np.arange(16) + 0.5) * h
+    cz = origin[2] + (np.arange(16) + 0.5) * h
+    Z, Y, X = np.meshgrid(cz, cx, cx, indexing="ij")
+    d = np.sqrt(X * X + Y * Y + Z * Z)
+    hat = np.maximum(1.0 - np.abs(d / (c * dt) - 0.5 - j), 0.0)
+    np.testing.assert_allclose(vol, (Z / d) * hat, rtol=1e-12, atol=1e-14)
+
+
+def test_das_linear_in_traces_and_weight_modes():
+    rng = np.random.default_rng(3)
+    pos = rng.normal(size=(5, 3)) * 10
+    nrm = -pos / np.linalg.norm(pos, axis=1, keepdims=True)
+    y1, y2 = rng.normal(size=(2, 5, 128))
+    args = (1.5, 0.05, (-2.0, -2.0, -2.0), 0.5, (8, 8, 8))
+    a = cnn.das_volume(y1 + 2 * y2, pos, nrm, *args)
+    b = cnn.das_volume(y1, pos, nrm, *args) + 2 * cnn.das_volume(y2, pos, nrm, *args)
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)
+    # with w = 1 a constant trace gives the sensor count wherever every delay
+    # falls inside the record
+    ones = np.ones((5, 4096))
+    v = cnn.das_volume(ones, pos, nrm, 1.5, 0.05, (-2.0, -2.0, -2.0), 0.5, (8, 8, 8),
+                       wmode="none")
+    np.testing.assert_allclose(v, 5.0, rtol=1e-12)
