@@ -78,3 +78,82 @@ def das_volume(y, pos, normal, c: float, dt: float, origin, spacing: float, dims
         y1 = np.where((j + 1 >= 0) & (j + 1 < T), y[m, np.clip(j + 1, 0, T - 1)], 0.0)
         vol += w * ((1.0 - f) * y0 + f * y1)
     return vol
+
+
+# --------------------------------------------------------------------------
+# the proposal CNN: 1 -> 16 -> 32 -> 32 channels of 3x3x3 convolutions with
+# ReLU and a 1x1x1 head with two outputs (logit, pressure) per voxel
+# --------------------------------------------------------------------------
+
+PARAM_SHAPES = (("w1", (16, 27, 1)), ("b1", (16,)), ("w2", (32, 27, 16)), ("b2", (32,)),
+                ("w3", (32, 27, 32)), ("b3", (32,)), ("wh", (2, 32)), ("bh", (2,)))
+
+
+def unpack_params(p) -> dict:
+    p = np.asarray(p, dtype=np.float64)
+    out, o = {}, 0
+    for name, shape in PARAM_SHAPES:
+        n = int(np.prod(shape))
+        out[name] = p[o:o + n].reshape(shape)
+        o += n
+    assert o == p.size
+    return out
+
+
+def scaled_input(vol) -> np.ndarray:
+    """The network input: vol / max|vol| rounded to bf16, shape (nz, ny, nx, 1)."""
+    v = np.asarray(vol, dtype=np.float64)
+    mx = np.max(np.abs(v))
+    x = (v / mx if mx > 0 else v).astype(np.float32)
+    return bf16_round(x)[..., None].astype(np.float64)
+
+
+def cnn_forward(p, vol, round_activations: bool = True) -> np.ndarray:
+    """Forward pass in float64 with bf16 weights and input; with
+    round_activations the three hidden activations are rounded to bf16 as
+    they are stored on the GPU. Returns (V, 2) in voxel order."""
+    P = unpack_params(p)
+    r = (lambda a: bf16_round(a.astype(np.float32)).astype(np.float64)) if round_activations \
+        else (lambda a: a)
+    bw = lambda w: bf16_round(w.astype(np.float32)).astype(np.float64)
+    h = scaled_input(vol)
+    for k in (1, 2, 3):
+        h = r(np.maximum(conv3d(h, bw(P[f"w{k}"]), P[f"b{k}"]), 0.0))
+    out = h @ P["wh"].T + P["bh"]
+    return out.reshape(-1, 2)
+
+
+def cnn_loss_grad(p, vol, occ, p0, pos_weight: float):
+    """Loss and its gradient with respect to the FP32 parameters, by torch
+    autograd in float64 on the CPU (activations not rounded; weights used
+    through their bf16 values, input bf16). Returns (loss0, loss1, grad)."""
+    import torch
+    import torch.nn.functional as F
+
+    P = unpack_params(p)
+    x = torch.from_numpy(scaled_input(vol)[..., 0])[None, None]  # (1, 1, nz, ny, nx)
+    t = torch.from_numpy(np.asarray(occ, dtype=np.float64).reshape(-1))
+    q0 = torch.from_numpy(np.asarray(p0, dtype=np.float64).reshape(-1))
+    leaves = {}
+    for name, _ in PARAM_SHAPES:
+        a = P[name]
+        if name.startswith("w") and name != "wh":
+            a = bf16_round(a.astype(np.float32)).astype(np.float64)
+        leaves[name] = torch.tensor(a, requires_grad=True)
+
+    def kern(w):  # (cout, 27, cin) -> (cout, cin, 3, 3, 3), tap = (dz+1)*9 + (dy+1)*3 + (dx+1)
+        co, _, ci = w.shape
+        return w.permute(0, 2, 1).reshape(co, ci, 3, 3, 3)
+
+    h = x
+    for k in (1, 2, 3):
+        h = torch.relu(F.conv3d(h, kern(leaves[f"w{k}"]), leaves[f"b{k}"], padding=1))
+    h = h[0].permute(1, 2, 3, 0).reshape(-1, 32)
+    out = h @ leaves["wh"].T + leaves["bh"]
+    z, q = out[:, 0], out[:, 1]
+    V = z.shape[0]
+    l0 = (pos_weight * t * F.softplus(-z) + (1 - t) * F.softplus(z)).sum() / V
+    l1 = (t * (q - q0) ** 2).sum() / V
+    (l0 + l1).backward()
+    grad = np.concatenate([leaves[n].grad.numpy().reshape(-1) for n, _ in PARAM_SHAPES])
+    return float(l0), float(l1), grad

@@ -77,3 +77,56 @@ def test_das_linear_in_traces_and_weight_modes():
     v = cnn.das_volume(ones, pos, nrm, 1.5, 0.05, (-2.0, -2.0, -2.0), 0.5, (8, 8, 8),
                        wmode="none")
     np.testing.assert_allclose(v, 5.0, rtol=1e-12)
+
+
+def random_params(seed=0, scale=1.0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for name, shape in cnn.PARAM_SHAPES:
+        fan = shape[1] * shape[2] if len(shape) == 3 else shape[-1]
+        out.append(rng.normal(size=shape).reshape(-1) * scale * np.sqrt(2.0 / fan)
+                   if name.startswith("w") else rng.normal(size=shape) * 0.1)
+    return np.concatenate(out).astype(np.float32)
+
+
+def test_cnn_forward_two_implementations_agree():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    vol = rng.normal(size=(5, 6, 7))
+    p = random_params(1)
+    a = cnn.cnn_forward(p, vol, round_activations=False)
+    # the same network through torch's conv3d (independent of cnn.conv3d)
+    import torch.nn.functional as F
+
+    P = cnn.unpack_params(p)
+    x = torch.from_numpy(cnn.scaled_input(vol)[..., 0])[None, None]
+    h = x
+    for k in (1, 2, 3):
+        w = cnn.bf16_round(P[f"w{k}"].astype(np.float32)).astype(np.float64)
+        co, _, ci = w.shape
+        kt = torch.from_numpy(w).permute(0, 2, 1).reshape(co, ci, 3, 3, 3)
+        h = torch.relu(F.conv3d(h, kt, torch.from_numpy(P[f"b{k}"]), padding=1))
+    out = h[0].permute(1, 2, 3, 0).reshape(-1, 32).numpy() @ P["wh"].T + P["bh"]
+    np.testing.assert_allclose(a, out, rtol=1e-10, atol=1e-10)
+
+
+def test_cnn_gradient_matches_central_differences():
+    pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    vol = rng.normal(size=(4, 4, 4))
+    occ = (rng.uniform(size=64) < 0.3).astype(np.float64)
+    p0 = rng.uniform(0.2, 1.0, size=64)
+    p = random_params(2).astype(np.float64)
+    # biases and the head enter without bf16 rounding: differentiate those
+    names = [n for n, _ in cnn.PARAM_SHAPES]
+    offs = np.cumsum([0] + [int(np.prod(s)) for _, s in cnn.PARAM_SHAPES])
+    _, _, g = cnn.cnn_loss_grad(p, vol, occ, p0, 5.0)
+    idx = [offs[names.index("b3")] + 3, offs[names.index("wh")] + 7,
+           offs[names.index("bh")] + 0, offs[names.index("bh")] + 1,
+           offs[names.index("b1")] + 2]
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = 1e-6
+        lp = sum(cnn.cnn_loss_grad(p + e, vol, occ, p0, 5.0)[:2])
+        lm = sum(cnn.cnn_loss_grad(p - e, vol, occ, p0, 5.0)[:2])
+        assert g[i] == pytest.approx((lp - lm) / 2e-6, rel=1e-5, abs=1e-9)
