@@ -407,6 +407,48 @@ int sbp_conv3d_bf16(const void* in_dev, int nx, int ny, int nz, int cin, const v
                     int kp, const float* bias_dev, int cout, int relu, void* out_dev, int out_f32,
                     sbp_stream stream);
 
+/* Delay-and-sum volume of measured traces (y_full_dev: [M][T] at the
+ * array's full rate) on a voxel grid: voxel v (centre origin + (index +
+ * 1/2) spacing, [nz][ny][nx]) takes sum_m w_m(v) y_m(|x_v - s_m| / c), the
+ * trace interpolated linearly between cell centres (j + 1/2) dt and zero
+ * outside the record, w the array's orientation weight (mode of
+ * sbp_create_array). vol_dev: float [nz][ny][nx], overwritten. */
+int sbp_das_volume(sbp_array arr, const float* y_full_dev, const double* origin3, double spacing,
+                   int nx, int ny, int nz, float* vol_dev, sbp_stream stream);
+
+/* The volume CNN of the learned proposal: a delay-and-sum volume scaled to
+ * max |.| = 1 (bf16), three 3x3x3 convolutions with ReLU (1 -> 16 -> 32 ->
+ * 32 channels, sbp_conv3d_bf16) and a 1x1x1 head with two outputs per voxel
+ * (the logit of "a source lies here" and its pressure). Weights are FP32
+ * masters (He-normal from `seed`, zero biases) with bf16 copies for the
+ * tensor cores; Adam state; activation buffers for one nx x ny x nz volume
+ * (allocated here). */
+typedef struct sbp_cnn_s* sbp_cnn;
+int sbp_cnn_create(int nx, int ny, int nz, uint64_t seed, sbp_cnn* out);
+int sbp_cnn_destroy(sbp_cnn cnn); /* synchronises the device */
+int sbp_cnn_num_params(void);
+/* Copy the FP32 parameters to (set = 0) or from (set = 1) host memory
+ * (sbp_cnn_num_params floats: w1, b1, w2, b2, w3, b3, head w, head b, each
+ * weight [cout][27][cin] or [2][32]). Synchronises. */
+int sbp_cnn_params(sbp_cnn cnn, float* host, int set);
+/* Forward pass; out_dev (float [V][2]: logit, pressure) may be NULL. */
+int sbp_cnn_forward(sbp_cnn cnn, const float* vol_dev, float* out_dev, sbp_stream stream);
+/* One Adam step (lr, beta = 0.9 / 0.999) on the loss
+ *   mean_v [ pos_weight t log(1 + e^-z) + (1 - t) log(1 + e^z) ]
+ *     + mean_v [ t (q - p)^2 ]
+ * for targets t = occ_dev (0/1) and p = p0_dev (float [V]); loss_dev
+ * (double [2]: the two terms) may be NULL. */
+int sbp_cnn_train_step(sbp_cnn cnn, const float* vol_dev, const float* occ_dev, const float* p0_dev,
+                       float pos_weight, float lr, double* loss_dev, sbp_stream stream);
+/* Proposal: forward pass, then one ball per voxel with sigmoid(z) >
+ * prob_threshold, in voxel order, at a uniformly random point of the voxel
+ * (SplitMix64 of `seed`, outputs 3v .. 3v+2), radius R, pressure q clamped
+ * to [p_min, p_max]. Writes at most n_cap balls and their number to *n_dev
+ * (device int). Allocates scratch on first use (synchronising then). */
+int sbp_cnn_propose(sbp_cnn cnn, const float* vol_dev, float prob_threshold, uint64_t seed,
+                    const double* origin3, double spacing, float R, float p_min, float p_max,
+                    sbp_balls out, int n_cap, int* n_dev, sbp_stream stream);
+
 /* Synchronise `stream` and return (then clear) the convolution status:
  * 0 = fine, 1 = a bounded wait gave up. */
 int sbp_cnn_status(sbp_stream stream, int* status);

@@ -156,4 +156,4 @@ def cnn_loss_grad(p, vol, occ, p0, pos_weight: float):
     l1 = (t * (q - q0) ** 2).sum() / V
     (l0 + l1).backward()
     grad = np.concatenate([leaves[n].grad.numpy().reshape(-1) for n, _ in PARAM_SHAPES])
-    return float(l0), float(l1), grad
+    return float(l0.detach()), float(l1.detach()), grad

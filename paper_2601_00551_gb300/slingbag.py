@@ -133,6 +133,19 @@ _SIGS = {
                                        _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P,
                                        ctypes.c_int, _P]),
     "sbp_cnn_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "sbp_das_volume": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, _P, _P]),
+    "sbp_cnn_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                      ctypes.POINTER(_P)]),
+    "sbp_cnn_destroy": (ctypes.c_int, [_P]),
+    "sbp_cnn_num_params": (ctypes.c_int, []),
+    "sbp_cnn_params": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "sbp_cnn_forward": (ctypes.c_int, [_P, _P, _P, _P]),
+    "sbp_cnn_train_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_float, ctypes.c_float, _P,
+                                          _P]),
+    "sbp_cnn_propose": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_uint64, _P,
+                                       ctypes.c_double, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_float, _Balls, ctypes.c_int, _P, _P]),
     "sbp_sync_status": (ctypes.c_int, [_P, _P]),
     "sbp_get_inside_pairs": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_longlong)]),
 }
@@ -422,6 +435,18 @@ class SensorArray:
             self.level = stages[-1].level
         elif zero_grad_mode is not None and zero_grad_mode >= 0:
             self.level = zero_grad_level
+
+    def das_volume(self, y_full: torch.Tensor, origin, spacing: float, dims, out=None):
+        """Delay-and-sum volume of [M][T] traces (sbp_das_volume):
+        float32 [nz][ny][nx]."""
+        self._check_traces(y_full, self.T)
+        nx, ny, nz = (int(v) for v in dims)
+        if out is None:
+            out = torch.empty((nz, ny, nx), dtype=torch.float32, device=self.device)
+        org = (ctypes.c_double * 3)(*[float(v) for v in origin])
+        _check("sbp_das_volume", self._lib.sbp_das_volume(
+            self._h, _dptr(y_full), org, float(spacing), nx, ny, nz, _dptr(out), _stream()))
+        return out
 
     # ------------------------------------------------------------ batched frames
     def set_frames(self, capacities) -> np.ndarray:
@@ -715,4 +740,76 @@ def pack_conv_weights(w: torch.Tensor) -> torch.Tensor:
     out = torch.zeros((cout, kp), dtype=torch.bfloat16, device=w.device)
     out[:, :k] = w.reshape(cout, k).to(torch.bfloat16)
     return out
+
+
+class VolumeCNN:
+    """The learned proposal's volume CNN (sbp_cnn_*): three tcgen05 3x3x3
+    convolutions with ReLU and a two-output head per voxel."""
+
+    def __init__(self, dims, seed: int = 1):
+        self._lib = load_library()
+        self.dims = tuple(int(v) for v in dims)
+        nx, ny, nz = self.dims
+        self.V = nx * ny * nz
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        h = _P()
+        _check("sbp_cnn_create", self._lib.sbp_cnn_create(nx, ny, nz, int(seed) & (2 ** 64 - 1),
+                                                          ctypes.byref(h)))
+        self._h = h
+        self.n_params = int(self._lib.sbp_cnn_num_params())
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check("sbp_cnn_params", self._lib.sbp_cnn_params(self._h, out.ctypes.data, 0))
+        return out
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        if p.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters")
+        _check("sbp_cnn_params", self._lib.sbp_cnn_params(self._h, p.ctypes.data, 1))
+
+    def _vol(self, vol):
+        if vol.dtype != torch.float32 or not vol.is_cuda or vol.numel() != self.V \
+                or not vol.is_contiguous():
+            raise ValueError("volume must be a contiguous float32 CUDA tensor of nx*ny*nz")
+        return _dptr(vol)
+
+    def forward(self, vol: torch.Tensor) -> torch.Tensor:
+        out = torch.empty((self.V, 2), dtype=torch.float32, device=self.device)
+        _check("sbp_cnn_forward", self._lib.sbp_cnn_forward(self._h, self._vol(vol), _dptr(out),
+                                                            _stream()))
+        return out
+
+    def train_step(self, vol, occ, p0, lr: float = 1e-3, pos_weight: float = 10.0, loss=None):
+        for t in (occ, p0):
+            if t.dtype != torch.float32 or not t.is_cuda or t.numel() != self.V:
+                raise ValueError("targets must be float32 CUDA tensors of nx*ny*nz")
+        _check("sbp_cnn_train_step", self._lib.sbp_cnn_train_step(
+            self._h, self._vol(vol), _dptr(occ), _dptr(p0), float(pos_weight), float(lr),
+            _dptr(loss), _stream()))
+
+    def propose(self, vol, origin, spacing: float, threshold: float = 0.5, seed: int = 1,
+                R: float = 0.1, p_range=(0.05, 2.0), out=None, n_dev=None):
+        if out is None:
+            out = torch.zeros((5, self.V), dtype=torch.float32, device=self.device)
+        if n_dev is None:
+            n_dev = torch.zeros(1, dtype=torch.int32, device=self.device)
+        org = (ctypes.c_double * 3)(*[float(v) for v in origin])
+        _check("sbp_cnn_propose", self._lib.sbp_cnn_propose(
+            self._h, self._vol(vol), float(threshold), int(seed) & (2 ** 64 - 1), org,
+            float(spacing), float(R), float(p_range[0]), float(p_range[1]), _rows(out),
+            out.shape[1], _dptr(n_dev), _stream()))
+        return out, n_dev
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sbp_cnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
