@@ -582,7 +582,7 @@ def run_to_residual(sb, arr, wl, y_full, init, n0, segs, zero_filter, target, se
         if it >= max_iter:
             break
     return {"seconds": hit, "iterations": it, "final_rel_residual": r,
-            "balls": int(n_dev.item())}
+            "balls": int(n_dev.item()), "elapsed_seconds": t}
 
 
 def time_to_residual(sb, arr, wl, y_full, init, n0, target=0.5, seg=10, max_iter=600):
@@ -628,7 +628,7 @@ def time_to_residual(sb, arr, wl, y_full, init, n0, target=0.5, seg=10, max_iter
 
 
 def learned_init(sb, arr, wl, y_full, init, plain_seconds, dev, n_train=96, epochs=8, grid=64,
-                 target=0.5, seg=10, max_iter=600, lr=1e-3, pos_weight=10.0):
+                 target=0.5, seg=10, max_iter=600, lr=1e-3, pos_weight=10.0, full_iters=400):
     """The learned initial proposal against the plain pipeline.
 
     Training set: `n_train` seeded vessel phantoms (the benchmark's tree
@@ -711,6 +711,16 @@ def learned_init(sb, arr, wl, y_full, init, plain_seconds, dev, n_train=96, epoc
         torch.cuda.synchronize()
     infer_s = a.elapsed_time(b) / 1e3
     n0 = int(n_prop.item())
+    # tensor-core throughput of the forward pass (three convolutions + head)
+    reps = 20
+    a.record()
+    for _ in range(reps):
+        net.forward(vol)
+    b.record()
+    torch.cuda.synchronize()
+    fwd_ms = a.elapsed_time(b) / reps
+    conv_flops = 2.0 * V * 27 * (1 * 16 + 16 * 32 + 32 * 32)
+    peak = measured_peaks().get("bf16_tflops")
     occ_truth, _ = targets(torch.from_numpy(wl.truth.stack()).to(dev))
     logit = net.forward(vol)[:, 0]
     pred = logit > 0.0
@@ -729,17 +739,37 @@ def learned_init(sb, arr, wl, y_full, init, plain_seconds, dev, n_train=96, epoc
     res = run_to_residual(sb, arr, wl, y_full, prop, n0, pro_segments(nl, seg), False, target,
                           seg, max_iter, rel)
     total = (res["seconds"] + infer_s) if res["seconds"] is not None else None
+    # the plain pipeline's final residual: a full Pro run of `full_iters` from
+    # the random cloud, then the learned proposal timed to that residual
+    plain_full = run_to_residual(sb, arr, wl, y_full, init, wl.init.n, pro_segments(nl, seg),
+                                 True, 0.0, seg, full_iters, rel)
+    r_final = plain_full["final_rel_residual"]
+    res_final = run_to_residual(sb, arr, wl, y_full, prop, n0, pro_segments(nl, seg), False,
+                                r_final, seg, 4 * full_iters, rel)
+    total_final = (res_final["seconds"] + infer_s) if res_final["seconds"] is not None else None
     net.close()
     return {
         "grid": list(dims), "spacing_mm": h, "train_phantoms": n_train, "epochs": epochs,
         "data_seconds": data_s, "train_seconds": train_s,
         "loss_per_epoch": curve, "proposal": {"balls": n0, **quality},
         "inference_seconds": infer_s,
+        "cnn_forward": {"ms": fwd_ms, "conv_tflops": conv_flops / (fwd_ms * 1e-3) / 1e12,
+                        "bf16_peak_tflops": peak,
+                        "frac_of_bf16_peak": (conv_flops / (fwd_ms * 1e-3) / 1e12 / peak)
+                        if peak else None},
         "reconstruction": res,
         "learned_seconds": total,
         "plain_seconds": plain_seconds,
         "target_rel_residual": target,
         "speedup_vs_plain": (plain_seconds / total) if (total and plain_seconds) else None,
+        "to_plain_final_residual": {
+            "plain_iterations": plain_full["iterations"],
+            "plain_seconds": plain_full["elapsed_seconds"],
+            "plain_final_rel_residual": r_final,
+            "learned": res_final,
+            "learned_seconds": total_final,
+            "speedup": (plain_full["elapsed_seconds"] / total_final) if total_final else None,
+        },
     }
 
 
