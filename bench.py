@@ -65,6 +65,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-frames", action="store_true",
                     help="skip the batched dynamic-imaging comparison")
+    ap.add_argument("--profile-cnn", action="store_true",
+                    help="only run the proposal CNN's forward pass a few times on a seeded "
+                         "64^3 volume (a short command for a profiler)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned initial proposal (CNN training and comparison)")
     ap.add_argument("--no-envelope", action="store_true",
@@ -475,10 +478,10 @@ def adj_ops_per_pair(mean_R, h):
 NCU_TRAFFIC = {
     "forward": {"sources": ["paper_2601_00551_gb300/csrc/sbp_forward.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "9a4cd47f3defc5b6", "bytes": 5.260800e6},
+                "sha256": "9a4cd47f3defc5b6", "bytes": 5.259776e6},
     "adjoint": {"sources": ["paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "8a3f5b3bff1a9855", "bytes": 3.748864e6},
+                "sha256": "1ac8c30767180fa9", "bytes": 3.752960e6},
 }
 
 
@@ -1139,8 +1142,34 @@ def run_reference(args, rank):
                     "d2h_bytes_per_step": 0}}
 
 
+def profile_cnn(passes=5):
+    """The proposal CNN's forward pass (three tcgen05 convolutions and the
+    head) on a seeded 64^3 volume, `passes` times."""
+    import torch
+
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_2601_00551_gb300 import slingbag as sb
+
+    torch.cuda.set_device(0)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    vol = torch.randn(64 ** 3, generator=g, device="cuda")
+    net = sb.VolumeCNN((64, 64, 64), seed=1)
+    for _ in range(passes):
+        net.forward(vol)
+    torch.cuda.synchronize()
+    ok = sb.cnn_status() == 0
+    net.close()
+    return {"profile_cnn": True, "passes": passes, "status_ok": ok}
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.profile_cnn:
+        print(json.dumps(profile_cnn()))
+        return 0
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
         res = run_reference(args, rank)
