@@ -76,6 +76,12 @@ def _load():
         lib.oracle_adjoint.argtypes = [L, d, d, d, d, d, L, d, d, ctypes.c_double,
                                        ctypes.c_double, L, ctypes.c_int, d, ctypes.c_int,
                                        d, d, d, d, d, d, ctypes.c_int]
+        lib.oracle_forward_gauss.restype = L
+        lib.oracle_forward_gauss.argtypes = lib.oracle_forward.argtypes
+        lib.oracle_adjoint_gauss.restype = L
+        lib.oracle_adjoint_gauss.argtypes = [L, d, d, d, d, d, L, d, d, ctypes.c_double,
+                                             ctypes.c_double, L, ctypes.c_int, d, ctypes.c_int,
+                                             d, d, d, d, d, ctypes.c_int]
         lib.oracle_downsample.restype = None
         lib.oracle_downsample.argtypes = [L, L, d, L, d]
         lib.oracle_num_procs.restype = ctypes.c_int
@@ -137,6 +143,41 @@ def adjoint(balls, pos, normal, c: float, dt: float, T: int, G, mask: int = MASK
         out[k] = outs[k]
     g = out[:5]
     return (g, out[5]) if with_abs else g
+
+
+def forward_gauss(balls, pos, normal, c: float, dt: float, T: int, wmode: str = "clamp",
+                  threads: int = 1, return_inside: bool = False):
+    """Traces of the Gaussian-profile radiator (Section 4.1's Gaussian
+    spherical sources; the R row holds the standard deviation a): cell
+    averages of p0 w (d - ct) exp(-(d - ct)^2 / 2a^2) / (2d), on every cell.
+    Pairs with d <= 6a are skipped (far-field reading) and counted."""
+    b = _f64(balls).reshape(5, -1)
+    pos = _f64(pos).reshape(-1, 3)
+    nrm = _f64(normal).reshape(-1, 3)
+    n, M = b.shape[1], pos.shape[0]
+    S = np.zeros((M, T), dtype=np.float64)
+    rows = [np.ascontiguousarray(b[k]) for k in range(5)]
+    inside = _load().oracle_forward_gauss(n, *(_ptr(r) for r in rows), M, _ptr(pos), _ptr(nrm),
+                                          float(c), float(dt), int(T), W_MODES[wmode], _ptr(S),
+                                          int(threads))
+    return (S, int(inside)) if return_inside else S
+
+
+def adjoint_gauss(balls, pos, normal, c: float, dt: float, T: int, G, mask: int = MASK_ALL,
+                  wmode: str = "clamp", threads: int = 1):
+    """Per-ball gradients (5, n: x, y, z, a, p0) of the Gaussian-profile
+    radiator for G = dL/dS."""
+    b = _f64(balls).reshape(5, -1)
+    pos = _f64(pos).reshape(-1, 3)
+    nrm = _f64(normal).reshape(-1, 3)
+    G = _f64(G).reshape(pos.shape[0], T)
+    n, M = b.shape[1], pos.shape[0]
+    rows = [np.ascontiguousarray(b[k]) for k in range(5)]
+    outs = [np.zeros(n) for _ in range(5)]
+    _load().oracle_adjoint_gauss(n, *(_ptr(r) for r in rows), M, _ptr(pos), _ptr(nrm), float(c),
+                                 float(dt), int(T), W_MODES[wmode], _ptr(G), int(mask),
+                                 *(_ptr(o) for o in outs), int(threads))
+    return np.stack(outs)
 
 
 def downsample(y, f: int) -> np.ndarray:

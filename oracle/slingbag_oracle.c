@@ -183,6 +183,117 @@ long oracle_adjoint(long n, const double* bx, const double* by, const double* bz
     return inside;
 }
 
+/*
+ * Gaussian-profile radiator (the variant of Section 4.1, where a ball is a
+ * Gaussian spherical source of peak p0 and standard deviation a0; stored in
+ * the R slot). The initial pressure p0 exp(-r^2 / (2 a^2)) launches the
+ * outgoing spherical wave p(t) = p0 w (d - c t) exp(-(d - c t)^2 / (2 a^2)) / (2 d)
+ * (the incoming half of the solution is dropped, the far field d >> a;
+ * pairs with d <= 6 a are skipped and counted). Its cell average is
+ *     S_j = p0 w a^2 [g(e_b) - g(e_a)] / (2 d c dt),   g(e) = exp(-e^2 / (2 a^2)),
+ * with e_a = d - c j dt, e_b = e_a - c dt, evaluated here on every cell of
+ * the record (no truncation of the support).
+ */
+long oracle_forward_gauss(long n, const double* bx, const double* by, const double* bz,
+                          const double* ba, const double* bp0, long M, const double* spos,
+                          const double* snrm, double c, double dt, long T, int wmode,
+                          double* S, int nthreads) {
+    long inside = 0;
+    const double h = c * dt;
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 1) reduction(+ : inside)
+#endif
+    for (long m = 0; m < M; ++m) {
+        double* row = S + m * T;
+        for (long j = 0; j < T; ++j) row[j] = 0.0;
+        const double sx = spos[3 * m], sy = spos[3 * m + 1], sz = spos[3 * m + 2];
+        const double nx = snrm[3 * m], ny = snrm[3 * m + 1], nz = snrm[3 * m + 2];
+        for (long i = 0; i < n; ++i) {
+            const double dx = bx[i] - sx, dy = by[i] - sy, dz = bz[i] - sz;
+            const double d = sqrt(dx * dx + dy * dy + dz * dz);
+            const double a = ba[i];
+            if (!(d > 6.0 * a)) {
+                inside++;
+                continue;
+            }
+            const double w = weight(wmode, (nx * dx + ny * dy + nz * dz) / d);
+            const double amp = bp0[i] * w * a * a / (2.0 * d * h);
+            for (long j = 0; j < T; ++j) {
+                const double ea = d - (double)j * h, eb = ea - h;
+                row[j] += amp * (exp(-eb * eb / (2.0 * a * a)) - exp(-ea * ea / (2.0 * a * a)));
+            }
+        }
+    }
+    return inside;
+}
+
+/* Adjoint of oracle_forward_gauss, derived from it: per pair, with
+ * K = w a^2 / (2 d c dt) and the cell sums over q_j = G_j,
+ *   A0 = sum_j G_j [g(e_b) - g(e_a)],
+ *   A1 = sum_j G_j [-(e_b / a^2) g(e_b) + (e_a / a^2) g(e_a)],     (d/dd of the bracket)
+ *   A2 = sum_j G_j [(e_b^2 / a^3) g(e_b) - (e_a^2 / a^3) g(e_a)],  (d/da of the bracket)
+ *   dL/dp0 += K A0,   dL/da += p0 (2 K / a A0 + K A2),
+ *   dL/dc  += p0 (-K / d A0 + K A1) u + p0 a^2 A0 / (2 d c dt) grad_c(w). */
+long oracle_adjoint_gauss(long n, const double* bx, const double* by, const double* bz,
+                          const double* ba, const double* bp0, long M, const double* spos,
+                          const double* snrm, double c, double dt, long T, int wmode,
+                          const double* G, int mask, double* gx, double* gy, double* gz,
+                          double* ga, double* gp0, int nthreads) {
+    long inside = 0;
+    const double h = c * dt;
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 64) reduction(+ : inside)
+#endif
+    for (long i = 0; i < n; ++i) {
+        double ax = 0, ay = 0, az = 0, aa = 0, ap = 0;
+        const double a = ba[i], p0 = bp0[i];
+        for (long m = 0; m < M; ++m) {
+            const double sx = spos[3 * m], sy = spos[3 * m + 1], sz = spos[3 * m + 2];
+            const double nx = snrm[3 * m], ny = snrm[3 * m + 1], nz = snrm[3 * m + 2];
+            const double dx = bx[i] - sx, dy = by[i] - sy, dz = bz[i] - sz;
+            const double d = sqrt(dx * dx + dy * dy + dz * dz);
+            if (!(d > 6.0 * a)) {
+                inside++;
+                continue;
+            }
+            const double ux = dx / d, uy = dy / d, uz = dz / d;
+            const double cosv = nx * ux + ny * uy + nz * uz;
+            const double w = weight(wmode, cosv);
+            const double K = w * a * a / (2.0 * d * h);
+            const double* g = G + m * T;
+            double A0 = 0.0, A1 = 0.0, A2 = 0.0;
+            for (long j = 0; j < T; ++j) {
+                const double ea = d - (double)j * h, eb = ea - h;
+                const double ga_ = exp(-ea * ea / (2.0 * a * a)), gb = exp(-eb * eb / (2.0 * a * a));
+                A0 += g[j] * (gb - ga_);
+                A1 += g[j] * (-(eb / (a * a)) * gb + (ea / (a * a)) * ga_);
+                A2 += g[j] * ((eb * eb / (a * a * a)) * gb - (ea * ea / (a * a * a)) * ga_);
+            }
+            ap += K * A0;
+            aa += p0 * (2.0 * K / a * A0 + K * A2);
+            const double gd = p0 * (-K / d * A0 + K * A1);
+            const double gw = p0 * a * a * A0 / (2.0 * d * h);
+            double wx = 0, wy = 0, wz = 0;
+            if (wmode == W_COS || (wmode == W_CLAMP && cosv > 0.0)) {
+                wx = (nx - cosv * ux) / d;
+                wy = (ny - cosv * uy) / d;
+                wz = (nz - cosv * uz) / d;
+            }
+            ax += gd * ux + gw * wx;
+            ay += gd * uy + gw * wy;
+            az += gd * uz + gw * wz;
+        }
+        gp0[i] = (mask & 1) ? ap : 0.0;
+        ga[i] = (mask & 2) ? aa : 0.0;
+        gx[i] = (mask & 4) ? ax : 0.0;
+        gy[i] = (mask & 4) ? ay : 0.0;
+        gz[i] = (mask & 4) ? az : 0.0;
+    }
+    return inside;
+}
+
 void oracle_downsample(long M, long T, const double* y, long f, double* yk) {
     const long Tk = (T + f - 1) / f;
     for (long m = 0; m < M; ++m) {
