@@ -327,6 +327,28 @@ int sbp_autotune_frames(sbp_array arr, sbp_balls packed, const int* n_dev, float
                         float* G_dev, int* fwd_chunk_out, int* adj_split_out);
 
 /* ------------------------------------------------------------------------
+ * Gaussian-profile radiator (Section 4.1: the balls as Gaussian spherical
+ * sources of peak p0 and standard deviation a0). The cloud's R row holds
+ * the standard deviation a. The initial pressure p0 exp(-r^2 / 2a^2)
+ * radiates the outgoing wave p0 w (d - ct) exp(-(d - ct)^2 / 2a^2) / (2d)
+ * (far field: pairs with d <= 6a are skipped and counted); sample j of the
+ * current level is its cell average
+ *     S_j = p0 w a^2 [g(b_{j+1}) - g(b_j)] / (2 d c dt_k),  g(b) = exp(-b^2 / 2a^2),
+ * b_j = d - j c dt_k, with the boundaries |b| >= 6a left out. Accumulated in
+ * fixed point like sbp_forward (bitwise independent of ball order).
+ * ---------------------------------------------------------------------- */
+
+/* Traces S (device [M][T_k], overwritten) of the live balls. Allocates its
+ * accumulators on first use per level size (synchronising then). */
+int sbp_forward_gauss(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap, float* S_dev,
+                      sbp_stream stream);
+
+/* Gradients (x, y, z, a, p0; overwritten, masked as in sbp_adjoint) of
+ * sum_j G_j S_j for G_dev = dL/dS ([M][T_k]). */
+int sbp_adjoint_gauss(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap,
+                      const float* G_dev, sbp_grads out, unsigned grad_mask, sbp_stream stream);
+
+/* ------------------------------------------------------------------------
  * Envelope, initialisation and voxel grid: the steps of Algorithm 1 before
  * and after the iteration (Section 4.1; Algorithm 1, envelope mesh
  * generation, ray-casting initialisation, point cloud to voxel grid).

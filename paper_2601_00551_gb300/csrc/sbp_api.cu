@@ -59,6 +59,7 @@ void free_array(sbp_array_s* a) {
     cudaFree(a->d_frame_n_new);
     cudaFree(a->d_frame_lossp);
     cudaFree(a->d_frame_pmax);
+    cudaFree(a->d_gacc);
     cudaFree(a->d_fr_yk);
     cudaFree(a->d_fr_S);
     cudaFree(a->d_fr_G);

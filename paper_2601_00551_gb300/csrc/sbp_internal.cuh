@@ -125,6 +125,9 @@ struct sbp_array_s {
     float* d_fr_S;
     float* d_fr_G;
     size_t fr_cells;
+    // Gaussian-profile forward: boundary accumulators [M][T_k + 1] (int64)
+    unsigned long long* d_gacc;
+    size_t gauss_cells;
     int fwd_chunk_frames;  // forward balls per CTA chosen by sbp_autotune_frames (0: default)
     int adj_split_frames;  // adjoint CTAs per cluster chosen by sbp_autotune_frames (0: default)
 };

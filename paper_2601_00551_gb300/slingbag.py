@@ -116,6 +116,9 @@ _SIGS = {
     "sbp_probe_fp32x2_fma": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "sbp_probe_issue": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "sbp_probe_smem_atomic": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "sbp_forward_gauss": (ctypes.c_int, [_P, _Balls, _P, ctypes.c_int, _P, _P]),
+    "sbp_adjoint_gauss": (ctypes.c_int, [_P, _Balls, _P, ctypes.c_int, _P, _Balls, ctypes.c_uint,
+                                         _P]),
     "sbp_envelope_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
     "sbp_envelope_destroy": (ctypes.c_int, [_P]),
     "sbp_envelope_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
@@ -435,6 +438,28 @@ class SensorArray:
             self.level = stages[-1].level
         elif zero_grad_mode is not None and zero_grad_mode >= 0:
             self.level = zero_grad_level
+
+    def forward_gauss(self, balls: torch.Tensor, n: torch.Tensor | None = None, out=None):
+        """Gaussian-profile traces at the current level (sbp_forward_gauss);
+        the R row of `balls` holds the standard deviation."""
+        nd = self._n(n, balls.shape[1])
+        if out is None:
+            out = torch.empty((self.M, self.Tk), dtype=torch.float32, device=self.device)
+        _check("sbp_forward_gauss", self._lib.sbp_forward_gauss(
+            self._h, _rows(balls), _dptr(nd), balls.shape[1], _dptr(out), _stream()))
+        return out
+
+    def adjoint_gauss(self, balls: torch.Tensor, G: torch.Tensor, n=None, mask: int = MASK_ALL,
+                      out=None):
+        """Gradients (5, n: x, y, z, a, p0) of the Gaussian-profile radiator."""
+        nd = self._n(n, balls.shape[1])
+        self._check_traces(G, self.Tk)
+        if out is None:
+            out = torch.empty_like(balls)
+        _check("sbp_adjoint_gauss", self._lib.sbp_adjoint_gauss(
+            self._h, _rows(balls), _dptr(nd), balls.shape[1], _dptr(G), _rows(out), mask,
+            _stream()))
+        return out
 
     def das_volume(self, y_full: torch.Tensor, origin, spacing: float, dims, out=None):
         """Delay-and-sum volume of [M][T] traces (sbp_das_volume):
