@@ -439,6 +439,11 @@ def run_native(args, rank, world, local):
             result["batched_frames"] = batched_frames(args, sb, dev)
         except Exception as exc:  # keep the main measurement if this part fails
             result["batched_frames"] = {"error": f"{type(exc).__name__}: {exc}"}
+    if not args.profile and args.workload == "vessel":
+        try:
+            result["gaussian_radiator"] = gaussian_radiator(sb, arr, wl, init, n0, dev)
+        except Exception as exc:  # keep the main measurement if this part fails
+            result["gaussian_radiator"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not (args.profile or args.no_envelope) and args.workload == "vessel":
         try:
             result["envelope_init_voxel"] = envelope_init_voxel(sb, dev)
@@ -996,6 +1001,41 @@ def envelope_init_voxel(sb, dev, reps=3):
     }
     env.close()
     return res
+
+
+def gaussian_radiator(sb, arr, wl, init, n0, dev, reps=5):
+    """The Gaussian-profile radiator on the benchmark's initial cloud (the R
+    row read as the standard deviation a) at the finest level: device time of
+    one forward and one adjoint call, and their pairs/s."""
+    import torch
+
+    nl = len(wl.levels)
+    arr.set_sampling_level(nl - 1)
+    balls = init[:, :n0].contiguous()
+    n = torch.tensor([n0], dtype=torch.int32, device=dev)
+    S = arr.forward_gauss(balls, n=n)
+    G = torch.randn(S.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(2))
+    out = torch.empty_like(balls)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    times = {}
+    for name, fn in (("forward", lambda: arr.forward_gauss(balls, n=n, out=S)),
+                     ("adjoint", lambda: arr.adjoint_gauss(balls, G, n=n, out=out))):
+        fn()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        times[name] = a.elapsed_time(b) / reps
+    pairs = float(n0) * wl.sensors.M
+    mean_a = float(np.mean(wl.init.R))
+    h = wl.c * wl.levels[-1] / wl.fs_mhz
+    return {"balls": n0, "sensors": wl.sensors.M, "level_mhz": wl.fs_mhz / wl.levels[-1],
+            "boundaries_per_pair": 12.0 * mean_a / h,
+            "forward_ms": times["forward"], "adjoint_ms": times["adjoint"],
+            "forward_pairs_per_s": pairs / (times["forward"] * 1e-3),
+            "adjoint_pairs_per_s": pairs / (times["adjoint"] * 1e-3)}
 
 
 def run_e2e(args, sb, arr, wl, y_host, init, n0, n_cap, stages, adam, pairs_per_step, dev):
