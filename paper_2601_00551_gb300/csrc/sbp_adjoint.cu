@@ -340,9 +340,18 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
 #pragma unroll 1
             for (int s = 0; s < cnt; s += 2) {
                 const float4 saA = sa_g[s], sbA = sb_g[s], saB = sa_g[s + 1], sbB = sb_g[s + 1];
+                // dL/dp0 is continuous in the distance (the cell values are), so the
+                // p0-only pass takes it in plain float; the full gradient, whose
+                // centre and radius terms jump at the window's ends, needs the
+                // exact one
                 const PairDist2 pd =
-                    sbp_pair_distance2(f2(cx), f2(cy), f2(cz), make_float2(saA.x, saB.x),
-                                       make_float2(saA.y, saB.y), make_float2(saA.z, saB.z));
+                    P0_ONLY ? sbp_pair_distance2_f32(f2(cx), f2(cy), f2(cz),
+                                                     make_float2(saA.x, saB.x),
+                                                     make_float2(saA.y, saB.y),
+                                                     make_float2(saA.z, saB.z))
+                            : sbp_pair_distance2(f2(cx), f2(cy), f2(cz), make_float2(saA.x, saB.x),
+                                                 make_float2(saA.y, saB.y),
+                                                 make_float2(saA.z, saB.z));
                 PairWindow wa, wb;
                 bool okA, okB;
                 sbp_window2(pd.dh, pd.dl, f2(R), g, wa, wb, okA, okB);
