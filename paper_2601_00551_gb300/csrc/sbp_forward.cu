@@ -171,14 +171,18 @@ fwd_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     __shared__ float s_red[kGroupWarps * 7];
     __shared__ float s_box[7];
     __shared__ int s_jlo[32];
-    const int c0 = blockIdx.x * chunk;
+    // one-dimensional grid, chunk-major: the CTAs of one ball chunk (one per
+    // group of 32 sensors) are consecutive, so live chunks come first
+    const int groups = (g.M + 31) / 32;
+    const int gid = (int)(blockIdx.x % (unsigned)groups);
+    const int c0 = (int)(blockIdx.x / (unsigned)groups) * chunk;
     const FrameSlot fs = sbp_frame_of(ft, c0);
     if (c0 >= fs.end) return;  // uniform over the block
     const int c1 = min(fs.end, c0 + chunk);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int Tk = g.Tk, M = g.M;
     unsigned long long* __restrict__ acc = acc_all + (size_t)fs.f * M * Tk;
-    const int m = blockIdx.y * 32 + lane;
+    const int m = gid * 32 + lane;
     const bool sv = m < M;
 
     sbp_chunk_box(b, c0, c1, s_red, s_box);
@@ -283,7 +287,7 @@ fwd_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
                 const long long v = (long long)hi * (1LL << kLoBits) + (long long)lo;
                 const int ln = t & 31, rel = t >> 5;
                 const int j = s_jlo[ln] + p * kWindow + rel;
-                atomicAdd(acc + (size_t)(blockIdx.y * 32 + ln) * Tk + j, (unsigned long long)v);
+                atomicAdd(acc + (size_t)(gid * 32 + ln) * Tk + j, (unsigned long long)v);
                 sacc[t] = 0u;
                 sacc[kWindow * 32 + t] = 0u;
             }
@@ -372,7 +376,7 @@ int sbp_launch_forward(sbp_array_s* a, const BallsDev& b, const int* n_dev, int 
     fwd_pmax_kernel<<<std::max(1, std::min(4 * a->sm_count, (n_cap + 255) / 256)), 256, 0,
                       st>>>(b.p0, ft, &a->d_state->pmax_bits);
     if (sbp_cuda_check(cudaGetLastError(), "forward: pmax launch")) return SBP_ERR_CUDA;
-    dim3 grid((n_cap + chunk - 1) / chunk, groups);
+    const unsigned grid = (unsigned)(((long long)n_cap + chunk - 1) / chunk * groups);
     fwd_group_kernel<<<grid, kGroupWarps * 32, smem, st>>>(
         b, ft, a->d_sens, g, chunk, &a->d_state->pmax_bits, a->d_state, a->d_acc);
     if (sbp_cuda_check(cudaGetLastError(), "forward: accumulate launch")) return SBP_ERR_CUDA;
@@ -406,7 +410,7 @@ int sbp_launch_forward_frames(sbp_array_s* a, const BallsDev& b, const int* n_de
     const int pmax_blocks = std::max(1, std::min(4 * a->sm_count / F, total / F / 256 + 1));
     fwd_pmax_kernel<<<dim3(pmax_blocks, F), 256, 0, st>>>(b.p0, ft, a->d_frame_pmax);
     if (sbp_cuda_check(cudaGetLastError(), "forward_frames: pmax launch")) return SBP_ERR_CUDA;
-    dim3 grid((total + chunk - 1) / chunk, groups);
+    const unsigned grid = (unsigned)(((long long)total + chunk - 1) / chunk * groups);
     fwd_group_kernel<<<grid, kGroupWarps * 32, smem, st>>>(b, ft, a->d_sens, g, chunk,
                                                            a->d_frame_pmax, a->d_state, a->d_acc);
     if (sbp_cuda_check(cudaGetLastError(), "forward_frames: accumulate launch"))
@@ -532,7 +536,7 @@ extern "C" int sbp_forward_static(const float* sensors_dev, int M, double c_mm_p
     fwd_pmax_kernel<<<std::max(1, std::min(4 * sms, (n_cap + 255) / 256)), 256, 0, st>>>(
         b.p0, ft, &state->pmax_bits);
     if (sbp_cuda_check(cudaGetLastError(), "forward_static: pmax launch")) return SBP_ERR_CUDA;
-    dim3 grid((n_cap + chunk - 1) / chunk, groups);
+    const unsigned grid = (unsigned)(((long long)n_cap + chunk - 1) / chunk * groups);
     fwd_group_kernel<<<grid, kGroupWarps * 32, smem, st>>>(b, ft, sensors_dev, g, chunk,
                                                            &state->pmax_bits, state, acc);
     if (sbp_cuda_check(cudaGetLastError(), "forward_static: accumulate launch"))
