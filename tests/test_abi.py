@@ -63,3 +63,34 @@ def test_create_array_rejects_bad_arguments_on_the_host(lib):
     zero = (ctypes.c_float * 3)(0, 0, 0)
     assert f(pos, zero, 1, 1.5, 40.0, 128, fac, 1, 10, None, ctypes.byref(out)) == -6  # |n| = 0
     assert out.value is None
+
+
+def test_new_entry_points_reject_bad_arguments_on_the_host(lib):
+    """The envelope, voxel grid, convolution and CNN entry points check their
+    arguments (and build the hull) on the host before any CUDA call."""
+    P = ctypes.c_void_p
+    out = ctypes.c_void_p()
+    f = lib.sbp_envelope_create
+    f.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+    pts = (ctypes.c_float * 30)(*([0.0] * 30))
+    assert f(pts, 3, ctypes.byref(out)) == -1  # fewer than 4 sensors
+    # ten sensors in the plane z = 1.5: no closed envelope
+    flat = (ctypes.c_float * 30)(*[v for i in range(10) for v in (float(i % 4), float(i // 4), 1.5)])
+    assert f(flat, 10, ctypes.byref(out)) == -1
+    nan = (ctypes.c_float * 12)(*([0.0] * 11 + [float("nan")]))
+    assert f(nan, 4, ctypes.byref(out)) == -6  # SBP_ERR_NUMERIC
+    g = lib.sbp_conv3d_bf16
+    g.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P,
+                  ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P]
+    assert g(None, 4, 4, 4, 16, None, 448, None, 32, 1, None, 0, None) == -1
+    buf = (ctypes.c_char * 64)()
+    addr = (ctypes.addressof(buf) + 15) // 16 * 16
+    assert g(addr, 4, 4, 4, 16, addr, 430, None, 32, 1, addr, 0, None) == -1  # kp % 64
+    assert g(addr, 4, 4, 4, 16, addr, 448, None, 48, 1, addr, 0, None) == -1  # unsupported cout
+    c = lib.sbp_cnn_create
+    c.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                  ctypes.POINTER(ctypes.c_void_p)]
+    assert c(0, 4, 4, 1, ctypes.byref(out)) == -1
+    v = lib.sbp_voxelize
+    v.restype = ctypes.c_int
+    assert lib.sbp_cnn_num_params() == 16 * 27 + 16 + 32 * 27 * 16 + 32 + 32 * 27 * 32 + 32 + 64 + 2
