@@ -483,10 +483,10 @@ def adj_ops_per_pair(mean_R, h):
 NCU_TRAFFIC = {
     "forward": {"sources": ["paper_2601_00551_gb300/csrc/sbp_forward.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "d6e8625ff88f66bd", "bytes": 5.263104e6},
+                "sha256": "785753c46f6b9bf1", "bytes": 5.263104e6},
     "adjoint": {"sources": ["paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "b4a4573eef46563c", "bytes": 3.753216e6},
+                "sha256": "e57ff03724d5cd3b", "bytes": 3.753216e6},
 }
 
 

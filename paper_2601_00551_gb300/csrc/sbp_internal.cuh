@@ -338,49 +338,13 @@ struct PairWindow {
     float b0, bL;
 };
 
-__device__ __forceinline__ bool sbp_window_ff(float dh, float dl, float R, const LevelGeo& g,
-                                              PairWindow& w) {
-    const float h = g.h_hi;
-    const float xr = dh * g.inv_h;
-    if (!(xr < (float)g.Tk + 4096.0f) || !(dh + dl > R)) return false;  // also NaN
-    const int jr = (int)floorf(xr);
-    const float e = sbp_boundary(dh, dl, jr, g.h_hi, g.h_lo);  // b_jr
-    const float tL = fminf(fmaxf((e - R) * g.inv_h, -1e6f), 1e6f);
-    const float tH = fminf(fmaxf((e + R) * g.inv_h, -1e6f), 1e6f);
-    int kL = (int)floorf(tL) + 1;
-    int kH = (int)ceilf(tH) - 1;
-    float b0 = fmaf(-(float)kL, h, e);
-    if (b0 >= R) {
-        ++kL;
-        b0 -= h;
-    } else if (b0 + h < R) {
-        --kL;
-        b0 += h;
-    }
-    float bL = fmaf(-(float)kH, h, e);
-    if (bL <= -R) {
-        --kH;
-        bL += h;
-    } else if (bL - h > -R) {
-        ++kH;
-        bL -= h;
-    }
-    w.jL = jr + kL;
-    w.jH = jr + kH;
-    w.b0 = b0;
-    w.bL = bL;
-    return w.jH >= w.jL && w.jL >= 1 && w.jL - 1 < g.Tk;
-}
-
-__device__ __forceinline__ bool sbp_window(const PairDist& pd, float R, const LevelGeo& g,
-                                           PairWindow& w) {
-    return sbp_window_ff(pd.dh, pd.dl, R, g, w);
-}
-
-// sbp_window for two pairs. The arithmetic is that of sbp_window_ff, with
-// the cell indices carried as exact small integers in float (below 2^24) and
-// converted once at the end; the fix-ups of the two ends are selects. Pairs
-// whose window is not valid (ok = false) may carry any values.
+// The window of two pairs at once. For each: jr = floor(d / h), the offset
+// e = b_jr taken in float-float (sbp_boundary), then jL and jH from small
+// integer steps kL = floor((e - R) / h) + 1, kH = ceil((e + R) / h) - 1
+// carried as exact floats (below 2^24), the end offsets b0 = e - kL h and
+// bL = e - kH h, and one exact fix-up step of each end against R (as
+// selects). Valid when d > R, the far end lies inside the record and jH >= jL
+// >= 1; pairs whose window is not valid (ok = false) may carry any values.
 __device__ __forceinline__ void sbp_window2(float2 dh, float2 dl, float2 R, const LevelGeo& g,
                                             PairWindow& wa, PairWindow& wb, bool& okA,
                                             bool& okB) {
