@@ -70,6 +70,8 @@ def parse_args(argv=None):
                          "64^3 volume (a short command for a profiler)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned initial proposal (CNN training and comparison)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 1M-ball x 1024-sensor configuration")
     ap.add_argument("--no-envelope", action="store_true",
                     help="skip the envelope / initialisation / voxel grid timing")
     ap.add_argument("--profile", action="store_true",
@@ -440,6 +442,15 @@ def run_native(args, rank, world, local):
         except Exception as exc:  # keep the main measurement if this part fails
             result["batched_frames"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.profile and args.workload == "vessel":
+        try:
+            result["autograd_memory"] = autograd_memory(sb, arr, wl, init, n0, dev)
+        except Exception as exc:  # keep the main measurement if this part fails
+            result["autograd_memory"] = {"error": f"{type(exc).__name__}: {exc}"}
+        if not args.no_large:
+            try:
+                result["large_config"] = large_config(sb, dev)
+            except Exception as exc:  # keep the main measurement if this part fails
+                result["large_config"] = {"error": f"{type(exc).__name__}: {exc}"}
         try:
             result["gaussian_radiator"] = gaussian_radiator(sb, arr, wl, init, n0, dev)
         except Exception as exc:  # keep the main measurement if this part fails
@@ -1036,6 +1047,80 @@ def gaussian_radiator(sb, arr, wl, init, n0, dev, reps=5):
             "forward_ms": times["forward"], "adjoint_ms": times["adjoint"],
             "forward_pairs_per_s": pairs / (times["forward"] * 1e-3),
             "adjoint_pairs_per_s": pairs / (times["adjoint"] * 1e-3)}
+
+
+def large_config(sb, dev, reps=3):
+    """The large configuration (1M balls in a 40 mm cube, 1024 sensors on a
+    (60, 60, 40) mm cap, T = 2048 / 4096 / 8192 at 20 / 40 / 80 MHz): device
+    time of one forward and one adjoint call of the 1M-ball initial cloud at
+    every level, their pairs/s, and the roofline fraction of the 80 MHz calls."""
+    import torch
+
+    import workloads
+
+    wl = workloads.large()
+    n = wl.init.n
+    arr = sb.SensorArray(wl.sensors.pos, wl.sensors.normal, wl.c, wl.fs_mhz, wl.T, wl.levels,
+                         n_cap=n)
+    B = torch.from_numpy(wl.init.stack()).to(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    pairs = float(n) * wl.sensors.M
+    out = {"workload": wl.name, "pairs_per_call": pairs, "levels": {}}
+    mean_R = float(np.mean(wl.init.R))
+    for k, f in enumerate(wl.levels):
+        arr.set_sampling_level(k)
+        S = arr.forward(B)
+        G = torch.randn(S.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(k))
+        gout = torch.empty_like(B)
+        res = {}
+        for name, fn in (("forward", lambda: arr.forward(B, out=S)),
+                         ("adjoint", lambda: arr.adjoint(B, G, out=gout))):
+            fn()
+            a.record()
+            for _ in range(reps):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            res[name + "_ms"] = a.elapsed_time(b) / reps
+        h = wl.c * f / wl.fs_mhz
+        res["forward_pairs_per_s"] = pairs / (res["forward_ms"] * 1e-3)
+        res["adjoint_pairs_per_s"] = pairs / (res["adjoint_ms"] * 1e-3)
+        peak = 152 * 128 * 2070e6
+        res["forward_frac"] = pairs * FWD_OPS_PER_PAIR / (res["forward_ms"] * 1e-3) / peak
+        res["adjoint_frac"] = pairs * adj_ops_per_pair(mean_R, h) / (res["adjoint_ms"] * 1e-3) / peak
+        out["levels"][f"{wl.fs_mhz / f:g}MHz"] = res
+    if arr.sync_status() != 0:
+        raise RuntimeError("device status latched in the large configuration")
+    arr.close()
+    return out
+
+
+def autograd_memory(sb, arr, wl, init, n0, dev):
+    """Per-level trace checkpointing: the autograd Function saves only the
+    cloud and recomputes the geometry in the adjoint. Peak device memory of
+    one radiate() forward + backward at the finest level of the vessel
+    workload, against what storing every pair's window would take (pairs x
+    mean window cells x 4 bytes)."""
+    import torch
+
+    nl = len(wl.levels)
+    k = nl - 1
+    x, y, z, R, p0 = (init[c, :n0].clone().requires_grad_(True) for c in range(5))
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    torch.cuda.reset_peak_memory_stats()
+    S = sb.radiate(arr, x, y, z, R, p0, level=k)
+    (S * S).sum().backward()
+    torch.cuda.synchronize()
+    peak = torch.cuda.max_memory_allocated() - base
+    h = wl.c * wl.levels[k] / wl.fs_mhz
+    cells = 2.0 * float(np.mean(wl.init.R)) / h + 1.0
+    pairs = float(n0) * wl.sensors.M
+    return {"balls": n0, "sensors": wl.sensors.M, "T": arr.level_info(k)[0],
+            "peak_bytes_forward_backward": int(peak),
+            "stored_windows_bytes_estimate": int(pairs * cells * 4),
+            "ratio": pairs * cells * 4 / max(1, peak)}
 
 
 def run_e2e(args, sb, arr, wl, y_host, init, n0, n_cap, stages, adam, pairs_per_step, dev):

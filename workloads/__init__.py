@@ -375,3 +375,19 @@ def envelope(M: int = 2006, axes=(48.0, 60.0, 26.0), n_init: int = 200_000,
         f"{n_init // 1000}k balls, 0.2 mm voxels over 80 x 104 x 40 mm",
         sens, n_init, inset, (0.05, 0.2), (0.0, 1.0), 1, (-40.0, -52.0, -20.0), 0.2,
         (400, 520, 200))
+
+
+def large(n_truth: int = 1_000_000, n_init: int = 1_000_000, M: int = 1024, T: int = 8192,
+          sort: bool = True) -> Workload:
+    """The large case: a seeded vessel-tree phantom of 1M balls in a 40 mm
+    cube, an initial cloud of 1M uniform balls (R ~ U(0.05, 0.2), p0 ~ U(0, 1),
+    Morton order), 1024 sensors on the z >= 0 half of a (60, 60, 40) mm
+    ellipsoid with normals jittered by up to 15 deg, and sampling at
+    80 MHz with T = 8192 (levels f = 4, 2, 1: 20 / 40 / 80 MHz)."""
+    sens = ellipsoid_cap(M, (60.0, 60.0, 40.0), 15.0, seed=2)
+    init = uniform_balls(n_init, 20.0, 0.05, 0.2, 0.0, 1.0, seed=1)
+    if sort:
+        init = init.take(morton_order(init, 20.0))
+    truth = vessel_tree(n_truth, half=20.0, seed=0)
+    return Workload("large: 1M balls x 1024 sensors, 20/40/80 MHz, T=2048/4096/8192", sens,
+                    init, truth, 80.0, T, (4, 2, 1), half=20.0)
