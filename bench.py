@@ -68,12 +68,17 @@ def parse_args(argv=None):
     ap.add_argument("--profile-cnn", action="store_true",
                     help="only run the proposal CNN's forward pass a few times on a seeded "
                          "64^3 volume (a short command for a profiler)")
+    ap.add_argument("--profile-large", action="store_true",
+                    help="only tune and run one forward and one adjoint of the 1M-ball x "
+                         "1024-sensor configuration at 80 MHz (a short command for a profiler)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned initial proposal (CNN training and comparison)")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 1M-ball x 1024-sensor configuration")
     ap.add_argument("--no-envelope", action="store_true",
                     help="skip the envelope / initialisation / voxel grid timing")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default tiles (no per-level autotuning before the warm-up)")
     ap.add_argument("--profile", action="store_true",
                     help="short run for a profiler: no clocks, e2e or CPU baseline")
     return ap.parse_args(argv)
@@ -310,6 +315,13 @@ def run_native(args, rank, world, local):
                                **GROW)
             arr.filter_grow(balls, grads, n_dev, mode=sb.GROW, grow=gp, extra=[mom])
 
+    # tiles per level, tuned (untimed) on the initial cloud
+    tiles = {}
+    if not args.no_autotune:
+        for k in range(nl):
+            arr.set_sampling_level(k)
+            tiles[k] = arr.autotune(init, n=n_init)
+
     # warm-up; the workload is deterministic, so every step sees the same counts
     for _ in range(max(0, args.warmup)):
         step(False)
@@ -403,6 +415,9 @@ def run_native(args, rank, world, local):
             "l2": "flushed before every timed step (512 MB write)",
             "parallelism": f"replicas x{world}",
             "launch": launch_mode,
+            "tiles": ({f"{wl.fs_mhz / wl.levels[k]:g}MHz": {"forward_balls_per_cta": c or "default",
+                                                           "adjoint_ctas_per_cluster": sp or "default"}
+                       for k, (c, sp) in tiles.items()} if tiles else "default"),
         },
         "gpu_launches": int(launches),
         "kernel_ms": {"forward": {str(k): v for k, v in fwd_ms.items()},
@@ -448,7 +463,7 @@ def run_native(args, rank, world, local):
             result["autograd_memory"] = {"error": f"{type(exc).__name__}: {exc}"}
         if not args.no_large:
             try:
-                result["large_config"] = large_config(sb, dev)
+                result["large_config"] = large_config(sb, dev, tune=not args.no_autotune)
             except Exception as exc:  # keep the main measurement if this part fails
                 result["large_config"] = {"error": f"{type(exc).__name__}: {exc}"}
         try:
@@ -494,10 +509,10 @@ def adj_ops_per_pair(mean_R, h):
 NCU_TRAFFIC = {
     "forward": {"sources": ["paper_2601_00551_gb300/csrc/sbp_forward.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "785753c46f6b9bf1", "bytes": 5.263104e6},
+                "sha256": "d8648d4dab2f1158", "bytes": 5.262848e6},
     "adjoint": {"sources": ["paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "e57ff03724d5cd3b", "bytes": 3.753216e6},
+                "sha256": "569ca33c90f16739", "bytes": 3.752704e6},
 }
 
 
@@ -1049,11 +1064,12 @@ def gaussian_radiator(sb, arr, wl, init, n0, dev, reps=5):
             "adjoint_pairs_per_s": pairs / (times["adjoint"] * 1e-3)}
 
 
-def large_config(sb, dev, reps=3):
+def large_config(sb, dev, reps=3, tune=True):
     """The large configuration (1M balls in a 40 mm cube, 1024 sensors on a
     (60, 60, 40) mm cap, T = 2048 / 4096 / 8192 at 20 / 40 / 80 MHz): device
     time of one forward and one adjoint call of the 1M-ball initial cloud at
-    every level, their pairs/s, and the roofline fraction of the 80 MHz calls."""
+    every level with the default tiles and with the level's autotuned tiles,
+    their pairs/s and roofline fractions (tuned tiles)."""
     import torch
 
     import workloads
@@ -1074,15 +1090,25 @@ def large_config(sb, dev, reps=3):
         G = torch.randn(S.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(k))
         gout = torch.empty_like(B)
         res = {}
-        for name, fn in (("forward", lambda: arr.forward(B, out=S)),
-                         ("adjoint", lambda: arr.adjoint(B, G, out=gout))):
-            fn()
-            a.record()
-            for _ in range(reps):
+
+        def timed():
+            for name, fn in (("forward", lambda: arr.forward(B, out=S)),
+                             ("adjoint", lambda: arr.adjoint(B, G, out=gout))):
                 fn()
-            b.record()
-            torch.cuda.synchronize()
-            res[name + "_ms"] = a.elapsed_time(b) / reps
+                a.record()
+                for _ in range(reps):
+                    fn()
+                b.record()
+                torch.cuda.synchronize()
+                res[name + "_ms"] = a.elapsed_time(b) / reps
+
+        timed()
+        res["default_tiles_ms"] = {"forward": res["forward_ms"], "adjoint": res["adjoint_ms"]}
+        if tune:
+            c, sp = arr.autotune(B, G=G)
+            res["tiles"] = {"forward_balls_per_cta": c or "default",
+                            "adjoint_ctas_per_cluster": sp or "default"}
+            timed()
         h = wl.c * f / wl.fs_mhz
         res["forward_pairs_per_s"] = pairs / (res["forward_ms"] * 1e-3)
         res["adjoint_pairs_per_s"] = pairs / (res["adjoint_ms"] * 1e-3)
@@ -1290,8 +1316,44 @@ def profile_cnn(passes=5):
     return {"profile_cnn": True, "passes": passes, "status_ok": ok}
 
 
+def profile_large():
+    """The large configuration at its finest level (1M balls x 1024 sensors,
+    80 MHz, T = 8192): the tile autotuner (5 forward and 5 adjoint settings,
+    6 launches each), then one forward and one adjoint call with the tuned
+    tiles (a short command for a profiler)."""
+    import torch
+
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_2601_00551_gb300 import slingbag as sb
+
+    import workloads
+
+    torch.cuda.set_device(0)
+    wl = workloads.large()
+    arr = sb.SensorArray(wl.sensors.pos, wl.sensors.normal, wl.c, wl.fs_mhz, wl.T, wl.levels,
+                         n_cap=wl.init.n)
+    B = torch.from_numpy(wl.init.stack()).cuda()
+    k = len(wl.levels) - 1
+    arr.set_sampling_level(k)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    G = torch.randn((wl.sensors.M, arr.Tk), generator=g, device="cuda")
+    tiles = arr.autotune(B, G=G)
+    arr.forward(B)
+    arr.adjoint(B, G)
+    torch.cuda.synchronize()
+    ok = arr.sync_status() == 0
+    arr.close()
+    return {"profile_large": True, "tiles": tiles, "status_ok": ok}
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.profile_large:
+        print(json.dumps(profile_large()))
+        return 0
     if args.profile_cnn:
         print(json.dumps(profile_cnn()))
         return 0

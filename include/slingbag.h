@@ -199,6 +199,27 @@ int sbp_residual(sbp_array arr, const float* S_dev, const float* y_k_dev, float*
 int sbp_adjoint(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap,
                 const float* G_dev, sbp_grads out, unsigned grad_mask, sbp_stream stream);
 
+/* Tile choice of the single-cloud sbp_forward and sbp_adjoint at level k
+ * (a launch parameter only: the forward is bitwise identical for every
+ * choice, the adjoint differs by float summation order). fwd_chunk: balls
+ * per forward CTA, 0 (default: 512, fewer for small clouds) or a power of
+ * two in [32, 1024]; adj_split: adjoint CTAs per cluster, 0 (default 4), 1,
+ * 2, 4 or 8. SBP_ERR_ARG for other values, SBP_ERR_LEVEL for k out of range. */
+int sbp_set_tiles(sbp_array arr, int k, int fwd_chunk, int adj_split);
+int sbp_get_tiles(sbp_array arr, int k, int* fwd_chunk, int* adj_split);
+
+/* Tile autotuner for the current level: times sbp_forward with the default
+ * tile and with 128, 256, 512 and 1024 balls per CTA, and sbp_adjoint (all
+ * components) with the default and with 1, 2, 4 and 8 CTAs per cluster, on
+ * the given cloud; keeps for this level (as sbp_set_tiles would) the
+ * fastest choice of each if it beats the default by more than 3%, else the
+ * default (reported as 0), and reports them in the optional outputs. S_dev [M][T_k] is overwritten; G_dev [M][T_k] is read only (its
+ * values change the timings little: pass a residual of the data). Allocates
+ * 5 n_cap floats of scratch and synchronises. On a failed launch the level
+ * keeps the defaults and the error is returned. */
+int sbp_autotune(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap, float* S_dev,
+                 const float* G_dev, int* fwd_chunk_out, int* adj_split_out);
+
 /* Filter and grow the point cloud in place (stable compaction/expansion).
  * mode SBP_KEEP_NEG / SBP_KEEP_NONPOS / SBP_DROP_ZERO: zero-gradient
  * filtering on grads.gp0 (computed by sbp_adjoint with G = -2 y_k, i.e.

@@ -558,7 +558,8 @@ int sbp_launch_adjoint(sbp_array_s* a, const BallsDev& b, const int* n_dev, int 
     o.o[3] = out.gR;
     o.o[4] = out.gp0;
     const FrameTable ft{1, nullptr, n_dev, n_cap};
-    return launch_adj(ft, n_cap, kAdjSplit, b, a->d_sens, g, G, mask, o, st);
+    const int split = a->adj_split_lvl[a->level] ? a->adj_split_lvl[a->level] : kAdjSplit;
+    return launch_adj(ft, n_cap, split, b, a->d_sens, g, G, mask, o, st);
 }
 
 // All frames of the packed layout in one launch (sbp_adjoint_frames).

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -270,6 +271,112 @@ int sbp_adjoint(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap, con
     }
     return sbp_launch_adjoint(arr, to_dev(balls), n_dev, n_cap, G_dev, out, grad_mask,
                               as_stream(stream));
+}
+
+namespace {
+
+bool fwd_chunk_ok(int c) { return c == 0 || (c >= 32 && c <= SBP_FRAME_ALIGN && !(c & (c - 1))); }
+bool adj_split_ok(int s) { return s == 0 || s == 1 || s == 2 || s == 4 || s == 8; }
+
+}  // namespace
+
+int sbp_set_tiles(sbp_array arr, int k, int fwd_chunk, int adj_split) {
+    if (int e = check_array(arr, "set_tiles")) return e;
+    if (k < 0 || k >= arr->n_levels) {
+        sbp_set_error("set_tiles: level out of range");
+        return SBP_ERR_LEVEL;
+    }
+    if (!fwd_chunk_ok(fwd_chunk) || !adj_split_ok(adj_split)) {
+        sbp_set_error("set_tiles: chunk must be 0 or a power of two in [32, 1024], split 0, 1, 2, 4 or 8");
+        return SBP_ERR_ARG;
+    }
+    arr->fwd_chunk_lvl[k] = fwd_chunk;
+    arr->adj_split_lvl[k] = adj_split;
+    return SBP_OK;
+}
+
+int sbp_get_tiles(sbp_array arr, int k, int* fwd_chunk, int* adj_split) {
+    if (int e = check_array(arr, "get_tiles")) return e;
+    if (k < 0 || k >= arr->n_levels) {
+        sbp_set_error("get_tiles: level out of range");
+        return SBP_ERR_LEVEL;
+    }
+    if (fwd_chunk) *fwd_chunk = arr->fwd_chunk_lvl[k];
+    if (adj_split) *adj_split = arr->adj_split_lvl[k];
+    return SBP_OK;
+}
+
+int sbp_autotune(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap, float* S_dev,
+                 const float* G_dev, int* fwd_chunk_out, int* adj_split_out) {
+    if (int e = check_array(arr, "autotune")) return e;
+    if (int e = check_cap(arr, n_cap, "autotune")) return e;
+    if (!balls_ok(balls) || !S_dev || !G_dev) {
+        sbp_set_error("autotune: null pointer");
+        return SBP_ERR_ARG;
+    }
+    cudaStream_t s;
+    if (sbp_cuda_check(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "autotune: stream"))
+        return SBP_ERR_CUDA;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const BallsDev bd = to_dev(balls);
+    const size_t cap = (size_t)n_cap;
+    float* g = nullptr;
+    int rc = SBP_OK;
+    if (sbp_cuda_check(cudaMalloc(&g, sizeof(float) * 5 * std::max<size_t>(cap, 1)),
+                       "autotune: alloc"))
+        rc = SBP_ERR_CUDA;
+    // a failed launch latches rc and ends the search with the defaults
+    auto time_it = [&](auto&& fn) -> float {
+        if (rc != SBP_OK) return 1e30f;
+        rc = fn();  // warm-up
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 5 && rc == SBP_OK; ++r) rc = fn();
+        cudaEventRecord(e1, s);
+        if (sbp_cuda_check(cudaEventSynchronize(e1), "autotune: run")) rc = SBP_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return rc == SBP_OK ? ms : 1e30f;
+    };
+    // the default tile (0) is timed first; another choice replaces it only
+    // when it is faster by more than kMargin, so timing noise and a cloud
+    // that differs from the one tuned on do not move the choice for little
+    constexpr float kMargin = 0.97f;
+    const int k = arr->level;
+    auto pick = [&](std::initializer_list<int> cands, int* field, auto&& launch) {
+        *field = 0;
+        const float base = time_it(launch);
+        float best = base * kMargin;
+        int choice = 0;
+        for (int c : cands) {
+            *field = c;
+            const float ms = time_it(launch);
+            if (ms < best) {
+                best = ms;
+                choice = c;
+            }
+        }
+        *field = choice;
+        return choice;
+    };
+    const sbp_grads gr{g, g + cap, g + 2 * cap, g + 3 * cap, g + 4 * cap};
+    int best_chunk = pick({128, 256, 512, 1024}, &arr->fwd_chunk_lvl[k], [&] {
+        return sbp_launch_forward(arr, bd, n_dev, n_cap, S_dev, s);
+    });
+    int best_split = pick({1, 2, 4, 8}, &arr->adj_split_lvl[k], [&] {
+        return sbp_launch_adjoint(arr, bd, n_dev, n_cap, G_dev, gr, SBP_MASK_ALL, s);
+    });
+    if (rc != SBP_OK) best_chunk = best_split = 0;
+    arr->fwd_chunk_lvl[k] = best_chunk;
+    arr->adj_split_lvl[k] = best_split;
+    if (fwd_chunk_out) *fwd_chunk_out = best_chunk;
+    if (adj_split_out) *adj_split_out = best_split;
+    cudaFree(g);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    return rc;
 }
 
 int sbp_filter_grow(sbp_array arr, sbp_balls balls, sbp_grads grads, float* const* extra,

@@ -26,8 +26,9 @@
 //                 lane's window is privatised in shared memory laid out
 //                 [cell][lane], so the shared atomics of a warp never
 //                 conflict on a bank, and flushed once per CTA to the global
-//                 int64 accumulators with global atomics. Windows longer than
-//                 the shared buffer are covered in several passes.
+//                 int64 accumulators with global atomics. Where a window is
+//                 longer than the shared buffer, the impulses past its end
+//                 go straight to the global accumulators.
 //                 A 64-bit shared atomic add costs several times a 32-bit one
 //                 on this GPU, so each int64 impulse v is added as two 32-bit
 //                 words: v mod 2^32 and v >> kLoBits (signed). The high word
@@ -98,12 +99,16 @@ __device__ __forceinline__ void fwd_add32(unsigned int* lo, int v) {
 }
 
 // Adds one pair's six second-difference impulses to the lane's column of the
-// split accumulator: three at cells ra .. ra+2 (relative to this pass) from
-// the first-cell, ramp and slope coefficients fa, f1, f2, three at rb .. rb+2
-// from the last-cell coefficient fe, with L = jH - jL ramp cells. Cells
-// outside [0, lim] belong to another pass or lie past the record.
-__device__ __forceinline__ void fwd_emit(unsigned int* col, int ra, int rb, int L, int lim,
-                                         float fa, float fe, float f1, float f2) {
+// split accumulator: three at cells ra .. ra+2 (relative to the lane's first
+// window cell) from the first-cell, ramp and slope coefficients fa, f1, f2,
+// three at rb .. rb+2 from the last-cell coefficient fe, with L = jH - jL
+// ramp cells. Cells in [0, lim] are held in shared memory; other cells
+// inside the record (relative cells -base .. glim) are added straight to the
+// lane's global accumulator row grow (indexed relative to the window start);
+// cells past the record are dropped (they cannot reach a stored sample).
+__device__ __forceinline__ void fwd_emit(unsigned int* col, unsigned long long* grow, int ra,
+                                         int rb, int L, int lim, int base, int glim, float fa,
+                                         float fe, float f1, float f2) {
     const bool fast_a = ra >= 0 && ra + 2 <= lim, fast_b = rb >= 0 && rb + 2 <= lim;
     // impulses are sums of at most four coefficient terms; below 2^28 each
     // they fit in 32 bits (the usual case)
@@ -130,16 +135,21 @@ __device__ __forceinline__ void fwd_emit(unsigned int* col, int ra, int rb, int 
     // the two triples overlap the impulses add up)
     const long long ia0 = qa, ia1 = q1 - 2 * qa, ia2 = qa - q1 + q2;
     const long long ib0 = qe - q1 - Lq2, ib1 = q1 + Lq2 - q2 - 2 * qe, ib2 = qe;
+    auto put = [&](int r, long long v) {
+        if (r >= 0 && r <= lim)
+            fwd_add(col + r * 32, v);
+        else if (r >= -base && r <= glim)
+            atomicAdd(grow + r, (unsigned long long)v);
+    };
     if (fast_a) {
         unsigned int* a = col + ra * 32;
         fwd_add(a, ia0);
         fwd_add(a + 32, ia1);
         fwd_add(a + 64, ia2);
     } else {
-        const long long v[3] = {ia0, ia1, ia2};
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-            if (ra + q >= 0 && ra + q <= lim) fwd_add(col + (ra + q) * 32, v[q]);
+        put(ra, ia0);
+        put(ra + 1, ia1);
+        put(ra + 2, ia2);
     }
     if (fast_b) {
         unsigned int* c = col + rb * 32;
@@ -147,10 +157,9 @@ __device__ __forceinline__ void fwd_emit(unsigned int* col, int ra, int rb, int 
         fwd_add(c + 32, ib1);
         fwd_add(c + 64, ib2);
     } else {
-        const long long v[3] = {ib0, ib1, ib2};
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-            if (rb + q >= 0 && rb + q <= lim) fwd_add(col + (rb + q) * 32, v[q]);
+        put(rb, ib0);
+        put(rb + 1, ib1);
+        put(rb + 2, ib2);
     }
 }
 
@@ -201,11 +210,11 @@ fwd_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     int wmax = max(0, jhi - jlo + 1);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-    const int passes = (wmax + kWindow - 1) / kWindow;  // identical in every warp
+    if (wmax == 0) return;  // no lane's sensor can be reached (uniform over the block)
     if (warp == 0) s_jlo[lane] = jlo;
     // only the cells some lane can touch are cleared (and later flushed)
-    const int used0 = min(wmax, kWindow) * 32;
-    for (int t = threadIdx.x; t < used0; t += blockDim.x) {
+    const int used = min(wmax, kWindow) * 32;
+    for (int t = threadIdx.x; t < used; t += blockDim.x) {
         sacc[t] = 0u;
         sacc[kWindow * 32 + t] = 0u;
     }
@@ -215,84 +224,84 @@ fwd_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     const float h = g.h_hi;
     const float d2c = -2.0f * h * h;
     unsigned int inside = 0;
-    for (int p = 0; p < passes; ++p) {
-        const int base = jlo + p * kWindow;  // this lane's first cell in this pass
-        // last cell of this pass that may be stored: inside the record and the buffer
-        const int lim = min(jhi - base, kWindow - 1);
-        unsigned int* col = sacc + lane;
-        // The warp takes its balls two at a time (i and i + kGroupWarps) and
-        // evaluates both pairs of its lane's sensor side by side; an odd last
-        // ball is paired with an empty one. Every ball goes through the same
-        // instructions, so its impulses do not depend on its partner.
-        for (int i = c0 + warp; i < c1; i += 2 * kGroupWarps) {
-            const int iB = i + kGroupWarps;
-            const bool hasB = iB < c1;
-            const float2 cx = make_float2(b.x[i], hasB ? b.x[iB] : 0.0f);
-            const float2 cy = make_float2(b.y[i], hasB ? b.y[iB] : 0.0f);
-            const float2 cz = make_float2(b.z[i], hasB ? b.z[iB] : 0.0f);
-            const float2 R2 = make_float2(b.R[i], hasB ? b.R[iB] : 0.0f);
-            const float2 P2 = make_float2(b.p0[i], hasB ? b.p0[iB] : 0.0f);
-            if ((P2.x == 0.0f && P2.y == 0.0f) || !sv) continue;
-            const PairDist2 pd = sbp_pair_distance2(cx, cy, cz, f2(sx), f2(sy), f2(sz));
-            // inside test and window, per pair
-            bool okA = P2.x != 0.0f, okB = P2.y != 0.0f;
-            if (okA && !(pd.dh.x + pd.dl.x > R2.x)) {
-                if (p == 0) ++inside;
-                okA = false;
-            }
-            if (okB && !(pd.dh.y + pd.dl.y > R2.y)) {
-                if (p == 0) ++inside;
-                okB = false;
-            }
-            PairWindow wa, wb;
-            bool wA, wB;
-            sbp_window2(pd.dh, pd.dl, R2, g, wa, wb, wA, wB);
-            okA = okA && wA;
-            okB = okB && wB;
-            if (!(okA || okB)) continue;
-            const float2 cosv = f2mul(
-                f2fma(f2(nx), pd.dx, f2fma(f2(ny), pd.dy, f2mul(f2(nz), pd.dz))), pd.rd);
-            float actA, actB;
-            const float2 w = make_float2(sbp_weight(g.wmode, cosv.x, actA),
-                                         sbp_weight(g.wmode, cosv.y, actB));
-            okA = okA && w.x != 0.0f;
-            okB = okB && w.y != 0.0f;
-            if (!(okA || okB)) continue;
-            const float2 b0 = make_float2(wa.b0, wb.b0), bL = make_float2(wa.bL, wb.bL);
-            // K 2^F = p0 w 2^F / (4 d h)
-            const float2 Ks = f2mul(f2mul(f2mul(P2, w), f2(g.inv_4h * scale)), pd.rd);
-            const float2 ra = make_float2(fmaxf(R2.x - b0.x, 0.0f), fmaxf(R2.y - b0.y, 0.0f));
-            const float2 re = make_float2(fmaxf(R2.x + bL.x, 0.0f), fmaxf(R2.y + bL.y, 0.0f));
-            const float2 fa = f2mul(f2mul(Ks, ra), f2add(R2, b0));
-            const float2 fe = f2neg(f2mul(f2mul(Ks, re), f2sub(R2, bL)));
-            const float2 f1 = f2mul(f2mul(Ks, f2(h)), f2fma(f2(2.0f), b0, f2(-h)));
-            const float2 fq = f2mul(Ks, f2(d2c));
-            if (okA) fwd_emit(col, wa.jL - 1 - base, wa.jH - base, wa.jH - wa.jL, lim, fa.x, fe.x,
-                              f1.x, fq.x);
-            if (okB) fwd_emit(col, wb.jL - 1 - base, wb.jH - base, wb.jH - wb.jL, lim, fa.y, fe.y,
-                              f1.y, fq.y);
+    // The lane's cells jlo .. jlo + kWindow - 1 are held in shared memory;
+    // impulses further out (a chunk whose window is longer than the buffer)
+    // go straight to the global accumulators.
+    const int base = jlo;
+    const int lim = min(jhi - base, kWindow - 1);  // last shared cell that may be stored
+    const int glim = Tk - 1 - base;                // last cell inside the record
+    unsigned int* col = sacc + lane;
+    unsigned long long* grow = acc + (size_t)m * Tk + base;
+    // The warp takes its balls two at a time (i and i + kGroupWarps) and
+    // evaluates both pairs of its lane's sensor side by side; an odd last
+    // ball is paired with an empty one. Every ball goes through the same
+    // instructions, so its impulses do not depend on its partner.
+    for (int i = c0 + warp; i < c1; i += 2 * kGroupWarps) {
+        const int iB = i + kGroupWarps;
+        const bool hasB = iB < c1;
+        const float2 cx = make_float2(b.x[i], hasB ? b.x[iB] : 0.0f);
+        const float2 cy = make_float2(b.y[i], hasB ? b.y[iB] : 0.0f);
+        const float2 cz = make_float2(b.z[i], hasB ? b.z[iB] : 0.0f);
+        const float2 R2 = make_float2(b.R[i], hasB ? b.R[iB] : 0.0f);
+        const float2 P2 = make_float2(b.p0[i], hasB ? b.p0[iB] : 0.0f);
+        if ((P2.x == 0.0f && P2.y == 0.0f) || !sv) continue;
+        const PairDist2 pd = sbp_pair_distance2(cx, cy, cz, f2(sx), f2(sy), f2(sz));
+        // inside test and window, per pair
+        bool okA = P2.x != 0.0f, okB = P2.y != 0.0f;
+        if (okA && !(pd.dh.x + pd.dl.x > R2.x)) {
+            ++inside;
+            okA = false;
         }
-        __syncthreads();
-        // flush this pass: lanes of a warp read 32 consecutive words (one cell
-        // of all 32 sensors), recombine the two halves and clear them
-        const int used = min(wmax - p * kWindow, kWindow) * 32;
-        for (int t = threadIdx.x; t < used; t += blockDim.x) {
-            const unsigned int wa = sacc[t];
-            const int hi = (int)sacc[kWindow * 32 + t];
-            if (wa | (unsigned)hi) {
-                // the low word holds the whole sum mod 2^32; the sum of the
-                // low kLoBits-bit parts lies in [0, 2^32), so it is that word
-                // minus hi * 2^kLoBits, mod 2^32
-                const unsigned int lo = wa - ((unsigned int)hi << kLoBits);
-                const long long v = (long long)hi * (1LL << kLoBits) + (long long)lo;
-                const int ln = t & 31, rel = t >> 5;
-                const int j = s_jlo[ln] + p * kWindow + rel;
-                atomicAdd(acc + (size_t)(gid * 32 + ln) * Tk + j, (unsigned long long)v);
-                sacc[t] = 0u;
-                sacc[kWindow * 32 + t] = 0u;
-            }
+        if (okB && !(pd.dh.y + pd.dl.y > R2.y)) {
+            ++inside;
+            okB = false;
         }
-        __syncthreads();
+        PairWindow wa, wb;
+        bool wA, wB;
+        sbp_window2(pd.dh, pd.dl, R2, g, wa, wb, wA, wB);
+        okA = okA && wA;
+        okB = okB && wB;
+        if (!(okA || okB)) continue;
+        const float2 cosv = f2mul(
+            f2fma(f2(nx), pd.dx, f2fma(f2(ny), pd.dy, f2mul(f2(nz), pd.dz))), pd.rd);
+        float actA, actB;
+        const float2 w = make_float2(sbp_weight(g.wmode, cosv.x, actA),
+                                     sbp_weight(g.wmode, cosv.y, actB));
+        okA = okA && w.x != 0.0f;
+        okB = okB && w.y != 0.0f;
+        if (!(okA || okB)) continue;
+        const float2 b0 = make_float2(wa.b0, wb.b0), bL = make_float2(wa.bL, wb.bL);
+        // K 2^F = p0 w 2^F / (4 d h)
+        const float2 Ks = f2mul(f2mul(f2mul(P2, w), f2(g.inv_4h * scale)), pd.rd);
+        const float2 ra = make_float2(fmaxf(R2.x - b0.x, 0.0f), fmaxf(R2.y - b0.y, 0.0f));
+        const float2 re = make_float2(fmaxf(R2.x + bL.x, 0.0f), fmaxf(R2.y + bL.y, 0.0f));
+        const float2 fa = f2mul(f2mul(Ks, ra), f2add(R2, b0));
+        const float2 fe = f2neg(f2mul(f2mul(Ks, re), f2sub(R2, bL)));
+        const float2 f1 = f2mul(f2mul(Ks, f2(h)), f2fma(f2(2.0f), b0, f2(-h)));
+        const float2 fq = f2mul(Ks, f2(d2c));
+        if (okA)
+            fwd_emit(col, grow, wa.jL - 1 - base, wa.jH - base, wa.jH - wa.jL, lim, base, glim,
+                     fa.x, fe.x, f1.x, fq.x);
+        if (okB)
+            fwd_emit(col, grow, wb.jL - 1 - base, wb.jH - base, wb.jH - wb.jL, lim, base, glim,
+                     fa.y, fe.y, f1.y, fq.y);
+    }
+    __syncthreads();
+    // flush: lanes of a warp read 32 consecutive words (one cell of all 32
+    // sensors), recombine the two halves and add them to the global rows
+    for (int t = threadIdx.x; t < used; t += blockDim.x) {
+        const unsigned int wa = sacc[t];
+        const int hi = (int)sacc[kWindow * 32 + t];
+        if (wa | (unsigned)hi) {
+            // the low word holds the whole sum mod 2^32; the sum of the low
+            // kLoBits-bit parts lies in [0, 2^32), so it is that word minus
+            // hi * 2^kLoBits, mod 2^32
+            const unsigned int lo = wa - ((unsigned int)hi << kLoBits);
+            const long long v = (long long)hi * (1LL << kLoBits) + (long long)lo;
+            const int ln = t & 31, rel = t >> 5;
+            const int j = s_jlo[ln] + rel;
+            atomicAdd(acc + (size_t)(gid * 32 + ln) * Tk + j, (unsigned long long)v);
+        }
     }
     if (inside) atomicAdd(&st->inside_pairs, (unsigned long long)inside);
 }
@@ -358,11 +367,15 @@ int sbp_launch_forward(sbp_array_s* a, const BallsDev& b, const int* n_dev, int 
                        float* S, cudaStream_t st) {
     const LevelGeo g = sbp_level_geo(a, a->level);
     const int groups = (g.M + 31) / 32;
-    // consecutive balls per CTA: up to 1024, fewer for small clouds so that
-    // the grid still covers the GPU
-    int chunk = kChunk;
-    while (chunk > 32 && (long long)((n_cap + chunk - 1) / chunk) * groups < 4LL * a->sm_count)
-        chunk >>= 1;
+    // consecutive balls per CTA: the level's tuned size if sbp_autotune chose
+    // one, else kChunk, fewer for small clouds so that the grid still covers
+    // the GPU
+    int chunk = a->fwd_chunk_lvl[a->level];
+    if (chunk < 32 || chunk > SBP_FRAME_ALIGN || (SBP_FRAME_ALIGN % chunk)) {
+        chunk = kChunk;
+        while (chunk > 32 && (long long)((n_cap + chunk - 1) / chunk) * groups < 4LL * a->sm_count)
+            chunk >>= 1;
+    }
     const size_t smem = (size_t)2 * kWindow * 32 * sizeof(unsigned int);
     if (sbp_cuda_check(cudaFuncSetAttribute(fwd_group_kernel,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -112,6 +112,11 @@ _SIGS = {
                                               _P]),
     "sbp_autotune_frames": (ctypes.c_int, [_P, _Balls, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int)]),
+    "sbp_set_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "sbp_get_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int)]),
+    "sbp_autotune": (ctypes.c_int, [_P, _Balls, _P, ctypes.c_int, _P, _P,
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "sbp_probe_fp32_fma": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "sbp_probe_fp32x2_fma": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "sbp_probe_issue": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
@@ -321,6 +326,33 @@ class SensorArray:
             self._h, k, _dptr(y_full), _dptr(out if y_full is not None else None), _stream()))
         self.level = k
         return out
+
+    def set_tiles(self, k: int, fwd_chunk: int = 0, adj_split: int = 0):
+        """Tile choice of the forward and adjoint at level k (sbp_set_tiles; 0 = default)."""
+        _check("sbp_set_tiles", self._lib.sbp_set_tiles(self._h, k, fwd_chunk, adj_split))
+
+    def get_tiles(self, k: int):
+        c, sp = ctypes.c_int(), ctypes.c_int()
+        _check("sbp_get_tiles", self._lib.sbp_get_tiles(self._h, k, ctypes.byref(c),
+                                                        ctypes.byref(sp)))
+        return c.value, sp.value
+
+    def autotune(self, balls: torch.Tensor, n=None, G: torch.Tensor | None = None):
+        """Tile autotuner at the current level (sbp_autotune); returns and keeps
+        (forward balls per CTA, adjoint CTAs per cluster). G defaults to
+        standard normal traces."""
+        Tk = self.Tk
+        S = torch.empty((self.M, Tk), dtype=torch.float32, device=self.device)
+        if G is None:
+            G = torch.randn((self.M, Tk), dtype=torch.float32, device=self.device)
+        self._check_traces(G, Tk)
+        nd = self._n(n, balls.shape[1])
+        c, sp = ctypes.c_int(), ctypes.c_int()
+        torch.cuda.synchronize()
+        _check("sbp_autotune", self._lib.sbp_autotune(
+            self._h, _rows(balls), _dptr(nd), balls.shape[1], _dptr(S), _dptr(G),
+            ctypes.byref(c), ctypes.byref(sp)))
+        return c.value, sp.value
 
     def _check_traces(self, t, T):
         if t.dtype != torch.float32 or not t.is_cuda or tuple(t.shape) != (self.M, T) \

@@ -529,3 +529,49 @@ def test_reconstruct_with_softplus_refinement_matches_oracle(sb):
     out = balls[:, :bo.shape[1]].cpu().numpy()
     np.testing.assert_allclose(out, bo, rtol=0, atol=1e-4)
     assert np.all(out[3] > 0)
+
+
+# ------------------------------------------------------------- tile choices
+
+def test_tile_choices_and_autotune(sb):
+    """The forward's balls per CTA change only the launch: every choice gives
+    bitwise the same traces. Every adjoint cluster split is at parity with the
+    oracle. The autotuner keeps a valid choice per level and the results stay
+    the same."""
+    wl = workloads.vessel(n_init=20000, n_truth=2000)
+    b = wl.init.stack()
+    arr = make_array(sb, wl, wl.levels, b.shape[1])
+    balls = torch.from_numpy(b).cuda()
+    pick = np.random.default_rng(7).choice(b.shape[1], 150, replace=False)
+    rng = np.random.default_rng(8)
+    with pytest.raises(sb.SlingbagError):
+        arr.set_tiles(0, 48, 0)
+    with pytest.raises(sb.SlingbagError):
+        arr.set_tiles(0, 0, 3)
+    with pytest.raises(sb.SlingbagError):
+        arr.set_tiles(len(wl.levels), 256, 2)
+    for k, f in enumerate(wl.levels):
+        Tk = wl.T // f
+        arr.set_sampling_level(k)
+        S0 = arr.forward(balls).clone()
+        for chunk in (32, 128, 256, 1024):
+            arr.set_tiles(k, chunk, 0)
+            assert torch.equal(arr.forward(balls), S0), (f, chunk)
+        G = rng.normal(size=(wl.sensors.M, Tk)).astype(np.float32)
+        Gd = torch.from_numpy(G).cuda()
+        ref = oracle.adjoint(b[:, pick], wl.sensors.pos, wl.sensors.normal, wl.c, dt_of(wl, f),
+                             Tk, G.astype(np.float64), threads=threads())
+        for split in (1, 2, 8):
+            arr.set_tiles(k, 0, split)
+            assert arr.get_tiles(k) == (0, split)
+            g = arr.adjoint(balls, Gd).cpu().numpy()
+            for c in range(5):
+                assert rel_l2(g[c, pick], ref[c]) <= GRAD_TOL, (f, split, c)
+        arr.set_tiles(k, 0, 0)
+        chunk, split = arr.autotune(balls, G=Gd)
+        assert chunk in (0, 128, 256, 512, 1024) and split in (0, 1, 2, 4, 8)
+        assert arr.get_tiles(k) == (chunk, split)
+        assert torch.equal(arr.forward(balls), S0)
+        g = arr.adjoint(balls, Gd).cpu().numpy()
+        for c in range(5):
+            assert rel_l2(g[c, pick], ref[c]) <= GRAD_TOL, (f, "tuned", c)
