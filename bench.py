@@ -512,7 +512,7 @@ NCU_TRAFFIC = {
                 "sha256": "d8648d4dab2f1158", "bytes": 5.262848e6},
     "adjoint": {"sources": ["paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "569ca33c90f16739", "bytes": 3.752704e6},
+                "sha256": "42b9d0b5d91595be", "bytes": 3.753472e6},
 }
 
 

@@ -25,20 +25,22 @@
 //   residual     G = 2 (S - y), L = sum (S - y)^2 (fixed-order last-block reduction)
 //   adj_group    A cluster of kAdjSplit CTAs shares one chunk of consecutive
 //                balls (one thread per ball) and splits the sensors between
-//                its CTAs. Each CTA walks its sensors in groups of 16. For
-//                each group it stages, per sensor, the window of G that the
-//                chunk's bounding box can reach into shared memory
-//                ([sensor][cell]) with asynchronous copies into one of two
-//                buffers, the next group's copies in flight while the
-//                current group is evaluated. Every thread takes the group's
+//                its CTAs. Each CTA walks its sensors in groups. For each
+//                group it stages, per sensor, the window of G that the
+//                chunk's bounding box can reach, packed one after another
+//                into one of two shared buffers with asynchronous copies,
+//                the next group's copies in flight while the current group
+//                is evaluated; a group takes as many sensor pairs as fill
+//                the buffer. Every thread takes the group's
 //                sensors two at a time, evaluating both pairs side by side
 //                in packed float2 arithmetic. A ball's five gradient
 //                components stay in its thread's registers across the CTA's
 //                sensors. The first CTA of the cluster then adds the other
 //                CTAs' partial sums through distributed shared memory, in
 //                rank order, and writes every ball's gradients exactly once.
-//                No atomics. Windows that do not fit (an unsorted cloud) are
-//                read from global memory instead.
+//                No atomics. A window longer than half a buffer (e.g. an
+//                unsorted cloud) is not staged: its pairs read the global
+//                row instead.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -54,8 +56,8 @@ namespace {
 
 constexpr int kAdjThreads = 128;  // balls (threads) per adjoint CTA
 constexpr int kAdjSplit = 4;      // default CTAs per cluster, each taking 1/split of the sensors
-constexpr int kAdjGroup = 16;     // sensors staged per round
-constexpr int kAdjWindow = 224;   // cells per sensor staged in shared memory
+constexpr int kAdjGroup = 16;     // staging buffer size: kAdjGroup windows of the mean length below
+constexpr int kAdjWindow = 224;   // mean cells per staged window the buffer is sized for
 constexpr int kAdjWindowP0 = 128; // the same for the p0-only adjoint, which keeps more CTAs per SM
 constexpr int kAdjMeta = 128;     // sensors whose set-up is held in shared memory at once
 
@@ -167,7 +169,7 @@ struct GradOut {
 // E0 = sum_q d_q and E1 = sum_q q d_q. Reads the staged window when it holds
 // every needed cell, else the global row.
 __device__ __forceinline__ void adj_window_sums(const float* __restrict__ sGrow, int jlo, int len,
-                                                bool staged, const float* __restrict__ Gm,
+                                                const float* __restrict__ Gm,
                                                 int jL, int jH, int Tk, float& gf, float& gl,
                                                 float& E0, float& E1) {
     const int L = min(jH, Tk) - jL;
@@ -175,7 +177,7 @@ __device__ __forceinline__ void adj_window_sums(const float* __restrict__ sGrow,
     E1 = 0.f;
     // the box bound puts cells jL-1 .. min(jH, Tk-1) inside the staged
     // window; checked anyway so that no read can leave it
-    if (staged && jL - 1 >= jlo && min(jH, Tk - 1) - jlo < len) {
+    if (jL - 1 >= jlo && min(jH, Tk - 1) - jlo < len) {
         const float* Gw = sGrow - jlo + jL;
         gf = Gw[-1];
         gl = jH < Tk ? Gw[jH - jL] : 0.0f;
@@ -212,17 +214,22 @@ template <bool P0_ONLY>
 __global__ void __launch_bounds__(kAdjThreads, P0_ONLY ? 8 : 6)
 adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, LevelGeo g,
                  const float* __restrict__ G_all, unsigned mask, GradOut out) {
-    // two staging buffers [sensor][cell]; after the last group the first one
-    // holds this CTA's partial sums
-    constexpr int kWin = P0_ONLY ? kAdjWindowP0 : kAdjWindow;
-    __shared__ __align__(16) float sG[2][kAdjGroup * kWin];
+    // two staging buffers of kCap cells, each holding the windows of one
+    // group of sensors packed one after another; after the last group the
+    // first one holds this CTA's partial sums
+    constexpr int kCap = kAdjGroup * (P0_ONLY ? kAdjWindowP0 : kAdjWindow);
+    constexpr int kWin = kCap / 2;  // longest window staged: a pair of them fills a buffer
+    __shared__ __align__(16) float sG[2][kCap];
     __shared__ float4 s_sa[kAdjMeta + 1];  // sx, sy, sz, nx (+1: partner of an odd last sensor)
-    __shared__ float4 s_sb[kAdjMeta + 1];  // ny, nz, jlo, len (as int bits)
-    __shared__ int s_glen[kAdjMeta / kAdjGroup];  // longest window of each group
+    __shared__ float4 s_sb[kAdjMeta + 1];  // ny, nz, jlo, staged length (as int bits; 0: not staged)
+    __shared__ int s_off[kAdjMeta + 1];    // offset of the staged window in its group's buffer
+    __shared__ int s_gfirst[kAdjMeta / 2 + 2];  // first sensor of each group, then the count
+    __shared__ int s_ng;
     __shared__ float s_red[(kAdjThreads / 32) * 7];
     __shared__ float s_box[7];
     float* const s_part = sG[0];  // this CTA's partial sums, [ball][5]
-    static_assert(kAdjThreads * 5 <= kAdjGroup * kWin, "partials do not fit");
+    static_assert(kAdjThreads * 5 <= kCap, "partials do not fit");
+    static_assert(2 * kWin <= kCap, "a pair of staged windows must fit one buffer");
     cg::cluster_group cluster = cg::this_cluster();
     const int c0 = blockIdx.x * kAdjThreads;
     const FrameSlot fs = sbp_frame_of(ft, c0);
@@ -279,44 +286,64 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     const int m_begin = min(M, part * per), m_end = min(M, m_begin + per);
     // The share is walked in blocks of up to kAdjMeta sensors whose positions,
     // normals and cell ranges are set up once, and within a block in groups of
-    // kAdjGroup sensors. The residual windows of group q + 1 are copied into
-    // the other staging buffer asynchronously while group q is evaluated, so
-    // one barrier per group both publishes a group and frees the buffer of
-    // the group before.
+    // consecutive sensor pairs whose residual windows, packed one after
+    // another, fill one staging buffer (a window longer than kWin is not
+    // staged: its pairs read the global row). Short windows (coarse levels,
+    // compact chunks) so make long groups and few barriers. The windows of
+    // group q + 1 are copied into the other buffer asynchronously while group
+    // q is evaluated, so one barrier per group both publishes a group and
+    // frees the buffer of the group before.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int mb = m_begin; mb < m_end; mb += kAdjMeta) {
         const int nsens = min(kAdjMeta, m_end - mb);
-        const int ng = (nsens + kAdjGroup - 1) / kAdjGroup;
         __syncthreads();  // the previous block is done with every shared buffer
-        for (int t = threadIdx.x; t < ng; t += blockDim.x) s_glen[t] = 0;
-        __syncthreads();
         for (int t = threadIdx.x; t < nsens; t += blockDim.x) {
             const int m = mb + t;
             const float sx = sens[m], sy = sens[M + m], sz = sens[2 * M + m];
             int jlo, jhi;
             sbp_box_cells(sx, sy, sz, s_box, g, jlo, jhi);
-            const int len = max(0, jhi - jlo + 1);
+            int len = max(0, jhi - jlo + 1);
+            if (len > kWin) len = 0;
             s_sa[t] = make_float4(sx, sy, sz, sens[3 * M + m]);
             s_sb[t] = make_float4(sens[4 * M + m], sens[5 * M + m], __int_as_float(jlo),
                                   __int_as_float(len));
-            atomicMax(&s_glen[t / kAdjGroup], len);
         }
         if ((nsens & 1) && threadIdx.x == 0) {  // odd count: a partner that no ball reaches
             s_sa[nsens] = make_float4(1e6f, 1e6f, 1e6f, 0.0f);
             s_sb[nsens] = make_float4(0.0f, 1.0f, __int_as_float(0), __int_as_float(0));
+            s_off[nsens] = 0;
         }
         __syncthreads();
-        // asynchronous copy of group q's windows into buffer q & 1 (skipped
-        // for a group whose longest window does not fit: it reads L2 instead)
+        if (threadIdx.x == 0) {  // greedy packing of sensor pairs into groups
+            int ng = 0, fill = 0;
+            s_gfirst[0] = 0;
+            for (int p = 0; p < nsens; p += 2) {
+                const int la = __float_as_int(s_sb[p].w);
+                const int lb = p + 1 < nsens ? __float_as_int(s_sb[p + 1].w) : 0;
+                if (fill + la + lb > kCap) {  // fill > 0 here, as 2 kWin <= kCap
+                    s_gfirst[++ng] = p;
+                    fill = 0;
+                }
+                s_off[p] = fill;
+                if (p + 1 < nsens) s_off[p + 1] = fill + la;
+                fill += la + lb;
+            }
+            s_gfirst[++ng] = nsens;
+            s_ng = ng;
+        }
+        __syncthreads();
+        const int ng = s_ng;
+        // asynchronous copy of group q's windows into buffer q & 1, a warp per
+        // sensor
         auto stage = [&](int q) {
-            if (s_glen[q] > kWin) return;
-            const int gb = q * kAdjGroup, cntq = min(kAdjGroup, nsens - gb);
             float* dst = sG[q & 1];
-            for (int s = 0; s < cntq; ++s) {
-                const float4 sb = s_sb[gb + s];
+            for (int s = s_gfirst[q] + warp; s < s_gfirst[q + 1]; s += kAdjThreads / 32) {
+                const float4 sb = s_sb[s];
                 const int jlo = __float_as_int(sb.z), len = __float_as_int(sb.w);
-                const float* row = G + (size_t)(mb + gb + s) * Tk + jlo;
-                for (int r = threadIdx.x; r < len; r += blockDim.x)
-                    __pipeline_memcpy_async(dst + s * kWin + r, row + r, sizeof(float));
+                const float* row = G + (size_t)(mb + s) * Tk + jlo;
+                float* d = dst + s_off[s];
+                for (int r = lane; r < len; r += 32)
+                    __pipeline_memcpy_async(d + r, row + r, sizeof(float));
             }
         };
         stage(0);
@@ -328,18 +355,20 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
                 stage(q + 1);
                 __pipeline_commit();
             }
-            const int gbase = q * kAdjGroup;
-            const int cnt = min(kAdjGroup, nsens - gbase);
+            const int gbase = s_gfirst[q];
+            const int cnt = s_gfirst[q + 1] - gbase;
             const int m0 = mb + gbase;
-            const bool staged = s_glen[q] <= kWin;  // uniform
             const float4* __restrict__ sa_g = s_sa + gbase;
             const float4* __restrict__ sb_g = s_sb + gbase;
+            const int* __restrict__ off_g = s_off + gbase;
             const float* __restrict__ sGb = sG[q & 1];
             if (!valid) continue;
             // two sensors at a time, evaluated side by side in the halves of float2
 #pragma unroll 1
             for (int s = 0; s < cnt; s += 2) {
                 const float4 saA = sa_g[s], sbA = sb_g[s], saB = sa_g[s + 1], sbB = sb_g[s + 1];
+                const float* __restrict__ sGA = sGb + off_g[s];
+                const float* __restrict__ sGB = sGb + off_g[s + 1];
                 // dL/dp0 is continuous in the distance (the cell values are), so the
                 // p0-only pass takes it in plain float; the full gradient, whose
                 // centre and radius terms jump at the window's ends, needs the
@@ -375,12 +404,12 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
                 // side by side when both windows are staged and differ by at most
                 // one ramp cell: the shorter one then reads one cell further, its
                 // own last cell G[jH] (inside the record), which adds d = 0
-                const bool inA = okA && staged && wa.jL - 1 >= jloA && min(wa.jH, Tk - 1) - jloA < lenA;
-                const bool inB = okB && staged && wb.jL - 1 >= jloB && min(wb.jH, Tk - 1) - jloB < lenB;
+                const bool inA = okA && wa.jL - 1 >= jloA && min(wa.jH, Tk - 1) - jloA < lenA;
+                const bool inB = okB && wb.jL - 1 >= jloB && min(wb.jH, Tk - 1) - jloB < lenB;
                 if (inA && inB && abs(LA - LB) <= 1 && (LA >= LB || wa.jH < Tk) &&
                     (LB >= LA || wb.jH < Tk)) {
-                    const float* GwA = sGb + s * kWin - jloA + wa.jL;
-                    const float* GwB = sGb + (s + 1) * kWin - jloB + wb.jL;
+                    const float* GwA = sGA - jloA + wa.jL;
+                    const float* GwB = sGB - jloB + wb.jL;
                     gf = make_float2(GwA[-1], GwB[-1]);
                     gl = make_float2(wa.jH < Tk ? GwA[wa.jH - wa.jL] : 0.0f,
                                      wb.jH < Tk ? GwB[wb.jH - wb.jL] : 0.0f);
@@ -403,11 +432,11 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
                     if (Lm > 0) E0 = f2add(run, f2add(make_float2(GwA[0], GwB[0]), ngl));
                 } else {
                     if (okA)
-                        adj_window_sums(sGb + s * kWin, jloA, lenA, staged,
+                        adj_window_sums(sGA, jloA, lenA,
                                         G + (size_t)(m0 + s) * Tk, wa.jL, wa.jH, Tk, gf.x, gl.x, E0.x,
                                         E1.x);
                     if (okB)
-                        adj_window_sums(sGb + (s + 1) * kWin, jloB, lenB, staged,
+                        adj_window_sums(sGB, jloB, lenB,
                                         G + (size_t)(m0 + s + 1) * Tk, wb.jL, wb.jH, Tk, gf.y, gl.y,
                                         E0.y, E1.y);
                 }
