@@ -232,27 +232,42 @@ fwd_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     const int glim = Tk - 1 - base;                // last cell inside the record
     unsigned int* col = sacc + lane;
     unsigned long long* grow = acc + (size_t)m * Tk + base;
-    // The warp takes its balls two at a time (i and i + kGroupWarps) and
-    // evaluates both pairs of its lane's sensor side by side; an odd last
-    // ball is paired with an empty one. Every ball goes through the same
-    // instructions, so its impulses do not depend on its partner.
-    for (int i = c0 + warp; i < c1; i += 2 * kGroupWarps) {
-        const int iB = i + kGroupWarps;
-        const bool hasB = iB < c1;
-        const float2 cx = make_float2(b.x[i], hasB ? b.x[iB] : 0.0f);
-        const float2 cy = make_float2(b.y[i], hasB ? b.y[iB] : 0.0f);
-        const float2 cz = make_float2(b.z[i], hasB ? b.z[iB] : 0.0f);
-        const float2 R2 = make_float2(b.R[i], hasB ? b.R[iB] : 0.0f);
-        const float2 P2 = make_float2(b.p0[i], hasB ? b.p0[iB] : 0.0f);
+    // The warp takes its balls two at a time (i and i + 1) and evaluates
+    // both pairs of its lane's sensor side by side; an odd last ball is
+    // paired with an empty one. Every ball goes through the same
+    // instructions, so its impulses do not depend on its partner. With the
+    // ball rows 8-byte aligned and c0 even (every chunk size and frame
+    // offset is), a pair of balls is read with one 8-byte load per row.
+    const bool pair_ld =
+        ((reinterpret_cast<uintptr_t>(b.x) | reinterpret_cast<uintptr_t>(b.y) |
+          reinterpret_cast<uintptr_t>(b.z) | reinterpret_cast<uintptr_t>(b.R) |
+          reinterpret_cast<uintptr_t>(b.p0) | (uintptr_t)(c0 & 1) * 4u) & 7u) == 0;
+    for (int i = c0 + 2 * warp; i < c1; i += 2 * kGroupWarps) {
+        const bool hasB = i + 1 < c1;
+        float2 cx, cy, cz, R2, P2;
+        if (pair_ld && hasB) {  // uniform over the warp
+            cx = __ldg(reinterpret_cast<const float2*>(b.x + i));
+            cy = __ldg(reinterpret_cast<const float2*>(b.y + i));
+            cz = __ldg(reinterpret_cast<const float2*>(b.z + i));
+            R2 = __ldg(reinterpret_cast<const float2*>(b.R + i));
+            P2 = __ldg(reinterpret_cast<const float2*>(b.p0 + i));
+        } else {
+            cx = make_float2(b.x[i], hasB ? b.x[i + 1] : 0.0f);
+            cy = make_float2(b.y[i], hasB ? b.y[i + 1] : 0.0f);
+            cz = make_float2(b.z[i], hasB ? b.z[i + 1] : 0.0f);
+            R2 = make_float2(b.R[i], hasB ? b.R[i + 1] : 0.0f);
+            P2 = make_float2(b.p0[i], hasB ? b.p0[i + 1] : 0.0f);
+        }
         if ((P2.x == 0.0f && P2.y == 0.0f) || !sv) continue;
         const PairDist2 pd = sbp_pair_distance2(cx, cy, cz, f2(sx), f2(sy), f2(sz));
         // inside test and window, per pair
         bool okA = P2.x != 0.0f, okB = P2.y != 0.0f;
-        if (okA && !(pd.dh.x + pd.dl.x > R2.x)) {
+        const float2 dd = f2add(pd.dh, pd.dl);
+        if (okA && !(dd.x > R2.x)) {
             ++inside;
             okA = false;
         }
-        if (okB && !(pd.dh.y + pd.dl.y > R2.y)) {
+        if (okB && !(dd.y > R2.y)) {
             ++inside;
             okB = false;
         }

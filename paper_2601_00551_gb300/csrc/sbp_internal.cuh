@@ -343,14 +343,23 @@ struct PairWindow {
 
 // The window of two pairs at once. For each: jr = floor(d / h), the offset
 // e = b_jr taken in float-float (sbp_boundary), then jL and jH from small
-// integer steps kL = floor((e - R) / h) + 1, kH = ceil((e + R) / h) - 1
-// carried as exact floats (below 2^24), the end offsets b0 = e - kL h and
-// bL = e - kH h, and one exact fix-up step of each end against R (as
-// selects). Valid when d > R, the far end lies inside the record and jH >= jL
-// >= 1; pairs whose window is not valid (ok = false) may carry any values.
+// integer steps kL and kH carried as exact floats (below 2^24), and the end
+// offsets b0 = e - kL h and bL = e - kH h, each rounded once (one FMA).
+// kL is the first step with b0 < R, kH the last with bL > -R, both decided
+// on those float offsets. The estimates kL = floor((e - R) / h - kBias) + 1
+// and kH = ceil((e + R) / h + kBias) - 1 are biased so that each is the
+// answer or one step short of it on one known side (kL below, kH above):
+// the bias of 2^-10 cells exceeds the rounding error of (e -+ R) / h, about
+// 3 |e -+ R| / h 2^-24 cells, for windows shorter than 2^11 cells. One
+// comparison per end then settles it. Where the float offset lands exactly
+// on +-R the cell it drops or keeps contributes zero, so either choice gives
+// the same cell values. Valid when d > R, the far end lies inside the record
+// and jH >= jL >= 1; pairs whose window is not valid (ok = false) may carry
+// any values.
 __device__ __forceinline__ void sbp_window2(float2 dh, float2 dl, float2 R, const LevelGeo& g,
                                             PairWindow& wa, PairWindow& wb, bool& okA,
                                             bool& okB) {
+    constexpr float kBias = 0.0009765625f;  // 2^-10 cells
     const float h = g.h_hi;
     const float2 xr = f2mul(dh, f2(g.inv_h));
     const float2 dd = f2add(dh, dl);
@@ -362,44 +371,16 @@ __device__ __forceinline__ void sbp_window2(float2 dh, float2 dl, float2 R, cons
     const float2 p = f2mul(jr, f2(g.h_hi));
     const float2 pe = f2fma(jr, f2(g.h_hi), f2neg(p));
     const float2 e = f2add(f2sub(dh, p), f2sub(f2sub(dl, pe), f2mul(jr, f2(g.h_lo))));
-    const float2 tL = f2mul(f2sub(e, R), f2(g.inv_h));
-    const float2 tH = f2mul(f2add(e, R), f2(g.inv_h));
+    const float2 tL = f2fma(f2sub(e, R), f2(g.inv_h), f2(-kBias));
+    const float2 tH = f2fma(f2add(e, R), f2(g.inv_h), f2(kBias));
     float2 kL = f2add(make_float2(floorf(tL.x), floorf(tL.y)), f2(1.0f));
     float2 kH = f2add(make_float2(ceilf(tH.x), ceilf(tH.y)), f2(-1.0f));
-    float2 b0 = f2fma(kL, f2(-h), e);
-    float2 bL = f2fma(kH, f2(-h), e);
-    // exact fix-ups: b0 must satisfy b0 < R <= b0 + h, bL must satisfy bL - h <= -R < bL
-    const float2 b0p = f2add(b0, f2(h)), b0m = f2add(b0, f2(-h));
-    const float2 bLp = f2add(bL, f2(h)), bLm = f2add(bL, f2(-h));
-    const float2 nR = f2neg(R);
-    if (b0.x >= R.x) {
-        kL.x += 1.0f;
-        b0.x = b0m.x;
-    } else if (b0p.x < R.x) {
-        kL.x -= 1.0f;
-        b0.x = b0p.x;
-    }
-    if (b0.y >= R.y) {
-        kL.y += 1.0f;
-        b0.y = b0m.y;
-    } else if (b0p.y < R.y) {
-        kL.y -= 1.0f;
-        b0.y = b0p.y;
-    }
-    if (bL.x <= nR.x) {
-        kH.x -= 1.0f;
-        bL.x = bLp.x;
-    } else if (bLm.x > nR.x) {
-        kH.x += 1.0f;
-        bL.x = bLm.x;
-    }
-    if (bL.y <= nR.y) {
-        kH.y -= 1.0f;
-        bL.y = bLp.y;
-    } else if (bLm.y > nR.y) {
-        kH.y += 1.0f;
-        bL.y = bLm.y;
-    }
+    const float2 b0t = f2fma(kL, f2(-h), e);
+    const float2 bLt = f2fma(kH, f2(-h), e);
+    kL = f2add(kL, make_float2(b0t.x >= R.x ? 1.0f : 0.0f, b0t.y >= R.y ? 1.0f : 0.0f));
+    kH = f2add(kH, make_float2(bLt.x <= -R.x ? -1.0f : 0.0f, bLt.y <= -R.y ? -1.0f : 0.0f));
+    const float2 b0 = f2fma(kL, f2(-h), e);
+    const float2 bL = f2fma(kH, f2(-h), e);
     const float2 jL = f2add(jr, kL), jH = f2add(jr, kH);
     okA = okA && jH.x >= jL.x && jL.x >= 1.0f && jL.x <= (float)g.Tk;
     okB = okB && jH.y >= jL.y && jL.y >= 1.0f && jL.y <= (float)g.Tk;
