@@ -61,20 +61,29 @@ constexpr int kAdjWindow = 224;   // mean cells per staged window the buffer is 
 constexpr int kAdjWindowP0 = 128; // the same for the p0-only adjoint, which keeps more CTAs per SM
 constexpr int kAdjMeta = 128;     // sensors whose set-up is held in shared memory at once
 
+__device__ __forceinline__ void downsample_one(const float* __restrict__ y, int T, int f,
+                                               float* __restrict__ yk, long long t, int m, int j) {
+    const float* row = y + (size_t)m * T;
+    float s = 0.0f;
+    for (int q = 0; q < f; ++q) {
+        const int i = j * f + q;
+        if (i < T) s += row[i];
+    }
+    yk[t] = s / (float)f;
+}
+
 __global__ void downsample_kernel(const float* __restrict__ y, int M, int T, int f, int Tk,
                                   float* __restrict__ yk) {
     const long long total = (long long)M * Tk;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int m = (int)(t / Tk), j = (int)(t % Tk);
-        const float* row = y + (size_t)m * T;
-        float s = 0.0f;
-        for (int q = 0; q < f; ++q) {
-            const int i = j * f + q;
-            if (i < T) s += row[i];
-        }
-        yk[t] = s / (float)f;
+    if (total < (1LL << 30)) {  // 32-bit index arithmetic (a 64-bit division is slow)
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < (int)total;
+             t += gridDim.x * blockDim.x)
+            downsample_one(y, T, f, yk, t, t / Tk, t % Tk);
+        return;
     }
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x)
+        downsample_one(y, T, f, yk, t, (int)(t / Tk), (int)(t % Tk));
 }
 
 // Sum of squares in float-float: hi + lo carries sum r^2 with the rounding
@@ -131,7 +140,8 @@ __device__ __forceinline__ double block_sum(double v, double* warp_sum) {
 }
 
 // G = 2 (S - y); per-block sums of (S - y)^2 in double; the last block to
-// finish adds the block sums in index order.
+// finish adds the block sums in a fixed order (thread t takes blocks t,
+// t + blockDim.x, ... in turn, then the fixed tree of block_sum).
 __global__ void residual_kernel(const float* __restrict__ S, const float* __restrict__ y,
                                 float* __restrict__ G, long long total, bool vec,
                                 double* __restrict__ partials, SbpDevState* st,
@@ -150,12 +160,16 @@ __global__ void residual_kernel(const float* __restrict__ S, const float* __rest
         is_last = (tk == gridDim.x - 1);
     }
     __syncthreads();
-    if (is_last && threadIdx.x == 0) {
+    if (is_last) {  // uniform over the block
         __threadfence();
-        double L = 0.0;
-        for (int bk = 0; bk < (int)gridDim.x; ++bk) L += ((volatile double*)partials)[bk];
-        *loss = L;
-        st->loss_ticket = 0;
+        double v = 0.0;
+        for (int bk = threadIdx.x; bk < (int)gridDim.x; bk += blockDim.x)
+            v += __ldcg(partials + bk);
+        const double L = block_sum(v, warp_sum);
+        if (threadIdx.x == 0) {
+            *loss = L;
+            st->loss_ticket = 0;
+        }
     }
 }
 
@@ -507,8 +521,8 @@ int sbp_launch_downsample(sbp_array_s* a, int k, const float* y_full, float* y_k
                           cudaStream_t st) {
     const int Tk = sbp_level_T(a, k);
     const long long total = (long long)a->M * Tk;
-    const int blocks = (int)std::max<long long>(
-        1, std::min<long long>(8LL * a->sm_count, (total + 255) / 256));
+    // about one output per thread, so that many loads are in flight
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(32768, (total + 255) / 256));
     downsample_kernel<<<blocks, 256, 0, st>>>(y_full, a->M, a->T, a->factors[k], Tk, y_k);
     sbp_count_launches(1);
     return sbp_cuda_check(cudaGetLastError(), "downsample launch") ? SBP_ERR_CUDA : SBP_OK;
@@ -519,8 +533,7 @@ int sbp_launch_downsample_rows(sbp_array_s* a, int k, int rows, const float* y_f
                                float* y_k, cudaStream_t st) {
     const int Tk = sbp_level_T(a, k);
     const long long total = (long long)rows * Tk;
-    const int blocks = (int)std::max<long long>(
-        1, std::min<long long>(8LL * a->sm_count, (total + 255) / 256));
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(32768, (total + 255) / 256));
     downsample_kernel<<<blocks, 256, 0, st>>>(y_full, rows, a->T, a->factors[k], Tk, y_k);
     sbp_count_launches(1);
     return sbp_cuda_check(cudaGetLastError(), "downsample launch") ? SBP_ERR_CUDA : SBP_OK;
