@@ -416,7 +416,7 @@ def run_native(args, rank, world, local):
             "parallelism": f"replicas x{world}",
             "launch": launch_mode,
             "tiles": ({f"{wl.fs_mhz / wl.levels[k]:g}MHz": {"forward_balls_per_cta": c or "default",
-                                                           "adjoint_ctas_per_cluster": sp or "default"}
+                                                           "adjoint_ctas_per_chunk": sp or "default"}
                        for k, (c, sp) in tiles.items()} if tiles else "default"),
         },
         "gpu_launches": int(launches),
@@ -963,7 +963,7 @@ def batched_frames(args, sb, dev, steps=8, warmup=3):
         "balls_init_range": [int(counts0.min()), int(counts0.max())],
         "pairs_per_step": pairs, "steps": steps, "warmup": warmup,
         "counts_identical_across_arms": bool(same),
-        "autotuned": {"forward_balls_per_cta": chunk, "adjoint_ctas_per_cluster": split},
+        "autotuned": {"forward_balls_per_cta": chunk, "adjoint_ctas_per_chunk": split},
         "kernel_launches_per_step": launches,
         **out,
         "speedup_batched_graph_vs_per_frame": (out["per_frame"]["ms_per_step"] /
@@ -1107,7 +1107,7 @@ def large_config(sb, dev, reps=3, tune=True):
         if tune:
             c, sp = arr.autotune(B, G=G)
             res["tiles"] = {"forward_balls_per_cta": c or "default",
-                            "adjoint_ctas_per_cluster": sp or "default"}
+                            "adjoint_ctas_per_chunk": sp or "default"}
             timed()
         h = wl.c * f / wl.fs_mhz
         res["forward_pairs_per_s"] = pairs / (res["forward_ms"] * 1e-3)

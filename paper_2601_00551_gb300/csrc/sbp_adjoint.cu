@@ -23,25 +23,24 @@
 // Kernels:
 //   downsample   y_k = block mean over f_k samples (zero padded)
 //   residual     G = 2 (S - y), L = sum (S - y)^2 (fixed-order last-block reduction)
-//   adj_group    A cluster of kAdjSplit CTAs shares one chunk of consecutive
-//                balls (one thread per ball) and splits the sensors between
-//                its CTAs. Each CTA walks its sensors in groups. For each
-//                group it stages, per sensor, the window of G that the
-//                chunk's bounding box can reach, packed one after another
-//                into one of two shared buffers with asynchronous copies,
-//                the next group's copies in flight while the current group
-//                is evaluated; a group takes as many sensor pairs as fill
-//                the buffer. Every thread takes the group's
-//                sensors two at a time, evaluating both pairs side by side
-//                in packed float2 arithmetic. A ball's five gradient
-//                components stay in its thread's registers across the CTA's
-//                sensors. The first CTA of the cluster then adds the other
-//                CTAs' partial sums through distributed shared memory, in
-//                rank order, and writes every ball's gradients exactly once.
-//                No atomics. A window longer than half a buffer (e.g. an
-//                unsorted cloud) is not staged: its pairs read the global
-//                row instead.
-#include <cooperative_groups.h>
+//   adj_group    kAdjSplit CTAs (grid.y) share one chunk of consecutive
+//                balls (one thread per ball) and split the sensors between
+//                them. Each CTA walks its sensors in groups. For each group
+//                it stages, per sensor, the window of G that the chunk's
+//                bounding box can reach, packed one after another into one
+//                of two shared buffers with asynchronous copies, the next
+//                group's copies in flight while the current group is
+//                evaluated; a group takes as many sensor pairs as fill the
+//                buffer. Every thread takes the group's sensors two at a
+//                time, evaluating both pairs side by side in packed float2
+//                arithmetic. A ball's five gradient components stay in its
+//                thread's registers across the CTA's sensors. Each CTA then
+//                writes its partial sums to global scratch; the last of the
+//                chunk's CTAs to finish adds them in rank order and writes
+//                every ball's gradients exactly once (no atomics on the
+//                gradients, so the result is reproducible). A window longer
+//                than half a buffer (e.g. an unsorted cloud) is not staged:
+//                its pairs read the global row instead.
 
 #include <algorithm>
 #include <cstdint>
@@ -50,12 +49,11 @@
 
 #include "sbp_internal.cuh"
 
-namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int kAdjThreads = 128;  // balls (threads) per adjoint CTA
-constexpr int kAdjSplit = 4;      // default CTAs per cluster, each taking 1/split of the sensors
+constexpr int kAdjThreads = SBP_ADJ_CHUNK;  // balls (threads) per adjoint CTA
+constexpr int kAdjSplit = 4;      // default CTAs per chunk, each taking 1/split of the sensors
 constexpr int kAdjGroup = 16;     // staging buffer size: kAdjGroup windows of the mean length below
 constexpr int kAdjWindow = 224;   // mean cells per staged window the buffer is sized for
 constexpr int kAdjWindowP0 = 128; // the same for the p0-only adjoint, which keeps more CTAs per SM
@@ -223,11 +221,12 @@ __device__ __forceinline__ void adj_window_sums(const float* __restrict__ sGrow,
 
 // P0_ONLY: only dL/dp0 is wanted (the zero-gradient pass), so the chain rule
 // for R and the centre is skipped.
-// Launched with a cluster of gridDim.y CTAs along y (cudaLaunchKernelEx).
+// gridDim.y CTAs share a chunk, each taking 1/gridDim.y of the sensors.
 template <bool P0_ONLY>
 __global__ void __launch_bounds__(kAdjThreads, P0_ONLY ? 8 : 6)
 adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, LevelGeo g,
-                 const float* __restrict__ G_all, unsigned mask, GradOut out) {
+                 const float* __restrict__ G_all, unsigned mask, GradOut out,
+                 float* __restrict__ part_all, unsigned int* __restrict__ tickets) {
     // two staging buffers of kCap cells, each holding the windows of one
     // group of sensors packed one after another; after the last group the
     // first one holds this CTA's partial sums
@@ -244,10 +243,9 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     float* const s_part = sG[0];  // this CTA's partial sums, [ball][5]
     static_assert(kAdjThreads * 5 <= kCap, "partials do not fit");
     static_assert(2 * kWin <= kCap, "a pair of staged windows must fit one buffer");
-    cg::cluster_group cluster = cg::this_cluster();
     const int c0 = blockIdx.x * kAdjThreads;
     const FrameSlot fs = sbp_frame_of(ft, c0);
-    if (c0 >= fs.end) return;  // uniform over the whole cluster (same chunk)
+    if (c0 >= fs.end) return;  // uniform over the chunk's CTAs
     const int c1 = min(fs.end, c0 + kAdjThreads);
     const int nb = c1 - c0;
     const int Tk = g.Tk, M = g.M;
@@ -294,8 +292,8 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     const float hh2 = 2.0f * h * h;
     float2 gx2 = f2(0.f), gy2 = f2(0.f), gz2 = f2(0.f), gR2 = f2(0.f), gp2 = f2(0.f);
     // this CTA's share of the sensors, whole groups
-    const int part = (int)cluster.block_rank();
-    const int split = (int)gridDim.y;  // one cluster spans all of y
+    const int part = (int)blockIdx.y;
+    const int split = (int)gridDim.y;
     const int per = ((M + split - 1) / split + kAdjGroup - 1) / kAdjGroup * kAdjGroup;
     const int m_begin = min(M, part * per), m_end = min(M, m_begin + per);
     // The share is walked in blocks of up to kAdjMeta sensors whose positions,
@@ -486,33 +484,45 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     }
     const float gx = gx2.x + gx2.y, gy = gy2.x + gy2.y, gz = gz2.x + gz2.y;
     const float gR = gR2.x + gR2.y, gp = gp2.x + gp2.y;
-    __syncthreads();  // every group is done with the staging buffers
+    // This CTA's partial sums go to global scratch [chunk][part][5][ball]. The
+    // last of the chunk's CTAs to arrive (a ticket per chunk) adds the parts
+    // in rank order and writes every ball's gradients exactly once, so the
+    // result does not depend on which CTA finishes last, and no CTA waits
+    // for another.
+    const size_t chunk = blockIdx.x;
+    float* __restrict__ mine = part_all + (chunk * split + part) * 5 * kAdjThreads;
     if (valid) {  // stored under the ball's chunk-local index
-        s_part[li * 5 + 0] = gx;
-        s_part[li * 5 + 1] = gy;
-        s_part[li * 5 + 2] = gz;
-        s_part[li * 5 + 3] = gR;
-        s_part[li * 5 + 4] = gp;
+        if (!P0_ONLY) {
+            mine[0 * kAdjThreads + li] = gx;
+            mine[1 * kAdjThreads + li] = gy;
+            mine[2 * kAdjThreads + li] = gz;
+            mine[3 * kAdjThreads + li] = gR;
+        }
+        mine[4 * kAdjThreads + li] = gp;
     }
-    cluster.sync();
-    if (part == 0 && valid) {
-        float ax = gx, ay = gy, az = gz, aR = gR, ap = gp;
-        for (int r = 1; r < split; ++r) {
-            const float* rp = cluster.map_shared_rank(s_part, r) + li * 5;
-            ax += rp[0];
-            ay += rp[1];
-            az += rp[2];
-            aR += rp[3];
-            ap += rp[4];
+    __threadfence();
+    __shared__ bool s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&tickets[chunk], 1u) == (unsigned int)(split - 1);
+    __syncthreads();
+    if (!s_last) return;  // uniform over the block
+    __threadfence();
+    if (valid) {
+        const float* __restrict__ all = part_all + chunk * split * 5 * kAdjThreads + li;
+        float a[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int r = 0; r < split; ++r) {
+            const float* pr = all + (size_t)r * 5 * kAdjThreads;
+#pragma unroll
+            for (int c = P0_ONLY ? 4 : 0; c < 5; ++c) a[c] += __ldcg(pr + c * kAdjThreads);
         }
         const bool xyz = mask & SBP_MASK_XYZ;
-        out.o[0][i] = xyz ? ax : 0.0f;
-        out.o[1][i] = xyz ? ay : 0.0f;
-        out.o[2][i] = xyz ? az : 0.0f;
-        out.o[3][i] = (mask & SBP_MASK_R) ? aR : 0.0f;
-        out.o[4][i] = (mask & SBP_MASK_P0) ? ap : 0.0f;
+        out.o[0][i] = xyz ? a[0] : 0.0f;
+        out.o[1][i] = xyz ? a[1] : 0.0f;
+        out.o[2][i] = xyz ? a[2] : 0.0f;
+        out.o[3][i] = (mask & SBP_MASK_R) ? a[3] : 0.0f;
+        out.o[4][i] = (mask & SBP_MASK_P0) ? a[4] : 0.0f;
     }
-    cluster.sync();  // the other CTAs' shared memory must outlive the reads above
+    if (threadIdx.x == 0) tickets[chunk] = 0u;  // ready for the next launch
 }
 
 }  // namespace
@@ -563,27 +573,24 @@ int sbp_launch_residual(sbp_array_s* a, const float* S, const float* y, float* G
 
 namespace {
 
-int launch_adj(const FrameTable& ft, int total, int split, const BallsDev& b, const float* sens,
+int launch_adj(sbp_array_s* a, const FrameTable& ft, int total, int split, const BallsDev& b,
                const LevelGeo& g, const float* G, unsigned mask, const GradOut& o,
                cudaStream_t st) {
     if (split != 1 && split != 2 && split != 4 && split != 8) split = kAdjSplit;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((total + kAdjThreads - 1) / kAdjThreads, split);
-    cfg.blockDim = dim3(kAdjThreads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 1;
-    attr[0].val.clusterDim.y = split;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    const cudaError_t e =
-        mask == SBP_MASK_P0
-            ? cudaLaunchKernelEx(&cfg, adj_group_kernel<true>, b, ft, sens, g, G, mask, o)
-            : cudaLaunchKernelEx(&cfg, adj_group_kernel<false>, b, ft, sens, g, G, mask, o);
-    if (sbp_cuda_check(e, "adjoint: launch")) return SBP_ERR_CUDA;
+    static_assert(kAdjSplit <= SBP_ADJ_MAX_SPLIT, "the scratch holds at most 8 parts");
+    const int chunks = (total + kAdjThreads - 1) / kAdjThreads;
+    if (chunks > a->adj_chunks) {
+        sbp_set_error("adjoint: more balls than the array's capacity");
+        return SBP_ERR_ARG;
+    }
+    const dim3 grid(chunks, split);
+    if (mask == SBP_MASK_P0)
+        adj_group_kernel<true><<<grid, kAdjThreads, 0, st>>>(b, ft, a->d_sens, g, G, mask, o,
+                                                             a->d_adj_part, a->d_adj_ticket);
+    else
+        adj_group_kernel<false><<<grid, kAdjThreads, 0, st>>>(b, ft, a->d_sens, g, G, mask, o,
+                                                              a->d_adj_part, a->d_adj_ticket);
+    if (sbp_cuda_check(cudaGetLastError(), "adjoint: launch")) return SBP_ERR_CUDA;
     sbp_count_launches(1);
     return SBP_OK;
 }
@@ -601,7 +608,7 @@ int sbp_launch_adjoint(sbp_array_s* a, const BallsDev& b, const int* n_dev, int 
     o.o[4] = out.gp0;
     const FrameTable ft{1, nullptr, n_dev, n_cap};
     const int split = a->adj_split_lvl[a->level] ? a->adj_split_lvl[a->level] : kAdjSplit;
-    return launch_adj(ft, n_cap, split, b, a->d_sens, g, G, mask, o, st);
+    return launch_adj(a, ft, n_cap, split, b, g, G, mask, o, st);
 }
 
 // All frames of the packed layout in one launch (sbp_adjoint_frames).
@@ -616,8 +623,8 @@ int sbp_launch_adjoint_frames(sbp_array_s* a, const BallsDev& b, const int* n_de
     o.o[4] = out.gp0;
     const int total = a->h_frame_off[a->frames];
     const FrameTable ft{a->frames, a->d_frame_off, n_dev, total};
-    return launch_adj(ft, total, a->adj_split_frames ? a->adj_split_frames : kAdjSplit, b,
-                      a->d_sens, g, G, mask, o, st);
+    return launch_adj(a, ft, total, a->adj_split_frames ? a->adj_split_frames : kAdjSplit, b, g,
+                      G, mask, o, st);
 }
 
 namespace {

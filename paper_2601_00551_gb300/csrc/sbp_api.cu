@@ -52,6 +52,8 @@ void free_array(sbp_array_s* a) {
     cudaFree(a->d_fg_counts);
     cudaFree(a->d_fg_buf);
     cudaFree(a->d_state);
+    cudaFree(a->d_adj_part);
+    cudaFree(a->d_adj_ticket);
     cudaFree(a->d_rc_yk);
     cudaFree(a->d_rc_S);
     cudaFree(a->d_rc_G);
@@ -187,6 +189,14 @@ int sbp_create_array(const float* pos_host, const float* normal_host, int M, dou
                                                             (size_t)n_cap),
                                "alloc filter buffer");
     ok = ok && !sbp_cuda_check(cudaMalloc(&a->d_state, sizeof(SbpDevState)), "alloc state");
+    a->adj_chunks = (n_cap + SBP_ADJ_CHUNK - 1) / SBP_ADJ_CHUNK;
+    ok = ok && !sbp_cuda_check(cudaMalloc(&a->d_adj_part, sizeof(float) * (size_t)a->adj_chunks *
+                                                              SBP_ADJ_MAX_SPLIT * 5 * SBP_ADJ_CHUNK),
+                               "alloc adjoint partials");
+    ok = ok && !sbp_cuda_check(cudaMalloc(&a->d_adj_ticket, sizeof(unsigned int) * a->adj_chunks),
+                               "alloc adjoint tickets");
+    ok = ok && !sbp_cuda_check(cudaMemset(a->d_adj_ticket, 0, sizeof(unsigned int) * a->adj_chunks),
+                               "clear adjoint tickets");
     ok = ok && !sbp_cuda_check(cudaMemcpy(a->d_sens, sens.data(), sizeof(float) * 6 * M,
                                           cudaMemcpyHostToDevice),
                                "copy sensors");

@@ -9,6 +9,8 @@
 #include "slingbag.h"
 
 #define SBP_MAX_LEVELS 16
+#define SBP_ADJ_CHUNK 128  // balls per adjoint CTA
+#define SBP_ADJ_MAX_SPLIT 8  // most CTAs sharing one adjoint chunk
 #define SBP_MAX_EXTRA 16
 #define SBP_FG_ARRAYS (10 + SBP_MAX_EXTRA)
 
@@ -133,6 +135,11 @@ struct sbp_array_s {
     // single-cloud tiles per level chosen by sbp_autotune (0: default)
     int fwd_chunk_lvl[SBP_MAX_LEVELS];
     int adj_split_lvl[SBP_MAX_LEVELS];
+    // adjoint: partial sums of the CTAs that split a chunk's sensors
+    // [chunk][part][5][128] and one arrival ticket per chunk (left zero)
+    float* d_adj_part;
+    unsigned int* d_adj_ticket;
+    int adj_chunks;  // chunks the two hold
 };
 
 // ----------------------------------------------------------------------------

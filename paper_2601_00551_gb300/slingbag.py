@@ -339,7 +339,7 @@ class SensorArray:
 
     def autotune(self, balls: torch.Tensor, n=None, G: torch.Tensor | None = None):
         """Tile autotuner at the current level (sbp_autotune); returns and keeps
-        (forward balls per CTA, adjoint CTAs per cluster). G defaults to
+        (forward balls per CTA, adjoint CTAs per ball chunk). G defaults to
         standard normal traces."""
         Tk = self.Tk
         S = torch.empty((self.M, Tk), dtype=torch.float32, device=self.device)
@@ -610,7 +610,7 @@ class SensorArray:
 
     def autotune_frames(self, balls, n_dev):
         """Tile autotuner of the batched path (sbp_autotune_frames); returns
-        (forward balls per CTA, adjoint CTAs per cluster)."""
+        (forward balls per CTA, adjoint CTAs per ball chunk)."""
         Tk = self.Tk
         S = torch.empty((self.frames, self.M, Tk), dtype=torch.float32, device=self.device)
         G = torch.randn((self.frames, self.M, Tk), dtype=torch.float32, device=self.device)
