@@ -509,10 +509,10 @@ def adj_ops_per_pair(mean_R, h):
 NCU_TRAFFIC = {
     "forward": {"sources": ["paper_2601_00551_gb300/csrc/sbp_forward.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "d8648d4dab2f1158", "bytes": 5.262848e6},
+                "sha256": "b406e1fb2be19f8e", "bytes": 5.264128e6},
     "adjoint": {"sources": ["paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "42b9d0b5d91595be", "bytes": 3.753472e6},
+                "sha256": "d50b92747cdb0cee", "bytes": 3.756288e6},
 }
 
 
