@@ -26,6 +26,7 @@
 // Every mbarrier wait is bounded; a wait that gives up sets a status word
 // (sbp_cnn_status) and the CTA skips to its clean-up.
 #include <cuda_bf16.h>
+#include <cuda_pipeline.h>
 
 #include <cstdint>
 
@@ -291,6 +292,152 @@ __global__ void __launch_bounds__(kTcThreads) conv3d_tc_kernel(ConvArgs a) {
                      : "memory");
 }
 
+// Halo variant (Cin a multiple of 16). A CTA computes a tile of 8 x 16 x 1
+// voxels (m = ty * 8 + tx, so the 16 groups of 8 MMA rows are the tile's 16
+// rows along y). The tile's input halo (10 x 18 x 3 voxels, zeros outside the
+// volume) is copied once into shared memory, chunk-major: [cc][hz][hy][hx]
+// with 16 bytes (8 channels) per voxel. For tap (dx, dy, dz) the im2col rows
+// of the 8 voxels of a tile row are then 8 consecutive 16-byte entries of
+// one halo row, which is a canonical K-major core matrix: the A operand of
+// the tap is a descriptor pointing into the halo (leading byte offset = one
+// chunk plane, stride byte offset = one halo row), and no im2col copy is
+// made. The weights of all 27 taps are staged once ([tap][cc][n] x 16
+// bytes). One thread then issues the 27 * Cin / 16 MMAs (M = 128, N = Cout,
+// K = 16) back to back and commits them to one mbarrier.
+constexpr int kHTX = 8, kHTY = 16;                 // tile
+constexpr int kHX = kHTX + 2, kHY = kHTY + 2, kHZ = 3;  // halo
+constexpr int kHV = kHX * kHY * kHZ;
+
+template <int CIN, int COUT>
+constexpr int halo_smem_bytes() {
+    return CIN / 8 * kHV * 16 + 27 * (CIN / 8) * COUT * 16;
+}
+
+template <int CIN, int COUT, bool RELU, bool OUT_F32>
+__global__ void __launch_bounds__(kTcThreads) conv3d_halo_kernel(ConvArgs a) {
+    static_assert(CIN % 16 == 0, "one MMA (K = 16) takes two channel chunks of one tap");
+    static_assert(COUT % 16 == 0 && COUT >= 16 && COUT <= kTcCols, "Cout must be 16, 32 or 64");
+    static_assert(kHTX * kHTY == kTcRows, "a tile is one MMA's M");
+    extern __shared__ __align__(1024) uint8_t s_dyn[];
+    constexpr int kChunks = CIN / 8;
+    constexpr int kPlane = kHV * 16;    // bytes of one 8-channel chunk of the halo
+    constexpr int kWBlock = COUT * 16;  // bytes of the weights of one (tap, chunk)
+    uint8_t* const s_halo = s_dyn;
+    uint8_t* const s_w = s_dyn + kChunks * kPlane;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_tmem;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int x0 = blockIdx.x * kHTX, y0 = blockIdx.y * kHTY, z0 = blockIdx.z;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // the halo: a voxel's chunks are adjacent in global memory (coalesced)
+    for (int t = tid; t < kHV * kChunks; t += kTcThreads) {
+        const int v = t / kChunks, cc = t - v * kChunks;
+        const int hx = v % kHX, hy = (v / kHX) % kHY, hz = v / (kHX * kHY);
+        const int xx = x0 + hx - 1, yy = y0 + hy - 1, zz = z0 + hz - 1;
+        uint8_t* dst = s_halo + cc * kPlane + v * 16;
+        if (xx >= 0 && xx < a.nx && yy >= 0 && yy < a.ny && zz >= 0 && zz < a.nz)
+            __pipeline_memcpy_async(
+                dst, a.in + (((long long)zz * a.ny + yy) * a.nx + xx) * CIN + cc * 8, 16);
+        else
+            *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    // the weights: w[n][tap * CIN + cc * 8 ...] -> [tap][cc][n] (a row's chunks coalesced)
+    for (int t = tid; t < COUT * 27 * kChunks; t += kTcThreads) {
+        const int n = t / (27 * kChunks), r = t - n * (27 * kChunks);  // r = tap * kChunks + cc
+        __pipeline_memcpy_async(s_w + r * kWBlock + n * 16, a.w + (size_t)n * a.Kp + r * 8, 16);
+    }
+    __pipeline_commit();
+    __pipeline_wait_prior(0);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    if (tid == 0) {
+        constexpr uint32_t idesc = umma_idesc_bf16(kTcRows, COUT);
+        const uint32_t hb = smem_u32(s_halo), wb = smem_u32(s_w);
+#pragma unroll 1
+        for (int tap = 0; tap < 27; ++tap) {
+            // (dx, dy, dz) + 1 = (tap % 3, tap / 3 % 3, tap / 9): the tile's voxel (0, 0)
+            // reads halo voxel (dx + 1, dy + 1, dz + 1)
+            const uint32_t aoff = (uint32_t)(((tap / 9) * kHY + (tap / 3) % 3) * kHX + tap % 3) * 16;
+#pragma unroll
+            for (int kp = 0; kp < kChunks / 2; ++kp)
+                tc_mma(tmem, umma_desc(hb + aoff + 2 * kp * kPlane, kPlane, kHX * 16),
+                       umma_desc(wb + (tap * kChunks + 2 * kp) * kWBlock, kWBlock, 128), idesc,
+                       (tap > 0 || kp > 0) ? 1u : 0u);
+        }
+        tc_commit(&bar);
+    }
+    const bool ok = mbar_wait(&bar, 0u);
+    tc_fence_after();
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicExch(&g_cnn_status, 1);
+    } else {
+        // epilogue: lane = tile row m = ty * 8 + tx, columns = output channels
+        const int m = warp * 32 + (tid & 31);
+        const int x = x0 + (m & 7), y = y0 + (m >> 3);
+        const bool mv = x < a.nx && y < a.ny;
+        const long long q = ((long long)z0 * a.ny + y) * a.nx + x;
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
+            float v[16];
+            tc_ld16(taddr + c0, v);
+            if (mv) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float r = v[j] + (a.bias ? a.bias[c0 + j] : 0.0f);
+                    if (RELU) r = fmaxf(r, 0.0f);
+                    v[j] = r;
+                }
+                if constexpr (OUT_F32) {
+                    float4* o = reinterpret_cast<float4*>(static_cast<float*>(a.out) + q * COUT + c0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                } else {
+                    __nv_bfloat162 h[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                    uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.out) + q * COUT + c0);
+                    o[0] = *reinterpret_cast<uint4*>(&h[0]);
+                    o[1] = *reinterpret_cast<uint4*>(&h[4]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTcCols)
+                     : "memory");
+}
+
+template <int CIN, int COUT, bool RELU, bool OUT_F32>
+int launch_halo_t(const ConvArgs& a, cudaStream_t st) {
+    constexpr int smem = halo_smem_bytes<CIN, COUT>();
+    auto k = conv3d_halo_kernel<CIN, COUT, RELU, OUT_F32>;
+    if (sbp_cuda_check(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                       "conv3d_bf16: smem attribute"))
+        return SBP_ERR_CUDA;
+    const dim3 grid((a.nx + kHTX - 1) / kHTX, (a.ny + kHTY - 1) / kHTY, a.nz);
+    k<<<grid, kTcThreads, smem, st>>>(a);
+    return SBP_OK;
+}
+
 template <int CIN, int COUT, bool RELU, bool OUT_F32>
 int launch_conv_t(const ConvArgs& a, unsigned blocks, cudaStream_t st) {
     constexpr int smem = 2 * (kTcRows + COUT) * kTcBK * 2;
@@ -304,6 +451,16 @@ int launch_conv_t(const ConvArgs& a, unsigned blocks, cudaStream_t st) {
 
 template <int CIN, int COUT>
 int launch_conv(const ConvArgs& a, bool relu, bool out_f32, long long V, cudaStream_t st) {
+    // the halo kernel where its staged halo and weights fit one CTA's shared
+    // memory and the grid's y and z extents allow it
+    if constexpr (CIN % 16 == 0 && halo_smem_bytes<CIN, COUT>() <= 200 * 1024) {
+        if ((a.ny + kHTY - 1) / kHTY <= 65535 && a.nz <= 65535) {
+            if (relu && out_f32) return launch_halo_t<CIN, COUT, true, true>(a, st);
+            if (relu) return launch_halo_t<CIN, COUT, true, false>(a, st);
+            if (out_f32) return launch_halo_t<CIN, COUT, false, true>(a, st);
+            return launch_halo_t<CIN, COUT, false, false>(a, st);
+        }
+    }
     const unsigned blocks = (unsigned)((V + kTcRows - 1) / kTcRows);
     if (relu && out_f32) return launch_conv_t<CIN, COUT, true, true>(a, blocks, st);
     if (relu) return launch_conv_t<CIN, COUT, true, false>(a, blocks, st);

@@ -26,7 +26,7 @@ def dyadic(rng, shape, scale=16):
     return (rng.integers(-24, 25, size=shape) / scale).astype(np.float32)
 
 
-@pytest.mark.parametrize("cin,cout", [(1, 16), (16, 32), (32, 64), (64, 64), (16, 16)])
+@pytest.mark.parametrize("cin,cout", [(1, 16), (16, 32), (32, 32), (32, 16), (32, 64), (64, 32), (64, 64), (16, 16)])
 def test_conv_exact_on_dyadic_values(sb, cin, cout):
     rng = np.random.default_rng(cin * 100 + cout)
     dims = (13, 9, 11)  # nx, ny, nz: 1287 voxels, a ragged last tile of 128
@@ -45,6 +45,21 @@ def test_conv_exact_on_dyadic_values(sb, cin, cout):
     got = sb.conv3d(X, dims, W, B, relu=True)
     refr = cnn.bf16_round(np.maximum(ref, 0.0).astype(np.float32))
     np.testing.assert_array_equal(got.float().cpu().numpy().reshape(nz, ny, nx, cout), refr)
+
+
+def test_conv_tiles_span_the_volume(sb):
+    """A volume of several halo tiles in every direction plus ragged ends
+    (x = 8 k + 3, y = 16 k + 5): every voxel against the oracle, exactly."""
+    rng = np.random.default_rng(11)
+    dims = (19, 37, 6)
+    nx, ny, nz = dims
+    x = dyadic(rng, (nz, ny, nx, 32))
+    w = dyadic(rng, (32, 27, 32))
+    ref = cnn.conv3d(x, w)
+    got = sb.conv3d(torch.from_numpy(x.reshape(-1, 32)).cuda().to(torch.bfloat16), dims,
+                    sb.pack_conv_weights(torch.from_numpy(w).cuda()), out_f32=True)
+    assert sb.cnn_status() == 0
+    np.testing.assert_array_equal(got.cpu().numpy().reshape(nz, ny, nx, 32), ref)
 
 
 def test_conv_random_values_within_fp32_accumulation(sb):
