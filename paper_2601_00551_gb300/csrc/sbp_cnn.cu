@@ -25,10 +25,14 @@
 //     (bf16 or fp32, channels-last).
 // Every mbarrier wait is bounded; a wait that gives up sets a status word
 // (sbp_cnn_status) and the CTA skips to its clean-up.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 #include <cuda_pipeline.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "sbp_internal.cuh"
 
@@ -438,6 +442,238 @@ int launch_halo_t(const ConvArgs& a, cudaStream_t st) {
     return SBP_OK;
 }
 
+// Persistent TMA variant (Cin 16 or 32). One CTA per SM stages the weights
+// once and walks its tiles (tile i of the CTA is global tile blockIdx.x + i
+// gridDim.x). Each tile's halo comes in by TMA: a 4-D tensor map over the
+// channels-last input (channel, x, y, z) and one box of 8 channels x 10 x 18
+// x 3 per 8-channel chunk, which lands as exactly the chunk plane the MMA
+// descriptors read (rows of 16 bytes along x); outside the volume TMA fills
+// zeros. The halos rotate through three slots, so a tile's copy is issued
+// two tiles ahead, and the accumulator alternates between two TMEM buffers,
+// so the epilogue of tile i - 1 runs while the MMAs of tile i are in flight.
+constexpr int kTmaSlots = 3;
+constexpr int kPlanePad = (kHV * 16 + 127) / 128 * 128;  // a TMA destination is 128-byte aligned
+
+template <int CIN, int COUT>
+constexpr int tma_smem_bytes() {  // + 128: the base is rounded up to 128 bytes in the kernel
+    return 27 * (CIN / 8) * COUT * 16 + kTmaSlots * (CIN / 8) * kPlanePad + 128;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <int CIN, int COUT, bool RELU, bool OUT_F32>
+__global__ void __launch_bounds__(kTcThreads, 1)
+conv3d_tma_kernel(const __grid_constant__ CUtensorMap tmap, ConvArgs a, int ntx, int nty,
+                  int ntiles) {
+    static_assert(CIN % 16 == 0 && CIN <= 32, "two or four channel chunks");
+    static_assert(COUT % 16 == 0 && COUT >= 16 && COUT <= kTcCols, "Cout must be 16, 32 or 64");
+    extern __shared__ __align__(1024) uint8_t s_dyn[];
+    constexpr int kChunks = CIN / 8;
+    constexpr int kWBlock = COUT * 16;
+    constexpr int kWBytes = 27 * kChunks * kWBlock;
+    constexpr int kSlotBytes = kChunks * kPlanePad;
+    constexpr uint32_t kTxBytes = kChunks * kHV * 16;  // one tile's halo
+    static_assert(kWBytes % 128 == 0, "halo slots must stay 128-byte aligned");
+    uint8_t* const s_w = s_dyn + ((128u - (smem_u32(s_dyn) & 127u)) & 127u);
+    uint8_t* const s_halo = s_w + kWBytes;
+    __shared__ __align__(8) uint64_t full[kTmaSlots];
+    __shared__ __align__(8) uint64_t done[2];
+    __shared__ uint32_t s_tmem;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        for (int s = 0; s < kTmaSlots; ++s) mbar_init(&full[s], 1);
+        mbar_init(&done[0], 1);
+        mbar_init(&done[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(2 * kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // the weights, once: w[n][tap * CIN + cc * 8 ...] -> [tap][cc][n] x 16 bytes
+    for (int t = tid; t < COUT * 27 * kChunks; t += kTcThreads) {
+        const int n = t / (27 * kChunks), r = t - n * (27 * kChunks);
+        __pipeline_memcpy_async(s_w + r * kWBlock + n * 16, a.w + (size_t)n * a.Kp + r * 8, 16);
+    }
+    __pipeline_commit();
+    __pipeline_wait_prior(0);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const int nmine = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    auto origin = [&](int i, int& x0, int& y0, int& z0) {
+        const int t = (int)blockIdx.x + i * (int)gridDim.x;
+        x0 = (t % ntx) * kHTX;
+        y0 = ((t / ntx) % nty) * kHTY;
+        z0 = t / (ntx * nty);
+    };
+    // thread 0: the copies of this CTA's tile i into slot i % kTmaSlots
+    auto load = [&](int i) {
+        if (i >= nmine) return;
+        int x0, y0, z0;
+        origin(i, x0, y0, z0);
+        const int s = i % kTmaSlots;
+        mbar_expect_tx(&full[s], kTxBytes);
+#pragma unroll
+        for (int cc = 0; cc < kChunks; ++cc)
+            tma_load_4d(smem_u32(s_halo + s * kSlotBytes + cc * kPlanePad), &tmap, cc * 8, x0 - 1,
+                        y0 - 1, z0 - 1, &full[s]);
+    };
+    if (tid == 0) {
+        load(0);
+        load(1);
+    }
+    bool ok = true;
+    for (int i = 0; i <= nmine; ++i) {
+        if (i < nmine && tid == 0) {  // the MMAs of tile i into TMEM buffer i & 1
+            const int s = i % kTmaSlots;
+            if (!mbar_wait(&full[s], (uint32_t)((i / kTmaSlots) & 1))) {
+                ok = false;
+            } else {
+                tc_fence_after();
+                constexpr uint32_t idesc = umma_idesc_bf16(kTcRows, COUT);
+                const uint32_t hb = smem_u32(s_halo + s * kSlotBytes), wb = smem_u32(s_w);
+                const uint32_t d = tmem + (uint32_t)((i & 1) * kTcCols);
+#pragma unroll 1
+                for (int tap = 0; tap < 27; ++tap) {
+                    const uint32_t aoff =
+                        (uint32_t)(((tap / 9) * kHY + (tap / 3) % 3) * kHX + tap % 3) * 16;
+#pragma unroll
+                    for (int kp = 0; kp < kChunks / 2; ++kp)
+                        tc_mma(d, umma_desc(hb + aoff + 2 * kp * kPlanePad, kPlanePad, kHX * 16),
+                               umma_desc(wb + (tap * kChunks + 2 * kp) * kWBlock, kWBlock, 128),
+                               idesc, (tap > 0 || kp > 0) ? 1u : 0u);
+                }
+                tc_commit(&done[i & 1]);
+            }
+        }
+        if (i >= 1 && ok) {  // the epilogue of tile i - 1 from TMEM buffer (i - 1) & 1
+            const int j = i - 1;
+            if (!mbar_wait(&done[j & 1], (uint32_t)((j >> 1) & 1))) ok = false;
+            tc_fence_after();
+            if (ok) {
+                int x0, y0, z0;
+                origin(j, x0, y0, z0);
+                const int m = warp * 32 + (tid & 31);
+                const int x = x0 + (m & 7), y = y0 + (m >> 3);
+                const bool mv = x < a.nx && y < a.ny;
+                const long long q = ((long long)z0 * a.ny + y) * a.nx + x;
+                const uint32_t taddr =
+                    tmem + (uint32_t)((j & 1) * kTcCols) + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+                for (int c0 = 0; c0 < COUT; c0 += 16) {
+                    float v[16];
+                    tc_ld16(taddr + c0, v);
+                    if (mv) {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) {
+                            float r = v[k] + (a.bias ? a.bias[c0 + k] : 0.0f);
+                            if (RELU) r = fmaxf(r, 0.0f);
+                            v[k] = r;
+                        }
+                        if constexpr (OUT_F32) {
+                            float4* o =
+                                reinterpret_cast<float4*>(static_cast<float*>(a.out) + q * COUT + c0);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                o[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                        } else {
+                            __nv_bfloat162 hh[8];
+#pragma unroll
+                            for (int k = 0; k < 8; ++k)
+                                hh[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+                            uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.out) +
+                                                                q * COUT + c0);
+                            o[0] = *reinterpret_cast<uint4*>(&hh[0]);
+                            o[1] = *reinterpret_cast<uint4*>(&hh[4]);
+                        }
+                    }
+                }
+            }
+        }
+        tc_fence_before();
+        if (!__syncthreads_and(ok)) break;
+        tc_fence_after();
+        // slot (i + 2) % 3 last held tile i - 1, whose MMAs are done; TMEM
+        // buffer (i + 1) & 1 was read by the epilogue above
+        if (tid == 0) load(i + 2);
+    }
+    if (!ok && tid == 0) atomicExch(&g_cnn_status, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(2 * kTcCols)
+                     : "memory");
+}
+
+// cuTensorMapEncodeTiled from the driver (looked up once)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 1 when launched, 0 when the tensor map could not be made (the caller then
+// uses the halo kernel), an sbp_status otherwise
+template <int CIN, int COUT, bool RELU, bool OUT_F32>
+int launch_tma_t(const ConvArgs& a, cudaStream_t st) {
+    const auto encode = tensor_map_encoder();
+    if (!encode) return 0;
+    CUtensorMap map;
+    const cuuint64_t dims[4] = {(cuuint64_t)CIN, (cuuint64_t)a.nx, (cuuint64_t)a.ny,
+                                (cuuint64_t)a.nz};
+    const cuuint64_t strides[3] = {(cuuint64_t)CIN * 2, (cuuint64_t)a.nx * CIN * 2,
+                                   (cuuint64_t)a.nx * a.ny * CIN * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)kHX, (cuuint32_t)kHY, (cuuint32_t)kHZ};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(a.in), dims,
+               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return 0;
+    constexpr int smem = tma_smem_bytes<CIN, COUT>();
+    auto k = conv3d_tma_kernel<CIN, COUT, RELU, OUT_F32>;
+    if (sbp_cuda_check(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                       "conv3d_bf16: smem attribute"))
+        return SBP_ERR_CUDA;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int ntx = (a.nx + kHTX - 1) / kHTX, nty = (a.ny + kHTY - 1) / kHTY;
+    const long long ntiles = (long long)ntx * nty * a.nz;
+    const int grid = (int)std::min<long long>(std::max(1, sms), ntiles);
+    k<<<grid, kTcThreads, smem, st>>>(map, a, ntx, nty, (int)ntiles);
+    return 1;
+}
+
 template <int CIN, int COUT, bool RELU, bool OUT_F32>
 int launch_conv_t(const ConvArgs& a, unsigned blocks, cudaStream_t st) {
     constexpr int smem = 2 * (kTcRows + COUT) * kTcBK * 2;
@@ -451,6 +687,18 @@ int launch_conv_t(const ConvArgs& a, unsigned blocks, cudaStream_t st) {
 
 template <int CIN, int COUT>
 int launch_conv(const ConvArgs& a, bool relu, bool out_f32, long long V, cudaStream_t st) {
+    // the persistent TMA kernel for 16 or 32 input channels, where its three
+    // halo slots and the weights fit one CTA's shared memory
+    if constexpr (CIN % 16 == 0 && CIN <= 32 && tma_smem_bytes<CIN, COUT>() <= 220 * 1024) {
+        if ((long long)((a.nx + kHTX - 1) / kHTX) * ((a.ny + kHTY - 1) / kHTY) * a.nz < (1LL << 31)) {
+            int r = 0;
+            if (relu && out_f32) r = launch_tma_t<CIN, COUT, true, true>(a, st);
+            else if (relu) r = launch_tma_t<CIN, COUT, true, false>(a, st);
+            else if (out_f32) r = launch_tma_t<CIN, COUT, false, true>(a, st);
+            else r = launch_tma_t<CIN, COUT, false, false>(a, st);
+            if (r != 0) return r == 1 ? SBP_OK : r;
+        }
+    }
     // the halo kernel where its staged halo and weights fit one CTA's shared
     // memory and the grid's y and z extents allow it
     if constexpr (CIN % 16 == 0 && halo_smem_bytes<CIN, COUT>() <= 200 * 1024) {

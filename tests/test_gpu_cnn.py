@@ -62,6 +62,30 @@ def test_conv_tiles_span_the_volume(sb):
     np.testing.assert_array_equal(got.cpu().numpy().reshape(nz, ny, nx, 32), ref)
 
 
+@pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (32, 16)])
+def test_conv_many_tiles_per_cta(sb, cin, cout):
+    """A volume of 960 tiles of 8 x 16 x 1 voxels: the persistent kernel
+    walks several tiles per CTA through its rotating halo slots and
+    alternating accumulators. Exact on dyadic values, ReLU and bf16 output
+    included."""
+    rng = np.random.default_rng(cin + 3 * cout)
+    dims = (64, 45, 40)  # ny = 16 k + 13: a ragged last tile row
+    nx, ny, nz = dims
+    x = dyadic(rng, (nz, ny, nx, cin))
+    w = dyadic(rng, (cout, 27, cin))
+    b = dyadic(rng, (cout,))
+    ref = cnn.conv3d(x, w, b)
+    X = torch.from_numpy(x.reshape(-1, cin)).cuda().to(torch.bfloat16)
+    W = sb.pack_conv_weights(torch.from_numpy(w).cuda())
+    B = torch.from_numpy(b).cuda()
+    got = sb.conv3d(X, dims, W, B, relu=False, out_f32=True)
+    assert sb.cnn_status() == 0
+    np.testing.assert_array_equal(got.cpu().numpy().reshape(nz, ny, nx, cout), ref)
+    got = sb.conv3d(X, dims, W, B, relu=True)
+    refr = cnn.bf16_round(np.maximum(ref, 0.0).astype(np.float32))
+    np.testing.assert_array_equal(got.float().cpu().numpy().reshape(nz, ny, nx, cout), refr)
+
+
 def test_conv_random_values_within_fp32_accumulation(sb):
     rng = np.random.default_rng(7)
     dims = (32, 24, 20)
