@@ -157,16 +157,17 @@ gfwd_group_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restri
             const int k0 = (int)ceilf((e - span) * g.inv_h);  // b_j = e - (j - jr) h < 6a
             const int k1 = (int)floorf((e + span) * g.inv_h);
             const float Ks = p0 * w * (a * a) * 0.5f * pd.rd * g.inv_h * scale;  // K p0 2^F
-            const float inv2a2 = 0.5f / (a * a);
-            for (int k = k0; k <= k1; ++k) {
-                const int j = jr + k;
-                const int r = j - base;
-                if (r < 0 || r > lim || j < 0 || j > Tk) continue;
+            const float nc = -0.72134752044448170f / (a * a);  // g(b) = 2^(b^2 nc)
+            // boundaries j = jr + k inside this pass's cells [base, base + lim]
+            // (which lie inside the record 0 .. Tk)
+            const int klo = max(k0, base - jr), khi = min(k1, base + lim - jr);
+            unsigned int* cb = col + (jr - base) * 32;
+            for (int k = klo; k <= khi; ++k) {
                 const float bj = fmaf(-(float)k, h, e);
-                const long long v = g_f2ll(Ks * expf(-bj * bj * inv2a2));
+                const long long v = g_f2ll(Ks * exp2f(bj * bj * nc));
                 if (v == 0) continue;
-                atomicAdd(col + r * 32, (unsigned int)v);
-                atomicAdd(col + r * 32 + kGWindow * 32, (unsigned int)(int)(v >> kGLoBits));
+                atomicAdd(cb + k * 32, (unsigned int)v);
+                atomicAdd(cb + k * 32 + kGWindow * 32, (unsigned int)(int)(v >> kGLoBits));
             }
         }
         __syncthreads();
@@ -220,7 +221,8 @@ gadj_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restrict__ s
     const bool valid = live && a0 > 0.0f;  // a ball without width radiates nothing
     const float a = valid ? a0 : 1.f;
     const int Tk = g.Tk, M = g.M;
-    const float h = g.h_hi, inv2a2 = 0.5f / (a * a), ia2 = 1.0f / (a * a);
+    const float h = g.h_hi, ia2 = 1.0f / (a * a);
+    const float nc = -0.72134752044448170f * ia2;  // g(b) = exp(-b^2 / 2a^2) = 2^(b^2 nc)
     float ax = 0.f, ay = 0.f, az = 0.f, aa = 0.f, ap = 0.f;
     for (int m0 = 0; m0 < M; m0 += kGSensTile) {
         const int cnt = min(kGSensTile, M - m0);
@@ -249,12 +251,17 @@ gadj_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restrict__ s
             const int k1 = (int)floorf((e + span) * g.inv_h);
             const float* Gm = G + (size_t)(m0 + q) * Tk;
             float A0 = 0.f, A1 = 0.f, A2 = 0.f;
-            for (int k = k0; k <= k1; ++k) {
-                const int j = jr + k;
-                if (j < 0 || j > Tk) continue;
-                const float cj = (j >= 1 ? Gm[j - 1] : 0.0f) - (j < Tk ? Gm[j] : 0.0f);
+            // boundaries j = jr + k in 0 .. Tk; c_j = G[j-1] - G[j] with G = 0
+            // outside the record, G[j-1] carried from the step before
+            const int klo = max(k0, -jr), khi = min(k1, Tk - jr);
+            int j = jr + klo;
+            float gprev = j >= 1 ? Gm[j - 1] : 0.0f;
+            for (int k = klo; k <= khi; ++k, ++j) {
+                const float gcur = j < Tk ? Gm[j] : 0.0f;
+                const float cj = gprev - gcur;
+                gprev = gcur;
                 const float bj = fmaf(-(float)k, h, e);
-                const float gv = expf(-bj * bj * inv2a2) * cj;
+                const float gv = exp2f(bj * bj * nc) * cj;
                 A0 += gv;
                 A1 = fmaf(gv, bj, A1);
                 A2 = fmaf(gv * bj, bj, A2);
