@@ -462,7 +462,7 @@ int sbp_das_volume(sbp_array arr, const float* y_full_dev, const double* origin3
 
 /* The volume CNN of the learned proposal: a delay-and-sum volume scaled to
  * max |.| = 1 (bf16), three 3x3x3 convolutions with ReLU (1 -> 16 -> 32 ->
- * 32 channels, sbp_conv3d_bf16) and a 1x1x1 head with two outputs per voxel
+ * 64 channels, sbp_conv3d_bf16) and a 1x1x1 head with two outputs per voxel
  * (the logit of "a source lies here" and its pressure). Weights are FP32
  * masters (He-normal from `seed`, zero biases) with bf16 copies for the
  * tensor cores; Adam state; activation buffers for one nx x ny x nz volume

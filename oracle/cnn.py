@@ -81,12 +81,12 @@ def das_volume(y, pos, normal, c: float, dt: float, origin, spacing: float, dims
 
 
 # --------------------------------------------------------------------------
-# the proposal CNN: 1 -> 16 -> 32 -> 32 channels of 3x3x3 convolutions with
+# the proposal CNN: 1 -> 16 -> 32 -> 64 channels of 3x3x3 convolutions with
 # ReLU and a 1x1x1 head with two outputs (logit, pressure) per voxel
 # --------------------------------------------------------------------------
 
 PARAM_SHAPES = (("w1", (16, 27, 1)), ("b1", (16,)), ("w2", (32, 27, 16)), ("b2", (32,)),
-                ("w3", (32, 27, 32)), ("b3", (32,)), ("wh", (2, 32)), ("bh", (2,)))
+                ("w3", (64, 27, 32)), ("b3", (64,)), ("wh", (2, 64)), ("bh", (2,)))
 
 
 def unpack_params(p) -> dict:
@@ -148,7 +148,7 @@ def cnn_loss_grad(p, vol, occ, p0, pos_weight: float):
     h = x
     for k in (1, 2, 3):
         h = torch.relu(F.conv3d(h, kern(leaves[f"w{k}"]), leaves[f"b{k}"], padding=1))
-    h = h[0].permute(1, 2, 3, 0).reshape(-1, 32)
+    h = h[0].permute(1, 2, 3, 0).reshape(-1, P["wh"].shape[1])
     out = h @ leaves["wh"].T + leaves["bh"]
     z, q = out[:, 0], out[:, 1]
     V = z.shape[0]

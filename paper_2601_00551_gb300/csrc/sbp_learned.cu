@@ -31,7 +31,7 @@ extern "C" int sbp_conv3d_bf16(const void* in_dev, int nx, int ny, int nz, int c
 
 namespace {
 
-constexpr int kC1 = 16, kC2 = 32, kC3 = 32, kHead = 2;
+constexpr int kC1 = 16, kC2 = 32, kC3 = 64, kHead = 2;
 // parameter blocks (FP32 masters), weights as [cout][27][cin]
 constexpr int kW1 = kC1 * 27 * 1, kB1 = kC1;
 constexpr int kW2 = kC2 * 27 * kC1, kB2 = kC2;
@@ -224,45 +224,41 @@ __global__ void loss_kernel(const float* __restrict__ out, const float* __restri
     }
 }
 
-// head backward: g3[v][c] = (sum_j dout[v][j] Wh[j][c]) [h3 > 0]; and the
-// head's parameter gradients dWh[j][c] = sum_v dout[v][j] h3[v][c], dbh[j]
-__global__ void head_bwd_kernel(const __nv_bfloat16* __restrict__ h3,
-                                const float* __restrict__ dout, long long V,
-                                const float* __restrict__ P, float* __restrict__ G,
-                                __nv_bfloat16* __restrict__ g3) {
+// head backward, data part: g3[v][c] = (sum_j dout[v][j] Wh[j][c]) [h3 > 0]
+__global__ void head_bwd_data_kernel(const __nv_bfloat16* __restrict__ h3,
+                                     const float* __restrict__ dout, long long V,
+                                     const float* __restrict__ P, __nv_bfloat16* __restrict__ g3) {
     __shared__ float w[kWh];
-    __shared__ float red[kWh + kBh];
     for (int t = threadIdx.x; t < kWh; t += blockDim.x) w[t] = P[kOWh + t];
-    for (int t = threadIdx.x; t < kWh + kBh; t += blockDim.x) red[t] = 0.f;
     __syncthreads();
-    float acc[kWh + kBh];
-#pragma unroll
-    for (int t = 0; t < kWh + kBh; ++t) acc[t] = 0.f;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V;
-         v += (long long)gridDim.x * blockDim.x) {
-        const float d0 = dout[2 * v], d1 = dout[2 * v + 1];
-        acc[kWh] += d0;
-        acc[kWh + 1] += d1;
-        const __nv_bfloat16* r = h3 + v * kC3;
-        __nv_bfloat16* o = g3 + v * kC3;
-#pragma unroll
-        for (int c = 0; c < kC3; ++c) {
-            const float hv = __bfloat162float(r[c]);
-            acc[c] = fmaf(d0, hv, acc[c]);
-            acc[kC3 + c] = fmaf(d1, hv, acc[kC3 + c]);
-            const float gv = hv > 0.f ? fmaf(d0, w[c], d1 * w[kC3 + c]) : 0.0f;
-            o[c] = __float2bfloat16(gv);
-        }
+    const long long n = V * kC3;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long v = i / kC3;
+        const int c = (int)(i - v * kC3);
+        const float hv = __bfloat162float(h3[i]);
+        g3[i] = __float2bfloat16(hv > 0.f ? fmaf(dout[2 * v], w[c], dout[2 * v + 1] * w[kC3 + c])
+                                          : 0.0f);
     }
-#pragma unroll
-    for (int t = 0; t < kWh + kBh; ++t) {
-        float a = acc[t];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&red[t], a);
+}
+
+// head backward, parameter part: dWh[j][c] = sum_v dout[v][j] h3[v][c] and
+// dbh[j] = sum_v dout[v][j]. A block takes `chunk` voxels; thread j kC3 + c
+// sums its weight over them (reading a voxel's channels coalesced), threads
+// 2 kC3 and 2 kC3 + 1 the biases; one atomic per thread and block.
+__global__ void head_bwd_param_kernel(const __nv_bfloat16* __restrict__ h3,
+                                      const float* __restrict__ dout, long long V, int chunk,
+                                      float* __restrict__ G) {
+    const int t = threadIdx.x;
+    if (t >= kWh + kBh) return;
+    const long long v0 = (long long)blockIdx.x * chunk, v1 = min(V, v0 + chunk);
+    const int j = t < kWh ? t / kC3 : t - kWh, c = t < kWh ? t % kC3 : 0;
+    float acc = 0.f;
+    for (long long v = v0; v < v1; ++v) {
+        const float d = dout[2 * v + j];
+        acc = t < kWh ? fmaf(d, __bfloat162float(h3[v * kC3 + c]), acc) : acc + d;
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < kWh + kBh; t += blockDim.x) atomicAdd(&G[kOWh + t], red[t]);
+    atomicAdd(&G[kOWh + t], acc);
 }
 
 // g[v][c] *= [h[v][c] > 0] (the ReLU of the layer that produced h)
@@ -649,13 +645,15 @@ int sbp_cnn_train_step(sbp_cnn c, const float* vol_dev, const float* occ_dev, co
     float* G = c->p + 3 * kParams;
     loss_kernel<<<blocks_for(V), 256, 0, st>>>(c->out, occ_dev, p0_dev, V, pos_weight, c->dout,
                                                c->loss);
-    head_bwd_kernel<<<blocks_for(V, 256, 1024), 256, 0, st>>>(c->h3, c->dout, V, c->p, G, c->g3);
+    head_bwd_data_kernel<<<blocks_for(V * kC3), 256, 0, st>>>(c->h3, c->dout, V, c->p, c->g3);
+    static_assert(kWh + kBh <= 256, "one thread per head parameter");
+    head_bwd_param_kernel<<<(unsigned)((V + 511) / 512), 256, 0, st>>>(c->h3, c->dout, V, 512, G);
     // conv3: weights, then the data gradient into g2 (masked by conv2's ReLU)
     const int chunk = 4096;
     const unsigned nchunk = (unsigned)((V + chunk - 1) / chunk);
     wgrad_kernel<kC2, kC3><<<dim3(nchunk, 27), 256, 0, st>>>(c->g3, c->h2, nx, ny, nz, chunk,
                                                            G + kOW3, G + kOB3);
-    sbp_count_launches(3);
+    sbp_count_launches(4);
     if (int e = sbp_conv3d_bf16(c->g3, nx, ny, nz, kC3, c->w3t, padded_k(kC3), nullptr, kC2, 0,
                                 c->g2, 0, s))
         return e;

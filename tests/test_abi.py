@@ -93,4 +93,4 @@ def test_new_entry_points_reject_bad_arguments_on_the_host(lib):
     assert c(0, 4, 4, 1, ctypes.byref(out)) == -1
     v = lib.sbp_voxelize
     v.restype = ctypes.c_int
-    assert lib.sbp_cnn_num_params() == 16 * 27 + 16 + 32 * 27 * 16 + 32 + 32 * 27 * 32 + 32 + 64 + 2
+    assert lib.sbp_cnn_num_params() == 16 * 27 + 16 + 32 * 27 * 16 + 32 + 64 * 27 * 32 + 64 + 128 + 2

@@ -106,7 +106,7 @@ def test_cnn_forward_two_implementations_agree():
         co, _, ci = w.shape
         kt = torch.from_numpy(w).permute(0, 2, 1).reshape(co, ci, 3, 3, 3)
         h = torch.relu(F.conv3d(h, kt, torch.from_numpy(P[f"b{k}"]), padding=1))
-    out = h[0].permute(1, 2, 3, 0).reshape(-1, 32).numpy() @ P["wh"].T + P["bh"]
+    out = h[0].permute(1, 2, 3, 0).reshape(-1, P["wh"].shape[1]).numpy() @ P["wh"].T + P["bh"]
     np.testing.assert_allclose(a, out, rtol=1e-10, atol=1e-10)
 
 
