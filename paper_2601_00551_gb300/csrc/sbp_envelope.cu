@@ -525,21 +525,41 @@ struct VoxGrid {
     double o[3];
     double h;
     int n[3];
+    float of[3], hf;  // the origin and spacing rounded to float
+    float E;          // bound on |x_f - x| of a float voxel-centre coordinate minus a ball's
 };
+
+// The exact test of reading 19, in double with explicit rounding:
+// (dx^2 + dy^2) + dz^2 < R^2, dx = (o + (i + 1/2) h) - c.
+__device__ __forceinline__ bool vox_inside_exact(const VoxGrid& grid, const double* c, double R2,
+                                                 int ii, int j, int k) {
+    const double xc = __dadd_rn(grid.o[0], __dmul_rn((double)ii + 0.5, grid.h));
+    const double yc = __dadd_rn(grid.o[1], __dmul_rn((double)j + 0.5, grid.h));
+    const double zc = __dadd_rn(grid.o[2], __dmul_rn((double)k + 0.5, grid.h));
+    const double dx = __dsub_rn(xc, c[0]), dy = __dsub_rn(yc, c[1]), dz = __dsub_rn(zc, c[2]);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return d2 < R2;
+}
 
 // One thread per ball: every voxel of its bounding range whose centre lies
 // inside the ball gets round(value 2^F) added (integer atomics, so the sum
-// does not depend on the order). The distance test is evaluated in double
-// with explicit rounding: (dx^2 + dy^2) + dz^2 < R^2.
+// does not depend on the order). The test is first made in float: each float
+// offset dx_f differs from the exact dx by at most E (grid.E, bounded on the
+// host) plus its own rounding, so |d2_f - d2| stays below
+// 2 (|dx_f| + |dy_f| + |dz_f| + 3E) E + 2^-20 (d2_f + R^2), and a voxel
+// further than that from the sphere is decided in float with the exact
+// test's outcome. The few voxels within that margin take the exact test.
 __global__ void vox_scatter_kernel(BallsDev b, const float* __restrict__ val, const int* n_dev,
                                    int n_cap, VoxGrid grid, const unsigned int* bits,
                                    unsigned long long* __restrict__ acc) {
     const int n = sbp_read_n(n_dev, n_cap);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double R = (double)b.R[i];
+    const float Rf = b.R[i];
+    const double R = (double)Rf;
     if (!(R > 0.0)) return;
-    const double c[3] = {(double)b.x[i], (double)b.y[i], (double)b.z[i]};
+    const float cf[3] = {b.x[i], b.y[i], b.z[i]};
+    const double c[3] = {(double)cf[0], (double)cf[1], (double)cf[2]};
     int lo[3], hi[3];
     for (int a = 0; a < 3; ++a) {
         const double fl = floor((c[a] - R - grid.o[a]) / grid.h) - 1.0;
@@ -553,20 +573,23 @@ __global__ void vox_scatter_kernel(BallsDev b, const float* __restrict__ val, co
     const long long q = __double2ll_rn(v * scale);
     if (q == 0) return;
     const double R2 = __dmul_rn(R, R);
+    const float R2f = Rf * Rf, E = grid.E;
     for (int k = lo[2]; k <= hi[2]; ++k) {
-        const double zc = __dadd_rn(grid.o[2], __dmul_rn((double)k + 0.5, grid.h));
-        const double dz = __dsub_rn(zc, c[2]);
-        const double dz2 = __dmul_rn(dz, dz);
+        const float dz = fmaf((float)k + 0.5f, grid.hf, grid.of[2]) - cf[2];
         for (int j = lo[1]; j <= hi[1]; ++j) {
-            const double yc = __dadd_rn(grid.o[1], __dmul_rn((double)j + 0.5, grid.h));
-            const double dy = __dsub_rn(yc, c[1]);
-            const double dy2 = __dmul_rn(dy, dy);
+            const float dy = fmaf((float)j + 0.5f, grid.hf, grid.of[1]) - cf[1];
+            const float dyz2 = fmaf(dy, dy, dz * dz);
+            const float ayz = fabsf(dy) + fabsf(dz) + 3.0f * E;
             unsigned long long* row = acc + ((size_t)k * grid.n[1] + j) * grid.n[0];
             for (int ii = lo[0]; ii <= hi[0]; ++ii) {
-                const double xc = __dadd_rn(grid.o[0], __dmul_rn((double)ii + 0.5, grid.h));
-                const double dx = __dsub_rn(xc, c[0]);
-                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), dy2), dz2);
-                if (d2 < R2) atomicAdd(row + ii, (unsigned long long)q);
+                const float dx = fmaf((float)ii + 0.5f, grid.hf, grid.of[0]) - cf[0];
+                const float d2 = fmaf(dx, dx, dyz2);
+                const float margin = fmaf(2.0f * (fabsf(dx) + ayz), E, 9.5367431640625e-7f * (d2 + R2f));
+                bool in;
+                if (d2 < R2f - margin) in = true;
+                else if (d2 > R2f + margin) in = false;
+                else in = vox_inside_exact(grid, c, R2, ii, j, k);
+                if (in) atomicAdd(row + ii, (unsigned long long)q);
             }
         }
     }
@@ -574,11 +597,13 @@ __global__ void vox_scatter_kernel(BallsDev b, const float* __restrict__ val, co
 
 __global__ void vox_finalize_kernel(unsigned long long* __restrict__ acc, long long total,
                                     const unsigned int* bits, float* __restrict__ out) {
-    const double inv = ldexp(1.0, -vox_frac_bits(*bits));
+    // 2^-F as a float (F in [-60, 120], so it is a normal float); the sum is
+    // converted by two 32-bit conversions (|q| < 2^40), not on the FP64 pipe
+    const float inv = __int_as_float((127 - vox_frac_bits(*bits)) << 23);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const long long q = (long long)acc[t];
-        out[t] = (float)((double)q * inv);
+        out[t] = fmaf((float)(int)(q >> 32), 4294967296.0f, (float)(unsigned int)q) * inv;
         acc[t] = 0ull;
     }
 }
@@ -843,6 +868,21 @@ int sbp_voxelize(sbp_balls balls, const float* value_dev, const int* n_dev, int 
     grid.n[0] = nx;
     grid.n[1] = ny;
     grid.n[2] = nz;
+    // float centre x_f = fl(fl(i + 1/2) hf + of) against x = fl(fl((i + 1/2) h) + o):
+    // |x_f - x| <= |o - of| + (n + 1) |h - hf| + two roundings of |x| plus one
+    // of x itself, and the subtraction of the ball's coordinate (at most
+    // |x| + 2 R away, bounded by the extent here with slack) one more
+    grid.hf = (float)spacing;
+    double E = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        grid.of[k] = (float)origin3[k];
+        const double ext = std::fabs(origin3[k]) + (grid.n[k] + 1.0) * spacing;
+        const double e = std::fabs(origin3[k] - (double)grid.of[k]) +
+                         (grid.n[k] + 1.0) * std::fabs(spacing - (double)grid.hf) +
+                         4.0 * ext * 5.9604644775390625e-8;
+        E = std::max(E, e);
+    }
+    grid.E = (float)(E * 2.0) + 1e-30f;  // twice the bound, rounded up
     if (sbp_cuda_check(cudaMemsetAsync(bits, 0, sizeof(unsigned int), st), "voxelize: reset"))
         return SBP_ERR_CUDA;
     int launched = 0;
