@@ -71,6 +71,10 @@ def parse_args(argv=None):
     ap.add_argument("--profile-large", action="store_true",
                     help="only tune and run one forward and one adjoint of the 1M-ball x "
                          "1024-sensor configuration at 80 MHz (a short command for a profiler)")
+    ap.add_argument("--learned-large", action="store_true",
+                    help="only the learned proposal at the large configuration's scale (2000 "
+                         "training phantoms, evaluation on the 1M-ball x 1024-sensor phantom; "
+                         "several minutes)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned initial proposal (CNN training and comparison)")
     ap.add_argument("--no-large", action="store_true",
@@ -753,7 +757,7 @@ def learned_init(sb, arr, wl, y_full, init, plain_seconds, dev, n_train=96, epoc
     b.record()
     torch.cuda.synchronize()
     fwd_ms = a.elapsed_time(b) / reps
-    conv_flops = 2.0 * V * 27 * (1 * 16 + 16 * 32 + 32 * 32)
+    conv_flops = 2.0 * V * 27 * (1 * 16 + 16 * 32 + 32 * 64)  # 1 -> 16 -> 32 -> 64 channels
     peak = measured_peaks().get("bf16_tflops")
     occ_truth, _ = targets(torch.from_numpy(wl.truth.stack()).to(dev))
     logit = net.forward(vol)[:, 0]
@@ -804,6 +808,146 @@ def learned_init(sb, arr, wl, y_full, init, plain_seconds, dev, n_train=96, epoc
             "learned_seconds": total_final,
             "speedup": (plain_full["elapsed_seconds"] / total_final) if total_final else None,
         },
+    }
+
+
+def _phantom(args):
+    """A training phantom (host side; runs in a spawned worker process)."""
+    import workloads
+
+    n, half, seed = args
+    return workloads.vessel_tree(n, half=half, seed=seed).stack()
+
+
+def learned_large(n_train=2000, epochs=4, n_phantom=100_000, grid=64, full_iters=300, seg=10,
+                  lr=1e-3, pos_weight=10.0, workers=16):
+    """The learned initial proposal at the large configuration's scale: the
+    CNN trains on `n_train` seeded vessel phantoms of the 40 mm cube (the
+    tree generator of the 1M-ball phantom, sampled with `n_phantom` balls:
+    the same tubes, sparser), each rendered at 80 MHz on the 1024-sensor cap
+    with 1% noise and turned into a grid^3 delay-and-sum volume; it is then
+    evaluated on the 1M-ball phantom. The plain pipeline runs the Pro
+    schedule for `full_iters` iterations from the 1M-ball random cloud with
+    zero-gradient filtering; the learned pipeline runs it from the proposal
+    until it reaches the plain pipeline's final residual. Phantoms are made
+    by `workers` spawned processes while the GPU renders them."""
+    import multiprocessing as mp
+
+    import torch
+
+    import __graft_entry__ as ge
+    import workloads
+
+    pool = mp.get_context("spawn").Pool(workers)
+    ge.build()
+    from paper_2601_00551_gb300 import slingbag as sb
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    wl = workloads.large()
+    nl = len(wl.levels)
+    fine = nl - 1
+    half = wl.half
+    n0 = wl.init.n
+    arr = sb.SensorArray(wl.sensors.pos, wl.sensors.normal, wl.c, wl.fs_mhz, wl.T, wl.levels,
+                         n_cap=2 * n0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(4)
+    arr.set_sampling_level(fine)
+    S = arr.forward(torch.from_numpy(wl.truth.stack()).to(dev))
+    y_full = S + torch.randn(S.shape, generator=gen, device=dev) * (0.01 * S.abs().max())
+    init = torch.zeros((5, 2 * n0), dtype=torch.float32, device=dev)
+    init[:, :n0] = torch.from_numpy(wl.init.stack()).to(dev)
+
+    dims = (grid, grid, grid)
+    h = 2.0 * half / grid
+    origin = (-half, -half, -half)
+    V = grid ** 3
+    scratch = torch.zeros(V + 1, dtype=torch.int64, device=dev)
+
+    def targets(B):
+        ones = torch.ones(B.shape[1], dtype=torch.float32, device=dev)
+        cnt = sb.voxelize(B, origin, h, dims, values=ones, scratch=scratch).reshape(-1).clone()
+        psum = sb.voxelize(B, origin, h, dims, scratch=scratch).reshape(-1)
+        occ = (cnt > 0.5).float()
+        return occ, torch.where(occ > 0, psum / cnt.clamp(min=1.0), torch.zeros_like(psum))
+
+    t0 = time.perf_counter()
+    vols, occs, p0s = [], [], []
+    jobs = [(n_phantom, half, 1000 + i) for i in range(n_train)]
+    for ph in pool.imap(_phantom, jobs, chunksize=4):
+        B = torch.from_numpy(ph).to(dev)
+        St = arr.forward(B)
+        St = St + torch.randn(St.shape, generator=gen, device=dev) * (0.01 * St.abs().max())
+        vols.append(arr.das_volume(St.contiguous(), origin, h, dims).reshape(-1).clone())
+        occ, p0t = targets(B)
+        occs.append(occ)
+        p0s.append(p0t)
+    pool.close()
+    torch.cuda.synchronize()
+    data_s = time.perf_counter() - t0
+
+    net = sb.VolumeCNN(dims, seed=1)
+    loss = torch.zeros(2, dtype=torch.float64, device=dev)
+    rng = np.random.default_rng(0)
+    curve = []
+    t0 = time.perf_counter()
+    for _ in range(epochs):
+        acc = torch.zeros(2, dtype=torch.float64, device=dev)
+        for i in rng.permutation(n_train):
+            net.train_step(vols[i], occs[i], p0s[i], lr=lr, pos_weight=pos_weight, loss=loss)
+            acc += loss
+        curve.append([float(v) / n_train for v in acc.cpu().tolist()])
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    if sb.cnn_status() != 0:
+        raise RuntimeError("a tensor-core wait gave up during training")
+    del vols, occs, p0s
+
+    prop = torch.zeros((5, 2 * n0), dtype=torch.float32, device=dev)
+    n_prop = torch.zeros(1, dtype=torch.int32, device=dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    for _ in range(2):  # the first call allocates the proposal scratch
+        a.record()
+        vol = arr.das_volume(y_full, origin, h, dims).reshape(-1)
+        net.propose(vol, origin, h, threshold=0.5, seed=7, R=0.5 * h, p_range=(0.05, 1.0),
+                    out=prop, n_dev=n_prop)
+        b.record()
+        torch.cuda.synchronize()
+    infer_s = a.elapsed_time(b) / 1e3
+    n_learn = int(n_prop.item())
+    occ_truth, _ = targets(torch.from_numpy(wl.truth.stack()).to(dev))
+    pred = net.forward(vol)[:, 0] > 0.0
+    tp = float((pred & (occ_truth > 0)).sum().item())
+    quality = {"proposed_voxels": int(pred.sum().item()), "true_voxels": int(occ_truth.sum().item()),
+               "precision": tp / max(1.0, float(pred.sum().item())),
+               "recall": tp / max(1.0, float(occ_truth.sum().item()))}
+    ynorm = float((y_full.double() ** 2).sum().item())
+
+    def rel(balls, n_dev):
+        arr.set_sampling_level(fine)
+        St = arr.forward(balls, n=n_dev)
+        _, L = arr.residual(St, y_full)
+        return float(L.item()) / ynorm
+
+    plain = run_to_residual(sb, arr, wl, y_full, init, n0, pro_segments(nl, seg), True, 0.0, seg,
+                            full_iters, rel)
+    r_final = plain["final_rel_residual"]
+    learned = run_to_residual(sb, arr, wl, y_full, prop, n_learn, pro_segments(nl, seg), False,
+                              r_final, seg, 4 * full_iters, rel)
+    total = (learned["seconds"] + infer_s) if learned["seconds"] is not None else None
+    net.close()
+    arr.close()
+    return {
+        "learned_large": True, "workload": wl.name, "grid": list(dims), "spacing_mm": h,
+        "train_phantoms": n_train, "phantom_balls": n_phantom, "epochs": epochs,
+        "data_seconds": data_s, "train_seconds": train_s, "loss_per_epoch": curve,
+        "proposal": {"balls": n_learn, **quality}, "inference_seconds": infer_s,
+        "plain": {"iterations": plain["iterations"], "seconds": plain["elapsed_seconds"],
+                  "final_rel_residual": r_final, "balls": plain["balls"]},
+        "learned": learned, "learned_seconds": total,
+        "speedup": (plain["elapsed_seconds"] / total) if total else None,
     }
 
 
@@ -1353,6 +1497,9 @@ def main(argv=None):
     args = parse_args(argv)
     if args.profile_large:
         print(json.dumps(profile_large()))
+        return 0
+    if args.learned_large:
+        print(json.dumps(learned_large()))
         return 0
     if args.profile_cnn:
         print(json.dumps(profile_cnn()))
