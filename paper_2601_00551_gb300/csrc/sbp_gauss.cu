@@ -207,14 +207,21 @@ __global__ void gfwd_finalize_kernel(unsigned long long* __restrict__ acc, int T
 constexpr int kGAdjThreads = 128;
 constexpr int kGSensTile = 128;
 
+// grid.y CTAs share a chunk of kGAdjThreads balls, each taking 1/grid.y of
+// the sensors; their partial sums go to scratch [chunk][part][5][ball] and
+// the last of them to arrive (a ticket per chunk) adds the parts in rank
+// order and writes the gradients, so the result does not depend on timing.
 __global__ void __launch_bounds__(kGAdjThreads)
 gadj_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restrict__ sens, LevelGeo g,
             const float* __restrict__ G, unsigned mask, float* gx_, float* gy_, float* gz_,
-            float* ga_, float* gp_) {
+            float* ga_, float* gp_, float* __restrict__ part_all,
+            unsigned int* __restrict__ tickets) {
+    static_assert(kGAdjThreads == SBP_ADJ_CHUNK, "the partial-sum scratch holds 128-ball chunks");
     __shared__ float s[kGSensTile * 6];
+    __shared__ bool s_last;
     const int n = sbp_read_n(n_dev, n_cap);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (blockIdx.x * blockDim.x >= n) return;  // uniform over the block
+    if (blockIdx.x * blockDim.x >= n) return;  // uniform over the chunk's CTAs
     const bool live = i < n;
     const float cx = live ? b.x[i] : 0.f, cy = live ? b.y[i] : 0.f, cz = live ? b.z[i] : 0.f;
     const float a0 = live ? b.R[i] : 1.f, p0 = live ? b.p0[i] : 0.f;
@@ -224,8 +231,11 @@ gadj_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restrict__ s
     const float h = g.h_hi, ia2 = 1.0f / (a * a);
     const float nc = -0.72134752044448170f * ia2;  // g(b) = exp(-b^2 / 2a^2) = 2^(b^2 nc)
     float ax = 0.f, ay = 0.f, az = 0.f, aa = 0.f, ap = 0.f;
-    for (int m0 = 0; m0 < M; m0 += kGSensTile) {
-        const int cnt = min(kGSensTile, M - m0);
+    const int split = (int)gridDim.y, part = (int)blockIdx.y;
+    const int per = (M + split - 1) / split;
+    const int m_begin = min(M, part * per), m_end = min(M, m_begin + per);
+    for (int m0 = m_begin; m0 < m_end; m0 += kGSensTile) {
+        const int cnt = min(kGSensTile, m_end - m0);
         __syncthreads();
         for (int t = threadIdx.x; t < cnt * 6; t += blockDim.x) {
             const int k = t / cnt, j = t % cnt;
@@ -276,13 +286,34 @@ gadj_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restrict__ s
             az += gd * uz + gw * (S6[5] - cosv * uz) * pd.rd;
         }
     }
-    if (!live) return;
-    const bool xyz = mask & SBP_MASK_XYZ;
-    gx_[i] = xyz ? ax : 0.0f;
-    gy_[i] = xyz ? ay : 0.0f;
-    gz_[i] = xyz ? az : 0.0f;
-    ga_[i] = (mask & SBP_MASK_R) ? aa : 0.0f;
-    gp_[i] = (mask & SBP_MASK_P0) ? ap : 0.0f;
+    const size_t chunk = blockIdx.x;
+    const int t = threadIdx.x;
+    float* __restrict__ mine = part_all + (chunk * split + part) * 5 * kGAdjThreads;
+    mine[0 * kGAdjThreads + t] = ax;
+    mine[1 * kGAdjThreads + t] = ay;
+    mine[2 * kGAdjThreads + t] = az;
+    mine[3 * kGAdjThreads + t] = aa;
+    mine[4 * kGAdjThreads + t] = ap;
+    __threadfence();
+    __syncthreads();
+    if (t == 0) s_last = atomicAdd(&tickets[chunk], 1u) == (unsigned int)(split - 1);
+    __syncthreads();
+    if (!s_last) return;  // uniform over the block
+    __threadfence();
+    if (live) {
+        const float* __restrict__ all = part_all + chunk * split * 5 * kGAdjThreads + t;
+        float a[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int r = 0; r < split; ++r)
+#pragma unroll
+            for (int c = 0; c < 5; ++c) a[c] += __ldcg(all + ((size_t)r * 5 + c) * kGAdjThreads);
+        const bool xyz = mask & SBP_MASK_XYZ;
+        gx_[i] = xyz ? a[0] : 0.0f;
+        gy_[i] = xyz ? a[1] : 0.0f;
+        gz_[i] = xyz ? a[2] : 0.0f;
+        ga_[i] = (mask & SBP_MASK_R) ? a[3] : 0.0f;
+        gp_[i] = (mask & SBP_MASK_P0) ? a[4] : 0.0f;
+    }
+    if (t == 0) tickets[chunk] = 0u;  // ready for the next launch
 }
 
 }  // namespace
@@ -347,10 +378,17 @@ int sbp_adjoint_gauss(sbp_array arr, sbp_balls balls, const int* n_dev, int n_ca
     if (n_cap == 0) return SBP_OK;
     const LevelGeo g = sbp_level_geo(arr, arr->level);
     const BallsDev bd{balls.x, balls.y, balls.z, balls.R, balls.p0};
-    gadj_kernel<<<(n_cap + kGAdjThreads - 1) / kGAdjThreads, kGAdjThreads, 0,
-                  reinterpret_cast<cudaStream_t>(stream)>>>(bd, n_dev, n_cap, arr->d_sens, g, G_dev,
-                                                            grad_mask, out.gx, out.gy, out.gz,
-                                                            out.gR, out.gp0);
+    // enough CTAs per chunk (each over a share of at least kGSensTile
+    // sensors) for about four waves of resident CTAs (~8 per SM): one CTA
+    // per chunk left the last wave mostly empty
+    const int chunks = (n_cap + kGAdjThreads - 1) / kGAdjThreads;
+    int split = 1;
+    while (split < SBP_ADJ_MAX_SPLIT && (long long)chunks * split < 32LL * arr->sm_count &&
+           2 * split * kGSensTile <= g.M)
+        split *= 2;
+    gadj_kernel<<<dim3(chunks, split), kGAdjThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        bd, n_dev, n_cap, arr->d_sens, g, G_dev, grad_mask, out.gx, out.gy, out.gz, out.gR,
+        out.gp0, arr->d_adj_part, arr->d_adj_ticket);
     sbp_count_launches(1);
     return sbp_cuda_check(cudaGetLastError(), "adjoint_gauss launch") ? SBP_ERR_CUDA : SBP_OK;
 }
