@@ -54,9 +54,9 @@ namespace {
 
 constexpr int kAdjThreads = SBP_ADJ_CHUNK;  // balls (threads) per adjoint CTA
 constexpr int kAdjSplit = 4;      // default CTAs per chunk, each taking 1/split of the sensors
-constexpr int kAdjGroup = 16;     // staging buffer size: kAdjGroup windows of the mean length below
-constexpr int kAdjWindow = 224;   // mean cells per staged window the buffer is sized for
-constexpr int kAdjWindowP0 = 128; // the same for the p0-only adjoint, which keeps more CTAs per SM
+constexpr int kAdjCap = 3584;     // cells per staging buffer (two buffers per CTA)
+constexpr int kAdjCapP0 = 2048;   // the same for the p0-only adjoint, which keeps more CTAs per SM
+constexpr int kAdjShare = 16;     // a CTA's share of the sensors is a multiple of this
 constexpr int kAdjMeta = 128;     // sensors whose set-up is held in shared memory at once
 
 __device__ __forceinline__ void downsample_one(const float* __restrict__ y, int T, int f,
@@ -230,7 +230,7 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     // two staging buffers of kCap cells, each holding the windows of one
     // group of sensors packed one after another; after the last group the
     // first one holds this CTA's partial sums
-    constexpr int kCap = kAdjGroup * (P0_ONLY ? kAdjWindowP0 : kAdjWindow);
+    constexpr int kCap = P0_ONLY ? kAdjCapP0 : kAdjCap;
     constexpr int kWin = kCap / 2;  // longest window staged: a pair of them fills a buffer
     __shared__ __align__(16) float sG[2][kCap];
     __shared__ float4 s_sa[kAdjMeta + 1];  // sx, sy, sz, nx (+1: partner of an odd last sensor)
@@ -294,7 +294,7 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     // this CTA's share of the sensors, whole groups
     const int part = (int)blockIdx.y;
     const int split = (int)gridDim.y;
-    const int per = ((M + split - 1) / split + kAdjGroup - 1) / kAdjGroup * kAdjGroup;
+    const int per = ((M + split - 1) / split + kAdjShare - 1) / kAdjShare * kAdjShare;
     const int m_begin = min(M, part * per), m_end = min(M, m_begin + per);
     // The share is walked in blocks of up to kAdjMeta sensors whose positions,
     // normals and cell ranges are set up once, and within a block in groups of
