@@ -204,7 +204,7 @@ int sbp_adjoint(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap,
  * choice, the adjoint differs by float summation order). fwd_chunk: balls
  * per forward CTA, 0 (default: 512, fewer for small clouds) or a power of
  * two in [32, 1024]; adj_split: adjoint CTAs sharing a ball chunk, each
- * taking a share of the sensors, 0 (default 4), 1, 2, 4 or 8. SBP_ERR_ARG
+ * taking a share of the sensors, 0 (default 8), 1, 2, 4 or 8. SBP_ERR_ARG
  * for other values, SBP_ERR_LEVEL for k out of range. */
 int sbp_set_tiles(sbp_array arr, int k, int fwd_chunk, int adj_split);
 int sbp_get_tiles(sbp_array arr, int k, int* fwd_chunk, int* adj_split);

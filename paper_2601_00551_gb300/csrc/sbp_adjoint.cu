@@ -53,7 +53,7 @@
 namespace {
 
 constexpr int kAdjThreads = SBP_ADJ_CHUNK;  // balls (threads) per adjoint CTA
-constexpr int kAdjSplit = 4;      // default CTAs per chunk, each taking 1/split of the sensors
+constexpr int kAdjSplit = 8;      // default CTAs per chunk, each taking 1/split of the sensors
 constexpr int kAdjCap = 3584;     // cells per staging buffer (two buffers per CTA)
 constexpr int kAdjCapP0 = 2048;   // the same for the p0-only adjoint, which keeps more CTAs per SM
 constexpr int kAdjShare = 16;     // a CTA's share of the sensors is a multiple of this
