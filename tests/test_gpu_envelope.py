@@ -134,3 +134,23 @@ def test_voxelize_is_order_independent(sb):
                      scratch=scratch)
     assert torch.equal(v1, v2)
     assert int(scratch.count_nonzero().item()) == 0  # left zero for the next call
+
+
+def test_voxelize_exact_on_sphere_boundaries(sb):
+    """Balls centred on voxel centres with radii whose squares are sums of
+    three squares of voxel steps (R = 0.5, 0.75, 1, 1.25 at h = 0.25): many
+    voxel centres lie exactly on a sphere (d^2 = R^2 in every precision),
+    some radii are one float step larger. The float screen must hand those
+    to the exact test and agree with the oracle's strict <."""
+    h = 0.25
+    origin, dims = (-4.0, -4.0, -4.0), (32, 32, 32)
+    rng = np.random.default_rng(9)
+    ijk = rng.integers(6, 26, size=(400, 3))
+    c = (np.array(origin) + (ijk + 0.5) * h).astype(np.float32)
+    R = rng.choice(np.array([0.5, 0.75, 1.0, 1.25], dtype=np.float32), 400)
+    R = np.where(rng.uniform(size=400) < 0.3, np.nextafter(R, np.float32(2)), R).astype(np.float32)
+    b = np.stack([c[:, 0], c[:, 1], c[:, 2], R, rng.uniform(0.1, 1.0, 400)]).astype(np.float32)
+    ref = E.voxelize(b, origin, h, dims)
+    got = sb.voxelize(torch.from_numpy(b).cuda(), origin, h, dims).cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(got != 0, ref != 0)
+    np.testing.assert_allclose(got, ref, rtol=1e-6, atol=1e-9 * np.abs(ref).max())
