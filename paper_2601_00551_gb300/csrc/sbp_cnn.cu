@@ -371,15 +371,19 @@ __global__ void __launch_bounds__(kTcThreads) conv3d_halo_kernel(ConvArgs a) {
     if (tid == 0) {
         constexpr uint32_t idesc = umma_idesc_bf16(kTcRows, COUT);
         const uint32_t hb = smem_u32(s_halo), wb = smem_u32(s_w);
-#pragma unroll 1
+        // base descriptors plus compile-time offsets (>> 4) in the start-address
+        // field, which cannot carry out of its 14 bits (shared addresses < 256 KB)
+        const uint64_t da = umma_desc(hb, kPlane, kHX * 16);
+        const uint64_t db = umma_desc(wb, kWBlock, 128);
+#pragma unroll
         for (int tap = 0; tap < 27; ++tap) {
             // (dx, dy, dz) + 1 = (tap % 3, tap / 3 % 3, tap / 9): the tile's voxel (0, 0)
             // reads halo voxel (dx + 1, dy + 1, dz + 1)
             const uint32_t aoff = (uint32_t)(((tap / 9) * kHY + (tap / 3) % 3) * kHX + tap % 3) * 16;
 #pragma unroll
             for (int kp = 0; kp < kChunks / 2; ++kp)
-                tc_mma(tmem, umma_desc(hb + aoff + 2 * kp * kPlane, kPlane, kHX * 16),
-                       umma_desc(wb + (tap * kChunks + 2 * kp) * kWBlock, kWBlock, 128), idesc,
+                tc_mma(tmem, da + ((aoff + 2 * kp * kPlane) >> 4),
+                       db + (((tap * kChunks + 2 * kp) * kWBlock) >> 4), idesc,
                        (tap > 0 || kp > 0) ? 1u : 0u);
         }
         tc_commit(&bar);
@@ -554,15 +558,20 @@ conv3d_tma_kernel(const __grid_constant__ CUtensorMap tmap, ConvArgs a, int ntx,
                 constexpr uint32_t idesc = umma_idesc_bf16(kTcRows, COUT);
                 const uint32_t hb = smem_u32(s_halo + s * kSlotBytes), wb = smem_u32(s_w);
                 const uint32_t d = tmem + (uint32_t)((i & 1) * kTcCols);
-#pragma unroll 1
+                // descriptors of the halo and weight bases; each MMA adds its
+                // compile-time offset (>> 4) to the start-address field, which
+                // cannot carry out of its 14 bits (shared addresses < 256 KB)
+                const uint64_t da = umma_desc(hb, kPlanePad, kHX * 16);
+                const uint64_t db = umma_desc(wb, kWBlock, 128);
+#pragma unroll
                 for (int tap = 0; tap < 27; ++tap) {
                     const uint32_t aoff =
                         (uint32_t)(((tap / 9) * kHY + (tap / 3) % 3) * kHX + tap % 3) * 16;
 #pragma unroll
                     for (int kp = 0; kp < kChunks / 2; ++kp)
-                        tc_mma(d, umma_desc(hb + aoff + 2 * kp * kPlanePad, kPlanePad, kHX * 16),
-                               umma_desc(wb + (tap * kChunks + 2 * kp) * kWBlock, kWBlock, 128),
-                               idesc, (tap > 0 || kp > 0) ? 1u : 0u);
+                        tc_mma(d, da + ((aoff + 2 * kp * kPlanePad) >> 4),
+                               db + (((tap * kChunks + 2 * kp) * kWBlock) >> 4), idesc,
+                               (tap > 0 || kp > 0) ? 1u : 0u);
                 }
                 tc_commit(&done[i & 1]);
             }
