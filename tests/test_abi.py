@@ -94,3 +94,17 @@ def test_new_entry_points_reject_bad_arguments_on_the_host(lib):
     v = lib.sbp_voxelize
     v.restype = ctypes.c_int
     assert lib.sbp_cnn_num_params() == 16 * 27 + 16 + 32 * 27 * 16 + 32 + 64 * 27 * 32 + 64 + 128 + 2
+
+
+def test_tile_entry_points_reject_a_null_array_on_the_host(lib):
+    """The per-level tile calls check their array before any CUDA call."""
+    P = ctypes.c_void_p
+    lib.sbp_set_tiles.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.sbp_get_tiles.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_int)]
+    assert lib.sbp_set_tiles(None, 0, 256, 2) == -1
+    c, s = ctypes.c_int(7), ctypes.c_int(7)
+    assert lib.sbp_get_tiles(None, 0, ctypes.byref(c), ctypes.byref(s)) == -1
+    assert (c.value, s.value) == (7, 7)  # untouched
+    lib.sbp_last_error.restype = ctypes.c_char_p
+    assert b"null array" in lib.sbp_last_error()
