@@ -178,6 +178,19 @@ struct GradOut {
 // Window sums of one pair against the residual row of its sensor: the first
 // cell gf = G[jL-1], the last cell gl = G[jH] (0 past the record) and, with
 // d_q = G[jL+q] - gl over the L = min(jH, Tk) - jL ramp cells,
+// Last cell any pair of the box can touch at this sensor, like sbp_box_cells
+// but not clamped to the record: the staged window runs on past the record's
+// end as zeros (G = 0 there), so the paired window sums need no clamps.
+__device__ __forceinline__ int adj_box_hi(float sx, float sy, float sz, const float* box,
+                                          const LevelGeo& g) {
+    const float fx = fmaxf(fabsf(sx - box[0]), fabsf(sx - box[3]));
+    const float fy = fmaxf(fabsf(sy - box[1]), fabsf(sy - box[4]));
+    const float fz = fmaxf(fabsf(sz - box[2]), fabsf(sz - box[5]));
+    const float dmax = sqrtf(fx * fx + fy * fy + fz * fz);
+    const float hi = ceilf((dmax + fmaxf(box[6], 0.0f)) * g.inv_h) + 3.0f;
+    return (int)fminf(fmaxf(hi, -1.0f), 2.0e9f);
+}
+
 // E0 = sum_q d_q and E1 = sum_q q d_q. Reads the staged window when it holds
 // every needed cell, else the global row.
 __device__ __forceinline__ void adj_window_sums(const float* __restrict__ sGrow, int jlo, int len,
@@ -314,6 +327,8 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
             const float sx = sens[m], sy = sens[M + m], sz = sens[2 * M + m];
             int jlo, jhi;
             sbp_box_cells(sx, sy, sz, s_box, g, jlo, jhi);
+            // staged through the box's last cell even past the record (zeros there)
+            jhi = max(jhi, adj_box_hi(sx, sy, sz, s_box, g));
             int len = max(0, jhi - jlo + 1);
             if (len > kWin) len = 0;
             s_sa[t] = make_float4(sx, sy, sz, sens[3 * M + m]);
@@ -354,8 +369,13 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
                 const int jlo = __float_as_int(sb.z), len = __float_as_int(sb.w);
                 const float* row = G + (size_t)(mb + s) * Tk + jlo;
                 float* d = dst + s_off[s];
-                for (int r = lane; r < len; r += 32)
-                    __pipeline_memcpy_async(d + r, row + r, sizeof(float));
+                const int inrec = min(len, Tk - jlo);  // cells before the record's end
+                for (int r = lane; r < len; r += 32) {
+                    if (r < inrec)
+                        __pipeline_memcpy_async(d + r, row + r, sizeof(float));
+                    else
+                        d[r] = 0.0f;
+                }
             }
         };
         stage(0);
@@ -412,19 +432,18 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
                 const int jloA = __float_as_int(sbA.z), lenA = __float_as_int(sbA.w);
                 const int jloB = __float_as_int(sbB.z), lenB = __float_as_int(sbB.w);
                 float2 gf = f2(0.f), gl = f2(0.f), E0 = f2(0.f), E1 = f2(0.f);
-                const int LA = min(wa.jH, Tk) - wa.jL, LB = min(wb.jH, Tk) - wb.jL;
-                // side by side when both windows are staged and differ by at most
-                // one ramp cell: the shorter one then reads one cell further, its
-                // own last cell G[jH] (inside the record), which adds d = 0
-                const bool inA = okA && wa.jL - 1 >= jloA && min(wa.jH, Tk - 1) - jloA < lenA;
-                const bool inB = okB && wb.jL - 1 >= jloB && min(wb.jH, Tk - 1) - jloB < lenB;
-                if (inA && inB && abs(LA - LB) <= 1 && (LA >= LB || wa.jH < Tk) &&
-                    (LB >= LA || wb.jH < Tk)) {
+                // side by side when both windows are staged (cells past the
+                // record staged as zeros, so no clamps) and differ by at most one
+                // ramp cell: the shorter one then reads one cell further, its own
+                // last cell G[jH], which adds d = 0
+                const int LA = wa.jH - wa.jL, LB = wb.jH - wb.jL;
+                const bool inA = okA && wa.jL - 1 >= jloA && wa.jH - jloA < lenA;
+                const bool inB = okB && wb.jL - 1 >= jloB && wb.jH - jloB < lenB;
+                if (inA && inB && abs(LA - LB) <= 1) {
                     const float* GwA = sGA - jloA + wa.jL;
                     const float* GwB = sGB - jloB + wb.jL;
                     gf = make_float2(GwA[-1], GwB[-1]);
-                    gl = make_float2(wa.jH < Tk ? GwA[wa.jH - wa.jL] : 0.0f,
-                                     wb.jH < Tk ? GwB[wb.jH - wb.jL] : 0.0f);
+                    gl = make_float2(GwA[LA], GwB[LB]);
                     const float2 ngl = f2neg(gl);
                     const int Lm = max(LA, LB);
                     float2 run = f2(0.f);
