@@ -516,7 +516,7 @@ NCU_TRAFFIC = {
                 "sha256": "b406e1fb2be19f8e", "bytes": 5.264128e6},
     "adjoint": {"sources": ["paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "483f842aadc4d2f0", "bytes": 3.758848e6},
+                "sha256": "623a69f982ba5e9b", "bytes": 3.758848e6},
 }
 
 

@@ -27,7 +27,8 @@
 //                balls (one thread per ball) and split the sensors between
 //                them. Each CTA walks its sensors in groups. For each group
 //                it stages, per sensor, the window of G that the chunk's
-//                bounding box can reach, packed one after another into one
+//                bounding box can reach (past the record's end as zeros),
+//                packed one after another into one
 //                of two shared buffers with asynchronous copies, the next
 //                group's copies in flight while the current group is
 //                evaluated; a group takes as many sensor pairs as fill the
@@ -48,7 +49,6 @@
 #include <cuda_pipeline.h>
 
 #include "sbp_internal.cuh"
-
 
 namespace {
 
