@@ -575,3 +575,34 @@ def test_tile_choices_and_autotune(sb):
         g = arr.adjoint(balls, Gd).cpu().numpy()
         for c in range(5):
             assert rel_l2(g[c, pick], ref[c]) <= GRAD_TOL, (f, "tuned", c)
+
+
+@pytest.mark.parametrize("sort", [False, True])
+def test_adjoint_windows_crossing_the_record_end(sb, sort):
+    """A record that ends inside the balls' arrival range: the tiny cloud
+    reaches the 20 mm cap at cells ~480-590 of 40 MHz and T = 560, so many
+    pairs' windows run past the record's end, where the staged windows are
+    padded with zeros. Full and p0-only gradients against the oracle at two
+    levels, sorted (staged) and unsorted (longer windows, partly unstaged)."""
+    wl = workloads.tiny(n_init=1500, T=560, sort=sort)
+    b = wl.init.stack()
+    n = b.shape[1]
+    arr = make_array(sb, wl, (2, 1), n)
+    balls = torch.from_numpy(b).cuda()
+    rng = np.random.default_rng(12)
+    d = np.linalg.norm(b[:3].T[:, None, :] - wl.sensors.pos[None], axis=2)
+    for k, f in enumerate((2, 1)):
+        Tk = -(-560 // f)
+        h = wl.c * dt_of(wl, f)
+        assert np.mean((d + b[3][:, None]) / h > Tk) > 0.05  # the case is real
+        arr.set_sampling_level(k)
+        G = rng.normal(size=(wl.sensors.M, Tk)).astype(np.float32)
+        Gd = torch.from_numpy(G).cuda()
+        ref = oracle.adjoint(b, wl.sensors.pos, wl.sensors.normal, wl.c, dt_of(wl, f), Tk,
+                             G.astype(np.float64), threads=threads())
+        g = arr.adjoint(balls, Gd).cpu().numpy()
+        for c in range(5):
+            assert rel_l2(g[c], ref[c]) <= GRAD_TOL, (f, c)
+        gp = arr.adjoint(balls, Gd, mask=sb.MASK_P0).cpu().numpy()
+        assert np.all(gp[:4] == 0)
+        assert rel_l2(gp[4], ref[4]) <= GRAD_TOL, f
