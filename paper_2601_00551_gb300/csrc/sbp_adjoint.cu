@@ -45,6 +45,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include <cuda_pipeline.h>
 
@@ -235,7 +236,7 @@ __device__ __forceinline__ void adj_window_sums(const float* __restrict__ sGrow,
 // P0_ONLY: only dL/dp0 is wanted (the zero-gradient pass), so the chain rule
 // for R and the centre is skipped.
 // gridDim.y CTAs share a chunk, each taking 1/gridDim.y of the sensors.
-template <bool P0_ONLY>
+template <bool P0_ONLY, int WMODE>
 __global__ void __launch_bounds__(kAdjThreads, P0_ONLY ? 8 : 6)
 adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, LevelGeo g,
                  const float* __restrict__ G_all, unsigned mask, GradOut out,
@@ -246,9 +247,20 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     constexpr int kCap = P0_ONLY ? kAdjCapP0 : kAdjCap;
     constexpr int kWin = kCap / 2;  // longest window staged: a pair of them fills a buffer
     __shared__ __align__(16) float sG[2][kCap];
-    __shared__ float4 s_sa[kAdjMeta + 1];  // sx, sy, sz, nx (+1: partner of an odd last sensor)
-    __shared__ float4 s_sb[kAdjMeta + 1];  // ny, nz, jlo, staged length (as int bits; 0: not staged)
-    __shared__ int s_off[kAdjMeta + 1];    // offset of the staged window in its group's buffer
+    // set-up of sensor pairs (2p, 2p + 1), each quantity of both sensors side
+    // by side so that a pair's float2 operands load as one register pair
+    __shared__ float4 s_q0[kAdjMeta / 2 + 1];  // sx, sy
+    __shared__ float4 s_q1[kAdjMeta / 2 + 1];  // sz, nx
+    __shared__ float4 s_q2[kAdjMeta / 2 + 1];  // ny, nz
+    __shared__ int4 s_q3[kAdjMeta / 2 + 1];    // jlo, staged length (0: not staged)
+    __shared__ int2 s_qo[kAdjMeta / 2 + 1];    // offset of the staged window in its group's buffer
+    float* const q0f = reinterpret_cast<float*>(s_q0);
+    float* const q1f = reinterpret_cast<float*>(s_q1);
+    float* const q2f = reinterpret_cast<float*>(s_q2);
+    int* const q3i = reinterpret_cast<int*>(s_q3);
+    int* const qoi = reinterpret_cast<int*>(s_qo);
+    // element of quantity c (0 or 1) of sensor t within its pair's record
+    auto at = [](int t, int c) { return 4 * (t >> 1) + 2 * c + (t & 1); };
     __shared__ int s_gfirst[kAdjMeta / 2 + 2];  // first sensor of each group, then the count
     __shared__ int s_ng;
     __shared__ float s_red[(kAdjThreads / 32) * 7];
@@ -331,32 +343,81 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
             jhi = max(jhi, adj_box_hi(sx, sy, sz, s_box, g));
             int len = max(0, jhi - jlo + 1);
             if (len > kWin) len = 0;
-            s_sa[t] = make_float4(sx, sy, sz, sens[3 * M + m]);
-            s_sb[t] = make_float4(sens[4 * M + m], sens[5 * M + m], __int_as_float(jlo),
-                                  __int_as_float(len));
+            q0f[at(t, 0)] = sx;
+            q0f[at(t, 1)] = sy;
+            q1f[at(t, 0)] = sz;
+            q1f[at(t, 1)] = sens[3 * M + m];
+            q2f[at(t, 0)] = sens[4 * M + m];
+            q2f[at(t, 1)] = sens[5 * M + m];
+            q3i[at(t, 0)] = jlo;
+            q3i[at(t, 1)] = len;
         }
         if ((nsens & 1) && threadIdx.x == 0) {  // odd count: a partner that no ball reaches
-            s_sa[nsens] = make_float4(1e6f, 1e6f, 1e6f, 0.0f);
-            s_sb[nsens] = make_float4(0.0f, 1.0f, __int_as_float(0), __int_as_float(0));
-            s_off[nsens] = 0;
+            const int t = nsens;
+            q0f[at(t, 0)] = 1e6f;
+            q0f[at(t, 1)] = 1e6f;
+            q1f[at(t, 0)] = 1e6f;
+            q1f[at(t, 1)] = 0.0f;
+            q2f[at(t, 0)] = 0.0f;
+            q2f[at(t, 1)] = 1.0f;
+            q3i[at(t, 0)] = 0;
+            q3i[at(t, 1)] = 0;
+            qoi[t] = 0;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {  // greedy packing of sensor pairs into groups
-            int ng = 0, fill = 0;
-            s_gfirst[0] = 0;
-            for (int p = 0; p < nsens; p += 2) {
-                const int la = __float_as_int(s_sb[p].w);
-                const int lb = p + 1 < nsens ? __float_as_int(s_sb[p + 1].w) : 0;
-                if (fill + la + lb > kCap) {  // fill > 0 here, as 2 kWin <= kCap
-                    s_gfirst[++ng] = p;
-                    fill = 0;
+        if (warp == 0) {
+            // Greedy packing of sensor pairs into groups: a group takes pairs
+            // in order while their windows fit one buffer. With P the
+            // inclusive prefix sums of the pairs' lengths, the group that
+            // starts at pair g (exclusive prefix E_g) ends before the first
+            // pair p with P_p - E_g > kCap; the window of pair p starts
+            // E_p - E_g cells into its group's buffer. Lane l holds pairs l
+            // and l + 32 (at most kAdjMeta / 2 = 64 pairs).
+            static_assert(kAdjMeta <= 128, "two pairs per lane");
+            const int npairs = (nsens + 1) >> 1;
+            int la[2], w[2], P[2], E[2], gb[2] = {0, 0};
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int p = lane + 32 * hh;
+                la[hh] = p < npairs ? q3i[at(2 * p, 1)] : 0;
+                const int lb = 2 * p + 1 < nsens ? q3i[at(2 * p + 1, 1)] : 0;
+                w[hh] = p < npairs ? la[hh] + lb : 0;
+                int x = w[hh];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += t;
                 }
-                s_off[p] = fill;
-                if (p + 1 < nsens) s_off[p + 1] = fill + la;
-                fill += la + lb;
+                P[hh] = x;
             }
-            s_gfirst[++ng] = nsens;
-            s_ng = ng;
+            P[1] += __shfl_sync(0xffffffffu, P[0], 31);
+            E[0] = P[0] - w[0];
+            E[1] = P[1] - w[1];
+            int ng = 0, base = 0;
+            for (;;) {  // each pass starts a group at a later pair: at most npairs passes
+                const unsigned m0 = __ballot_sync(0xffffffffu, lane < npairs && P[0] - base > kCap);
+                const unsigned m1 =
+                    __ballot_sync(0xffffffffu, lane + 32 < npairs && P[1] - base > kCap);
+                if (!(m0 | m1)) break;
+                const int first = m0 ? __ffs(m0) - 1 : 32 + __ffs(m1) - 1;
+                base = __shfl_sync(0xffffffffu, first < 32 ? E[0] : E[1], first & 31);
+                if (lane == 0) s_gfirst[++ng] = 2 * first;
+                if (lane >= first) gb[0] = base;
+                if (lane + 32 >= first) gb[1] = base;
+            }
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int p = lane + 32 * hh;
+                if (p < npairs) {
+                    qoi[2 * p] = E[hh] - gb[hh];
+                    if (2 * p + 1 < nsens) qoi[2 * p + 1] = E[hh] - gb[hh] + la[hh];
+                }
+            }
+            if (lane == 0) {
+                s_gfirst[0] = 0;
+                s_gfirst[ng + 1] = nsens;
+                s_ng = ng + 1;
+            }
         }
         __syncthreads();
         const int ng = s_ng;
@@ -365,10 +426,9 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
         auto stage = [&](int q) {
             float* dst = sG[q & 1];
             for (int s = s_gfirst[q] + warp; s < s_gfirst[q + 1]; s += kAdjThreads / 32) {
-                const float4 sb = s_sb[s];
-                const int jlo = __float_as_int(sb.z), len = __float_as_int(sb.w);
+                const int jlo = q3i[at(s, 0)], len = q3i[at(s, 1)];
                 const float* row = G + (size_t)(mb + s) * Tk + jlo;
-                float* d = dst + s_off[s];
+                float* d = dst + qoi[s];
                 const int inrec = min(len, Tk - jlo);  // cells before the record's end
                 for (int r = lane; r < len; r += 32) {
                     if (r < inrec)
@@ -390,47 +450,48 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
             const int gbase = s_gfirst[q];
             const int cnt = s_gfirst[q + 1] - gbase;
             const int m0 = mb + gbase;
-            const float4* __restrict__ sa_g = s_sa + gbase;
-            const float4* __restrict__ sb_g = s_sb + gbase;
-            const int* __restrict__ off_g = s_off + gbase;
+            const int pbase = gbase >> 1;  // groups start at even sensors
             const float* __restrict__ sGb = sG[q & 1];
             if (!valid) continue;
             // two sensors at a time, evaluated side by side in the halves of float2
 #pragma unroll 1
             for (int s = 0; s < cnt; s += 2) {
-                const float4 saA = sa_g[s], sbA = sb_g[s], saB = sa_g[s + 1], sbB = sb_g[s + 1];
-                const float* __restrict__ sGA = sGb + off_g[s];
-                const float* __restrict__ sGB = sGb + off_g[s + 1];
+                const int pi = pbase + (s >> 1);
+                const float4 Q0 = s_q0[pi], Q1 = s_q1[pi], Q2 = s_q2[pi];
+                const int4 Q3 = s_q3[pi];
+                const int2 QO = s_qo[pi];
+                const float* __restrict__ sGA = sGb + QO.x;
+                const float* __restrict__ sGB = sGb + QO.y;
                 // dL/dp0 is continuous in the distance (the cell values are), so the
                 // p0-only pass takes it in plain float; the full gradient, whose
                 // centre and radius terms jump at the window's ends, needs the
                 // exact one
                 const PairDist2 pd =
                     P0_ONLY ? sbp_pair_distance2_f32(f2(cx), f2(cy), f2(cz),
-                                                     make_float2(saA.x, saB.x),
-                                                     make_float2(saA.y, saB.y),
-                                                     make_float2(saA.z, saB.z))
-                            : sbp_pair_distance2(f2(cx), f2(cy), f2(cz), make_float2(saA.x, saB.x),
-                                                 make_float2(saA.y, saB.y),
-                                                 make_float2(saA.z, saB.z));
+                                                     make_float2(Q0.x, Q0.y),
+                                                     make_float2(Q0.z, Q0.w),
+                                                     make_float2(Q1.x, Q1.y))
+                            : sbp_pair_distance2(f2(cx), f2(cy), f2(cz), make_float2(Q0.x, Q0.y),
+                                                 make_float2(Q0.z, Q0.w),
+                                                 make_float2(Q1.x, Q1.y));
                 PairWindow wa, wb;
                 bool okA, okB;
                 sbp_window2(pd.dh, pd.dl, f2(R), g, wa, wb, okA, okB);
                 if (!(okA || okB)) continue;
                 const float2 ux = f2mul(pd.dx, pd.rd), uy = f2mul(pd.dy, pd.rd),
                              uz = f2mul(pd.dz, pd.rd);
-                const float2 nx = make_float2(saA.w, saB.w), ny = make_float2(sbA.x, sbB.x),
-                             nz = make_float2(sbA.y, sbB.y);
+                const float2 nx = make_float2(Q1.z, Q1.w), ny = make_float2(Q2.x, Q2.y),
+                             nz = make_float2(Q2.z, Q2.w);
                 const float2 cosv = f2fma(nx, ux, f2fma(ny, uy, f2mul(nz, uz)));
                 float actA, actB;
-                float wA = sbp_weight(g.wmode, cosv.x, actA), wB = sbp_weight(g.wmode, cosv.y, actB);
+                float wA = sbp_weight(WMODE, cosv.x, actA), wB = sbp_weight(WMODE, cosv.y, actB);
                 okA = okA && !(wA == 0.0f && actA == 0.0f);
                 okB = okB && !(wB == 0.0f && actB == 0.0f);
                 if (!(okA || okB)) continue;
                 // window sums; a pair that does not count gets zeros, so that its
                 // half contributes exactly nothing below
-                const int jloA = __float_as_int(sbA.z), lenA = __float_as_int(sbA.w);
-                const int jloB = __float_as_int(sbB.z), lenB = __float_as_int(sbB.w);
+                const int jloA = Q3.x, lenA = Q3.z;
+                const int jloB = Q3.y, lenB = Q3.w;
                 float2 gf = f2(0.f), gl = f2(0.f), E0 = f2(0.f), E1 = f2(0.f);
                 // side by side when both windows are staged (cells past the
                 // record staged as zeros, so no clamps) and differ by at most one
@@ -603,12 +664,23 @@ int launch_adj(sbp_array_s* a, const FrameTable& ft, int total, int split, const
         return SBP_ERR_ARG;
     }
     const dim3 grid(chunks, split);
+    auto go = [&](auto p0_only, auto wmode) {
+        adj_group_kernel<decltype(p0_only)::value, decltype(wmode)::value>
+            <<<grid, kAdjThreads, 0, st>>>(b, ft, a->d_sens, g, G, mask, o, a->d_adj_part,
+                                           a->d_adj_ticket);
+    };
+    auto by_mode = [&](auto p0_only) {
+        if (g.wmode == SBP_W_NONE)
+            go(p0_only, std::integral_constant<int, SBP_W_NONE>{});
+        else if (g.wmode == SBP_W_COS)
+            go(p0_only, std::integral_constant<int, SBP_W_COS>{});
+        else
+            go(p0_only, std::integral_constant<int, SBP_W_CLAMP>{});
+    };
     if (mask == SBP_MASK_P0)
-        adj_group_kernel<true><<<grid, kAdjThreads, 0, st>>>(b, ft, a->d_sens, g, G, mask, o,
-                                                             a->d_adj_part, a->d_adj_ticket);
+        by_mode(std::true_type{});
     else
-        adj_group_kernel<false><<<grid, kAdjThreads, 0, st>>>(b, ft, a->d_sens, g, G, mask, o,
-                                                              a->d_adj_part, a->d_adj_ticket);
+        by_mode(std::false_type{});
     if (sbp_cuda_check(cudaGetLastError(), "adjoint: launch")) return SBP_ERR_CUDA;
     sbp_count_launches(1);
     return SBP_OK;

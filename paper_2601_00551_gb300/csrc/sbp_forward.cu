@@ -172,6 +172,7 @@ __device__ __forceinline__ int fwd_frac_bits(unsigned int pmax_bits) {
     return F < 0 ? 0 : (F > 60 ? 60 : F);
 }
 
+template <int WMODE>
 __global__ void __launch_bounds__(kGroupWarps * 32, 2)
 fwd_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, LevelGeo g,
                  int chunk, const unsigned int* __restrict__ pmax, SbpDevState* st,
@@ -280,8 +281,8 @@ fwd_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
         const float2 cosv = f2mul(
             f2fma(f2(nx), pd.dx, f2fma(f2(ny), pd.dy, f2mul(f2(nz), pd.dz))), pd.rd);
         float actA, actB;
-        const float2 w = make_float2(sbp_weight(g.wmode, cosv.x, actA),
-                                     sbp_weight(g.wmode, cosv.y, actB));
+        const float2 w = make_float2(sbp_weight(WMODE, cosv.x, actA),
+                                     sbp_weight(WMODE, cosv.y, actB));
         okA = okA && w.x != 0.0f;
         okB = okB && w.y != 0.0f;
         if (!(okA || okB)) continue;
@@ -378,6 +379,16 @@ fwd_finalize_kernel(unsigned long long* __restrict__ acc, int Tk,
 
 }  // namespace
 
+using FwdGroupKernel = void (*)(BallsDev, FrameTable, const float*, LevelGeo, int,
+                                const unsigned int*, SbpDevState*, unsigned long long*);
+
+// The accumulation kernel compiled for one orientation weight (SBP_W_*).
+static FwdGroupKernel fwd_group_for(int wmode) {
+    if (wmode == SBP_W_NONE) return fwd_group_kernel<SBP_W_NONE>;
+    if (wmode == SBP_W_COS) return fwd_group_kernel<SBP_W_COS>;
+    return fwd_group_kernel<SBP_W_CLAMP>;
+}
+
 int sbp_launch_forward(sbp_array_s* a, const BallsDev& b, const int* n_dev, int n_cap,
                        float* S, cudaStream_t st) {
     const LevelGeo g = sbp_level_geo(a, a->level);
@@ -392,7 +403,7 @@ int sbp_launch_forward(sbp_array_s* a, const BallsDev& b, const int* n_dev, int 
             chunk >>= 1;
     }
     const size_t smem = (size_t)2 * kWindow * 32 * sizeof(unsigned int);
-    if (sbp_cuda_check(cudaFuncSetAttribute(fwd_group_kernel,
+    if (sbp_cuda_check(cudaFuncSetAttribute(fwd_group_for(g.wmode),
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem),
                        "forward: smem attribute"))
@@ -405,7 +416,7 @@ int sbp_launch_forward(sbp_array_s* a, const BallsDev& b, const int* n_dev, int 
                       st>>>(b.p0, ft, &a->d_state->pmax_bits);
     if (sbp_cuda_check(cudaGetLastError(), "forward: pmax launch")) return SBP_ERR_CUDA;
     const unsigned grid = (unsigned)(((long long)n_cap + chunk - 1) / chunk * groups);
-    fwd_group_kernel<<<grid, kGroupWarps * 32, smem, st>>>(
+    fwd_group_for(g.wmode)<<<grid, kGroupWarps * 32, smem, st>>>(
         b, ft, a->d_sens, g, chunk, &a->d_state->pmax_bits, a->d_state, a->d_acc);
     if (sbp_cuda_check(cudaGetLastError(), "forward: accumulate launch")) return SBP_ERR_CUDA;
     fwd_finalize_kernel<<<g.M, kFinalizeThreads, 0, st>>>(a->d_acc, g.Tk,
@@ -424,7 +435,7 @@ int sbp_launch_forward_frames(sbp_array_s* a, const BallsDev& b, const int* n_de
     const int groups = (g.M + 31) / 32;
     if (chunk < 32 || chunk > SBP_FRAME_ALIGN || (SBP_FRAME_ALIGN % chunk)) chunk = kChunk;
     const size_t smem = (size_t)2 * kWindow * 32 * sizeof(unsigned int);
-    if (sbp_cuda_check(cudaFuncSetAttribute(fwd_group_kernel,
+    if (sbp_cuda_check(cudaFuncSetAttribute(fwd_group_for(g.wmode),
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem),
                        "forward_frames: smem attribute"))
@@ -439,7 +450,7 @@ int sbp_launch_forward_frames(sbp_array_s* a, const BallsDev& b, const int* n_de
     fwd_pmax_kernel<<<dim3(pmax_blocks, F), 256, 0, st>>>(b.p0, ft, a->d_frame_pmax);
     if (sbp_cuda_check(cudaGetLastError(), "forward_frames: pmax launch")) return SBP_ERR_CUDA;
     const unsigned grid = (unsigned)(((long long)total + chunk - 1) / chunk * groups);
-    fwd_group_kernel<<<grid, kGroupWarps * 32, smem, st>>>(b, ft, a->d_sens, g, chunk,
+    fwd_group_for(g.wmode)<<<grid, kGroupWarps * 32, smem, st>>>(b, ft, a->d_sens, g, chunk,
                                                            a->d_frame_pmax, a->d_state, a->d_acc);
     if (sbp_cuda_check(cudaGetLastError(), "forward_frames: accumulate launch"))
         return SBP_ERR_CUDA;
@@ -555,7 +566,7 @@ extern "C" int sbp_forward_static(const float* sensors_dev, int M, double c_mm_p
     int chunk = kChunk;
     while (chunk > 32 && (long long)((n_cap + chunk - 1) / chunk) * groups < 4LL * sms) chunk >>= 1;
     const size_t smem = (size_t)2 * kWindow * 32 * sizeof(unsigned int);
-    if (sbp_cuda_check(cudaFuncSetAttribute(fwd_group_kernel,
+    if (sbp_cuda_check(cudaFuncSetAttribute(fwd_group_for(g.wmode),
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem),
                        "forward_static: smem attribute"))
@@ -565,7 +576,7 @@ extern "C" int sbp_forward_static(const float* sensors_dev, int M, double c_mm_p
         b.p0, ft, &state->pmax_bits);
     if (sbp_cuda_check(cudaGetLastError(), "forward_static: pmax launch")) return SBP_ERR_CUDA;
     const unsigned grid = (unsigned)(((long long)n_cap + chunk - 1) / chunk * groups);
-    fwd_group_kernel<<<grid, kGroupWarps * 32, smem, st>>>(b, ft, sensors_dev, g, chunk,
+    fwd_group_for(g.wmode)<<<grid, kGroupWarps * 32, smem, st>>>(b, ft, sensors_dev, g, chunk,
                                                            &state->pmax_bits, state, acc);
     if (sbp_cuda_check(cudaGetLastError(), "forward_static: accumulate launch"))
         return SBP_ERR_CUDA;
