@@ -502,21 +502,18 @@ def adj_ops_per_pair(mean_R, h):
     return 156.0 + 3.0 * max(0.0, L - 1.0) + 2.0
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
-# the hot kernels at the 40 MHz level of the vessel workload, from one ncu
-# capture, valid while the kernel source is the one that was measured (its
-# SHA-256 prefix below); otherwise reported as null.
-# DRAM bytes (read + write) of one launch at the finest level, from one ncu
-# capture of the kernel (dram__bytes_read.sum + dram__bytes_write.sum). A
-# record holds only while the kernel's sources hash to the value it was
-# taken with; after any change the traffic is reported as null.
+# DRAM bytes (read + write) of one launch at the 40 MHz level of the vessel
+# workload, from one ncu capture of the kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum). A record holds only while the kernel's sources hash
+# to the value it was taken with (the SHA-256 prefix below); after any change
+# the traffic is reported as null.
 NCU_TRAFFIC = {
     "forward": {"sources": ["paper_2601_00551_gb300/csrc/sbp_forward.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "b406e1fb2be19f8e", "bytes": 5.264128e6},
+                "sha256": "944e5db08c8a91cf", "bytes": 5.261824e6},
     "adjoint": {"sources": ["paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "623a69f982ba5e9b", "bytes": 3.758848e6},
+                "sha256": "a5fbd9d94b898a70", "bytes": 3.762432e6},
 }
 
 
