@@ -132,10 +132,11 @@ def test_forward_vessel_sampled_sensors(sb):
         assert e <= TRACE_TOL, (f, e)
 
 
-def test_unsorted_cloud_multi_pass_and_direct_reads(sb):
-    """A cloud in random order: a chunk's balls span the whole volume, so the
-    forward covers each sensor's window in several passes and the adjoint
-    reads the residual directly instead of staging it."""
+def test_unsorted_cloud_long_windows(sb):
+    """A cloud in random order: a chunk's balls span the whole 20 mm cube, so
+    the forward adds most impulses past its shared-memory window straight to
+    the global accumulators, and the adjoint stages windows of up to ~930
+    cells at 40 MHz, a few sensors per group (many groups per CTA)."""
     wl = workloads.vessel(n_init=20000, n_truth=2000, sort=False)
     b = wl.init.stack()
     arr = make_array(sb, wl, wl.levels, b.shape[1])
@@ -595,6 +596,50 @@ def test_adjoint_windows_crossing_the_record_end(sb, sort):
         Tk = -(-560 // f)
         h = wl.c * dt_of(wl, f)
         assert np.mean((d + b[3][:, None]) / h > Tk) > 0.05  # the case is real
+        arr.set_sampling_level(k)
+        G = rng.normal(size=(wl.sensors.M, Tk)).astype(np.float32)
+        Gd = torch.from_numpy(G).cuda()
+        ref = oracle.adjoint(b, wl.sensors.pos, wl.sensors.normal, wl.c, dt_of(wl, f), Tk,
+                             G.astype(np.float64), threads=threads())
+        g = arr.adjoint(balls, Gd).cpu().numpy()
+        for c in range(5):
+            assert rel_l2(g[c], ref[c]) <= GRAD_TOL, (f, c)
+        gp = arr.adjoint(balls, Gd, mask=sb.MASK_P0).cpu().numpy()
+        assert np.all(gp[:4] == 0)
+        assert rel_l2(gp[4], ref[4]) <= GRAD_TOL, f
+
+
+def test_adjoint_unstaged_windows_read_directly(sb):
+    """Windows too long to stage next to staged ones in the same CTA: the
+    unsorted tiny cloud (a chunk spans the 4 mm cube) sampled at 400 MHz
+    reaches 1400-1930 cells of each sensor per chunk, on both sides of the
+    1792 cells a staging buffer holds for one window (1024 in the p0-only
+    pass, where none is staged). Unstaged windows are read from the global
+    row and take no room in a group, so groups mix them with staged ones.
+    Full and p0-only gradients against the oracle at 400 MHz and at 200 MHz,
+    where every window of the full pass is staged."""
+    import dataclasses
+
+    wl = dataclasses.replace(workloads.tiny(n_init=768, M=32, T=6400), fs_mhz=400.0)
+    b = wl.init.stack()
+    n = b.shape[1]
+    h = wl.c / wl.fs_mhz
+    spans = []
+    for c0 in range(0, n, 128):  # the reach of each 128-ball chunk, in cells
+        ch = b[:, c0:c0 + 128]
+        lo, hi = ch[:3].min(axis=1), ch[:3].max(axis=1)
+        near = np.linalg.norm(np.maximum(np.maximum(lo - wl.sensors.pos, wl.sensors.pos - hi),
+                                         0.0), axis=1)
+        far = np.linalg.norm(np.maximum(np.abs(wl.sensors.pos - lo), np.abs(wl.sensors.pos - hi)),
+                             axis=1)
+        spans.append((far - near + 2.0 * ch[3].max()) / h)
+    spans = np.concatenate(spans)
+    assert 0.2 < np.mean(spans > 1792) < 0.8  # the case is real
+    arr = make_array(sb, wl, (2, 1), n)
+    balls = torch.from_numpy(b).cuda()
+    rng = np.random.default_rng(21)
+    for k, f in enumerate((2, 1)):
+        Tk = 6400 // f
         arr.set_sampling_level(k)
         G = rng.normal(size=(wl.sensors.M, Tk)).astype(np.float32)
         Gd = torch.from_numpy(G).cuda()
