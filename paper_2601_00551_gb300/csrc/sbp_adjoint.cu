@@ -234,7 +234,8 @@ __device__ __forceinline__ void adj_window_sums(const float* __restrict__ sGrow,
 }
 
 // P0_ONLY: only dL/dp0 is wanted (the zero-gradient pass), so the chain rule
-// for R and the centre is skipped.
+// for R and the centre is skipped. WMODE: the orientation weight (SBP_W_*),
+// fixed at compile time so that no pair branches on it.
 // gridDim.y CTAs share a chunk, each taking 1/gridDim.y of the sensors.
 template <bool P0_ONLY, int WMODE>
 __global__ void __launch_bounds__(kAdjThreads, P0_ONLY ? 8 : 6)
@@ -242,8 +243,7 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
                  const float* __restrict__ G_all, unsigned mask, GradOut out,
                  float* __restrict__ part_all, unsigned int* __restrict__ tickets) {
     // two staging buffers of kCap cells, each holding the windows of one
-    // group of sensors packed one after another; after the last group the
-    // first one holds this CTA's partial sums
+    // group of sensors packed one after another
     constexpr int kCap = P0_ONLY ? kAdjCapP0 : kAdjCap;
     constexpr int kWin = kCap / 2;  // longest window staged: a pair of them fills a buffer
     __shared__ __align__(16) float sG[2][kCap];
@@ -265,8 +265,6 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     __shared__ int s_ng;
     __shared__ float s_red[(kAdjThreads / 32) * 7];
     __shared__ float s_box[7];
-    float* const s_part = sG[0];  // this CTA's partial sums, [ball][5]
-    static_assert(kAdjThreads * 5 <= kCap, "partials do not fit");
     static_assert(2 * kWin <= kCap, "a pair of staged windows must fit one buffer");
     const int c0 = blockIdx.x * kAdjThreads;
     const FrameSlot fs = sbp_frame_of(ft, c0);

@@ -172,6 +172,8 @@ __device__ __forceinline__ int fwd_frac_bits(unsigned int pmax_bits) {
     return F < 0 ? 0 : (F > 60 ? 60 : F);
 }
 
+// WMODE: the orientation weight (SBP_W_*), fixed at compile time so that no
+// pair branches on it; fwd_group_for picks the instance.
 template <int WMODE>
 __global__ void __launch_bounds__(kGroupWarps * 32, 2)
 fwd_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, LevelGeo g,
