@@ -510,10 +510,10 @@ def adj_ops_per_pair(mean_R, h):
 NCU_TRAFFIC = {
     "forward": {"sources": ["paper_2601_00551_gb300/csrc/sbp_forward.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "7dedb623f00fb6dd", "bytes": 5.261824e6},
+                "sha256": "492ec1fc8c88f6a4", "bytes": 5.261824e6},
     "adjoint": {"sources": ["paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "80ee295b26077fde", "bytes": 3.762432e6},
+                "sha256": "772b91a283843ec6", "bytes": 3.762432e6},
 }
 
 

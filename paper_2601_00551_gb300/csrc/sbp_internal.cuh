@@ -131,7 +131,7 @@ struct sbp_array_s {
     unsigned long long* d_gacc;
     size_t gauss_cells;
     int fwd_chunk_frames;  // forward balls per CTA chosen by sbp_autotune_frames (0: default)
-    int adj_split_frames;  // adjoint CTAs per cluster chosen by sbp_autotune_frames (0: default)
+    int adj_split_frames;  // adjoint CTAs per ball chunk chosen by sbp_autotune_frames (0: default)
     // single-cloud tiles per level chosen by sbp_autotune (0: default)
     int fwd_chunk_lvl[SBP_MAX_LEVELS];
     int adj_split_lvl[SBP_MAX_LEVELS];
