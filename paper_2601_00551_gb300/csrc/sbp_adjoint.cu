@@ -56,7 +56,7 @@ namespace {
 constexpr int kAdjThreads = SBP_ADJ_CHUNK;  // balls (threads) per adjoint CTA
 constexpr int kAdjSplit = 8;      // default CTAs per chunk, each taking 1/split of the sensors
 constexpr int kAdjCap = 3584;     // cells per staging buffer (two buffers per CTA)
-constexpr int kAdjCapP0 = 2048;   // the same for the p0-only adjoint, which keeps more CTAs per SM
+constexpr int kAdjCapP0 = 1792;   // the same for the p0-only adjoint, which keeps more CTAs per SM
 constexpr int kAdjShare = 16;     // a CTA's share of the sensors is a multiple of this
 constexpr int kAdjMeta = 128;     // sensors whose set-up is held in shared memory at once
 
@@ -238,7 +238,7 @@ __device__ __forceinline__ void adj_window_sums(const float* __restrict__ sGrow,
 // fixed at compile time so that no pair branches on it.
 // gridDim.y CTAs share a chunk, each taking 1/gridDim.y of the sensors.
 template <bool P0_ONLY, int WMODE>
-__global__ void __launch_bounds__(kAdjThreads, P0_ONLY ? 8 : 6)
+__global__ void __launch_bounds__(kAdjThreads, P0_ONLY ? 10 : 6)
 adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, LevelGeo g,
                  const float* __restrict__ G_all, unsigned mask, GradOut out,
                  float* __restrict__ part_all, unsigned int* __restrict__ tickets) {
