@@ -513,7 +513,7 @@ NCU_TRAFFIC = {
                 "sha256": "492ec1fc8c88f6a4", "bytes": 5.261824e6},
     "adjoint": {"sources": ["paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "d1c95f0501288365", "bytes": 3.762432e6},
+                "sha256": "0fa46a80c8fb55ce", "bytes": 3.762432e6},
 }
 
 

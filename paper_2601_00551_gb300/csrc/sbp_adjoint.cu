@@ -391,7 +391,7 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
             P[1] += __shfl_sync(0xffffffffu, P[0], 31);
             E[0] = P[0] - w[0];
             E[1] = P[1] - w[1];
-            int ng = 0, base = 0;
+            int ng = 0, base = 0;  // ng: groups started so far, kept by lane 0 (which writes them)
             for (;;) {  // each pass starts a group at a later pair: at most npairs passes
                 const unsigned m0 = __ballot_sync(0xffffffffu, lane < npairs && P[0] - base > kCap);
                 const unsigned m1 =
