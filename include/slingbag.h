@@ -18,7 +18,9 @@
  *  - The current number of balls lives in DEVICE memory (`n_dev`, int32), so
  *    that growth can change it without a host round trip; every kernel reads
  *    it and the grid is sized from `n_cap`. Passing n_dev = NULL means
- *    "n = n_cap".
+ *    "n = n_cap". Balls at and past the live count are ignored, and per-ball
+ *    outputs (gradients, Adam moments) are written for the live balls only:
+ *    entries past the live count are left as they were.
  *  - Traces are float32 row-major [M][T_k] device arrays owned by the caller.
  *  - All work is enqueued on `stream` (a cudaStream_t passed as void*; NULL
  *    is the legacy default stream); calls do not synchronise unless stated.

@@ -651,3 +651,25 @@ def test_adjoint_unstaged_windows_read_directly(sb):
         gp = arr.adjoint(balls, Gd, mask=sb.MASK_P0).cpu().numpy()
         assert np.all(gp[:4] == 0)
         assert rel_l2(gp[4], ref[4]) <= GRAD_TOL, f
+
+
+def test_adjoint_ragged_live_count(sb):
+    """A live count below the capacity: the gradients of the live balls equal
+    those of the truncated cloud, and the entries past the live count are
+    left as they were (for the full and the p0-only kernels)."""
+    wl = workloads.tiny(n_init=1000, M=16, T=600)
+    b = wl.init.stack()
+    cap = b.shape[1]
+    arr = make_array(sb, wl, (1,), cap)
+    balls = torch.from_numpy(b).cuda()
+    rng = np.random.default_rng(31)
+    G = torch.from_numpy(rng.normal(size=(wl.sensors.M, 600)).astype(np.float32)).cuda()
+    for mask in (sb.MASK_ALL, sb.MASK_P0):
+        for n in (1, 129, 700):
+            junk = balls.clone()
+            junk[:, n:] = torch.from_numpy(rng.normal(size=(5, cap - n)).astype(np.float32)).cuda()
+            sentinel = torch.full((5, cap), 7.0, device="cuda")
+            g = arr.adjoint(junk, G, n=n, mask=mask, out=sentinel).cpu().numpy()
+            assert np.all(g[:, n:] == 7.0), (mask, n)
+            ref = arr.adjoint(balls[:, :n].contiguous(), G, mask=mask).cpu().numpy()
+            np.testing.assert_array_equal(g[:, :n], ref, err_msg=f"{mask} {n}")
