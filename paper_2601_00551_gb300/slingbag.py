@@ -87,6 +87,9 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_double)]),
     "sbp_set_sampling_level": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "sbp_forward": (ctypes.c_int, [_P, _Balls, _P, ctypes.c_int, _P, ctypes.c_uint, _P]),
+    "sbp_forward_static": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_int, ctypes.c_int, _Balls, _P, ctypes.c_int,
+                                          _P, _P]),
     "sbp_residual": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "sbp_adjoint": (ctypes.c_int, [_P, _Balls, _P, ctypes.c_int, _P, _Balls, ctypes.c_uint, _P]),
     "sbp_filter_grow": (ctypes.c_int, [_P, _Balls, _Balls, ctypes.POINTER(_P), ctypes.c_int, _P,
@@ -629,6 +632,31 @@ class SensorArray:
         _check("sbp_get_inside_pairs", self._lib.sbp_get_inside_pairs(self._h, _stream(),
                                                                        ctypes.byref(c)))
         return c.value
+
+
+def forward_static(sensors: torch.Tensor, c: float, dt_us: float, T_k: int,
+                   balls: torch.Tensor, n: torch.Tensor | None = None,
+                   out: torch.Tensor | None = None, weight_mode: str = "clamp") -> torch.Tensor:
+    """Traces S (M, T_k) without an array object (sbp_forward_static): the
+    library allocates nothing, so the call may sit in a stream capture.
+    sensors: (6, M) float32 CUDA tensor, positions then unit normals; balls:
+    (5, N); n: None (all N balls) or an int32 CUDA tensor holding the live
+    count; M * T_k must stay within the library's static scratch (2^21 cells)."""
+    if sensors.dim() != 2 or sensors.shape[0] != 6 or sensors.dtype != torch.float32 or \
+            not sensors.is_cuda or not sensors.is_contiguous():
+        raise ValueError("sensors must be a contiguous (6, M) float32 CUDA tensor")
+    M = sensors.shape[1]
+    if out is None:
+        out = torch.empty((M, int(T_k)), dtype=torch.float32, device=sensors.device)
+    if out.shape != (M, int(T_k)) or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous ({M}, {T_k}) float32 tensor")
+    if n is not None and (n.dtype != torch.int32 or not n.is_cuda):
+        raise ValueError("n must be an int32 CUDA tensor")
+    lib = load_library()
+    _check("sbp_forward_static", lib.sbp_forward_static(
+        _dptr(sensors), M, float(c), float(dt_us), int(T_k), W_MODES[weight_mode], _rows(balls),
+        _dptr(n), balls.shape[1], _dptr(out), _stream()))
+    return out
 
 
 class _Radiator(torch.autograd.Function):

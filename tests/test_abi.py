@@ -39,6 +39,30 @@ def test_library_exports_every_declared_symbol(lib):
     assert not missing, missing
 
 
+def declared_parameter_counts():
+    counts = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for name, params in re.findall(r"\b(sbp_\w+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
+            p = params.strip()
+            counts[name] = 0 if p in ("", "void") else len(p.split(","))
+    return counts
+
+
+def test_python_binding_covers_every_entry_point_with_its_arity():
+    """The binding is argument marshalling only: one ctypes signature per
+    declared entry point, with the header's number of parameters."""
+    from paper_2601_00551_gb300 import slingbag
+
+    counts = declared_parameter_counts()
+    assert set(counts) == declared_symbols()
+    missing = sorted(set(counts) - set(slingbag._SIGS))
+    assert not missing, missing
+    wrong = {n: (counts[n], len(slingbag._SIGS[n][1])) for n in counts
+             if len(slingbag._SIGS[n][1]) != counts[n]}
+    assert not wrong, wrong
+
+
 def test_version_and_error_string_without_gpu(lib):
     lib.sbp_version.restype = ctypes.c_char_p
     lib.sbp_last_error.restype = ctypes.c_char_p

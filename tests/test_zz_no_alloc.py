@@ -4,7 +4,6 @@ its buffers), against the regular sbp_forward through the C ABI.
 
 Collected last on purpose: it uses the library's one static scratch array,
 and the rest of the suite has already run if it fails."""
-import ctypes
 
 import numpy as np
 import pytest
@@ -26,12 +25,7 @@ def sb():
 
     assert torch.cuda.is_available()
     torch.cuda.set_device(0)
-    lib = slingbag.load_library()
-    lib.sbp_forward_static.restype = ctypes.c_int
-    lib.sbp_forward_static.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
-                                       ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                                       slingbag._Balls, ctypes.c_void_p, ctypes.c_int,
-                                       ctypes.c_void_p, ctypes.c_void_p]
+    slingbag.load_library()
     return slingbag
 
 
@@ -55,23 +49,19 @@ def test_static_forward_matches_regular_forward_twice(sb):
                          n_cap=n)
     balls = torch.from_numpy(b).cuda()
     sens = torch.from_numpy(sensors_6xM(wl.sensors.pos, wl.sensors.normal)).cuda()
-    lib = sb.load_library()
-    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     for k, f in enumerate((4, 1)):
         arr.set_sampling_level(k)
         ref = arr.forward(balls).cpu().numpy()
         Tk = wl.T // f
         for _ in range(2):  # two calls in a row share (and clear) the static scratch
             out = torch.full((wl.sensors.M, Tk), float("nan"), device="cuda")
-            rc = lib.sbp_forward_static(sens.data_ptr(), wl.sensors.M, wl.c, f / wl.fs_mhz, Tk,
-                                        0, sb._rows(balls), None, n, out.data_ptr(), stream)
-            assert rc == 0, lib.sbp_last_error().decode()
-            got = out.cpu().numpy()
+            got = sb.forward_static(sens, wl.c, f / wl.fs_mhz, Tk, balls, out=out).cpu().numpy()
             assert np.all(np.isfinite(got))
             assert rel_l2(got, ref) <= TRACE_TOL
 
 
 def test_static_forward_rejects_sizes_beyond_its_scratch(sb):
+    """Through the C ABI directly: the error code and message."""
     lib = sb.load_library()
     dummy = torch.zeros((5, 4), device="cuda")
     sens = torch.zeros((6, 1024), device="cuda")
