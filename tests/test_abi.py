@@ -132,3 +132,18 @@ def test_tile_entry_points_reject_a_null_array_on_the_host(lib):
     assert (c.value, s.value) == (7, 7)  # untouched
     lib.sbp_last_error.restype = ctypes.c_char_p
     assert b"null array" in lib.sbp_last_error()
+
+
+def test_forward_static_binding_checks_its_arguments_on_the_host():
+    """Shapes, dtypes and devices are checked before the library is called."""
+    import torch
+
+    from paper_2601_00551_gb300 import slingbag
+
+    balls = torch.zeros((5, 4))
+    on_host = torch.zeros((6, 4))
+    three_rows = torch.zeros((3, 4))
+    doubles = torch.zeros((6, 4), dtype=torch.float64)
+    for sensors in (on_host, three_rows, doubles):
+        with pytest.raises(ValueError):
+            slingbag.forward_static(sensors, 1.5, 0.025, 16, balls)
