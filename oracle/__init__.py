@@ -427,9 +427,10 @@ def reconstruct(balls, pos, normal, c, fs_mhz, T, factors, y_full, stages,
     (Section 4.2), then for each stage `iterations` times: simulate at the
     stage's sampling level (Section 4.3), L = ||S - y_k||^2, backpropagate,
     one Adam step on the stage's components, then filter/grow (destroy,
-    split, and duplicate in the fine stage; Section 4.1). The cloud is stored
-    in float32 between steps, like the measured cloud it stands for; all
-    arithmetic is float64. Returns (balls (5, n) float32, losses, counts)
+    split, and duplicate in the fine stage; Section 4.1). The cloud, the Adam
+    moments and the residual handed to the backpropagation are stored in
+    float32 between steps, the precision of the arrays that carry the
+    method's state; all arithmetic is float64. Returns (balls (5, n) float32, losses, counts)
     where counts[t] is the ball count entering iteration t."""
     ap = adam_params or AdamParams()
     gpar = grow_params or GrowParams()
