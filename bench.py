@@ -3,16 +3,16 @@
 
 Metric: ball x sensor pairs per second through forward + adjoint.
 
-One step is one pass of the whole hot path over the vessel workload (a
-seeded vessel-tree phantom measured by 512 sensors on an ellipsoidal cap;
-an initial cloud of 200,000 uniform random balls; levels 10 / 20 / 40 MHz
-with T = 1024 / 2048 / 4096):
+One step is one pass of the whole hot path over the large workload (a
+seeded 1M-ball vessel-tree phantom in a 40 mm cube measured by 1024 sensors
+on a (60, 60, 40) mm ellipsoidal cap; an initial cloud of 1M uniform random
+balls; levels 20 / 40 / 80 MHz with T = 2048 / 4096 / 8192):
   restore the initial cloud;
-  zero-gradient filtering at 10 MHz (residual with S = 0, p0 adjoint,
-    compaction);
+  zero-gradient filtering at the coarsest level (residual with S = 0, p0
+    adjoint, compaction);
   one iteration at each level: downsample the measured traces, forward,
     residual and loss, adjoint, Adam, filter/grow (coarse stage p0/R at
-    10 MHz, fine stage at 20 and 40 MHz with duplication at 40 MHz).
+    the coarsest level, fine stage above it, duplication at the finest).
 The pairs of a step are sum over the three iterations of n_k x M, with n_k
 the live ball count entering iteration k (the zero-gradient pass is extra
 work and is not counted). L2 is flushed (a 512 MB write) before every timed
@@ -22,7 +22,11 @@ in the same order; `eager` gives the same step launched call by call, and
 the per-kernel times and the roofline come from that eager pass);
 `e2e` times the same step through sbp_reconstruct with the cloud and the
 measured traces copied from pinned host memory and the result copied back
-inside the timed region.
+inside the timed region. `--workload vessel` (200k balls x 512 sensors,
+10 / 20 / 40 MHz) or `tiny` time that workload's step instead; after the
+large step the default run also times the vessel step (`vessel_step`) and
+the schedule, learned-proposal, batched-frames, autograd-memory, Gaussian
+and envelope measurements.
 
 N > 1 (torchrun): every rank runs an independent replica of the workload on
 its own GPU (the problem has no exchange step); value = all ranks' pairs /
@@ -59,7 +63,10 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="vessel", choices=["vessel", "tiny"])
+    ap.add_argument("--workload", default="large", choices=["large", "vessel", "tiny"],
+                    help="the step's workload (default: 1M balls x 1024 sensors at 20/40/80 "
+                         "MHz; the vessel workload's step and the schedule, learned-proposal, "
+                         "frames and envelope measurements run after it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -77,8 +84,9 @@ def parse_args(argv=None):
                          "several minutes)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned initial proposal (CNN training and comparison)")
-    ap.add_argument("--no-large", action="store_true",
-                    help="skip the 1M-ball x 1024-sensor configuration")
+    ap.add_argument("--large-calls", action="store_true",
+                    help="only time one forward and one adjoint call of the 1M-ball initial "
+                         "cloud per level, default and tuned tiles")
     ap.add_argument("--no-envelope", action="store_true",
                     help="skip the envelope / initialisation / voxel grid timing")
     ap.add_argument("--no-autotune", action="store_true",
@@ -210,7 +218,7 @@ def measured_peaks():
 def make_workload(name):
     import workloads
 
-    return workloads.vessel() if name == "vessel" else workloads.tiny()
+    return {"large": workloads.large, "vessel": workloads.vessel, "tiny": workloads.tiny}[name]()
 
 
 def stages_for(sb, wl):
@@ -228,133 +236,163 @@ def stages_for(sb, wl):
 GROW = dict(p_min=1e-3, R_min=0.02, R_max=0.3, g_dup=5.0)
 
 
-def run_native(args, rank, world, local):
+class StepContext:
+    """Device state of one workload for the step measurement: the sensor
+    array, the measured traces (the phantom rendered at the finest level by
+    the library's forward, plus 1% noise), the initial cloud and every
+    buffer the step writes."""
+
+    def __init__(self, sb, wl, dev, n_cap_factor=2):
+        import torch
+
+        import workloads
+
+        self.wl = wl
+        self.M = wl.sensors.M
+        self.n0 = wl.init.n
+        self.n_cap = n_cap_factor * self.n0
+        self.nl = len(wl.levels)
+        self.arr = sb.SensorArray(wl.sensors.pos, wl.sensors.normal, wl.c, wl.fs_mhz, wl.T,
+                                  wl.levels, n_cap=self.n_cap)
+        arr, M, nl, n_cap = self.arr, self.M, self.nl, self.n_cap
+        truth = torch.from_numpy(wl.truth.stack()).to(dev)
+        arr.set_sampling_level(nl - 1)
+        y_clean = arr.forward(truth).cpu().numpy()
+        del truth
+        self.y_host = workloads.add_noise(y_clean)
+        self.y_full = torch.from_numpy(self.y_host).to(dev)
+        self.init = torch.zeros((5, n_cap), dtype=torch.float32, device=dev)
+        self.init[:, :self.n0] = torch.from_numpy(wl.init.stack()).to(dev)
+        self.n_init = torch.tensor([self.n0], dtype=torch.int32, device=dev)
+        self.balls = torch.empty_like(self.init)
+        self.n_dev = torch.empty_like(self.n_init)
+        self.grads = torch.zeros((5, n_cap), dtype=torch.float32, device=dev)
+        self.mom = torch.zeros((10, n_cap), dtype=torch.float32, device=dev)
+        self.mom0 = torch.zeros_like(self.mom)
+        self.yk = {k: torch.empty((M, arr.level_info(k)[0]), dtype=torch.float32, device=dev)
+                   for k in range(nl)}
+        self.S = {k: torch.empty_like(self.yk[k]) for k in range(nl)}
+        self.G = {k: torch.empty_like(self.yk[k]) for k in range(nl)}
+        self.loss = torch.zeros(nl, dtype=torch.float64, device=dev)
+        self.n_log = torch.zeros(nl, dtype=torch.int32, device=dev)
+        self.R_log = None
+        self.stages = stages_for(sb, wl)
+        self.adam = sb.AdamParams()
+        self.ev = {name: [] for name in ("fwd", "adj", "zero")}
+
+    def step(self, sb, record=False, keep_R=False):
+        """One pass of the hot path: restore the initial cloud, zero-gradient
+        filtering at the coarsest level, then one iteration per level
+        (forward, residual, adjoint, Adam, filter/grow)."""
+        import torch
+
+        arr, stream = self.arr, torch.cuda.current_stream()
+        self.balls.copy_(self.init)
+        self.n_dev.copy_(self.n_init)
+        self.mom.copy_(self.mom0)
+
+        def mark():
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            return e
+
+        zl = 0
+        arr.set_sampling_level(zl, self.y_full, out=self.yk[zl])
+        arr.residual(None, self.yk[zl], G=self.G[zl], want_loss=False)
+        z0 = mark() if record else None
+        arr.adjoint(self.balls, self.G[zl], n=self.n_dev, mask=sb.MASK_P0, out=self.grads)
+        if record:
+            self.ev["zero"].append((zl, z0, mark()))
+        arr.filter_grow(self.balls, self.grads, self.n_dev, mode=sb.KEEP_NEG, extra=[self.mom])
+        for t, st in enumerate(self.stages, start=1):
+            k = st.level
+            arr.set_sampling_level(k, self.y_full, out=self.yk[k])
+            self.n_log[t - 1:t].copy_(self.n_dev)
+            if keep_R:
+                self.R_log[k] = self.balls[3].clone()
+            e0 = mark() if record else None
+            arr.forward(self.balls, n=self.n_dev, out=self.S[k])
+            e1 = mark() if record else None
+            arr.residual(self.S[k], self.yk[k], G=self.G[k], loss=self.loss[t - 1:t])
+            e2 = mark() if record else None
+            arr.adjoint(self.balls, self.G[k], n=self.n_dev, mask=st.grad_mask, out=self.grads)
+            if record:
+                e3 = mark()
+                self.ev["fwd"].append((k, e0, e1))
+                self.ev["adj"].append((k, e2, e3))
+            arr.adam_step(self.balls, self.grads, self.mom[:5], self.mom[5:], t, self.adam,
+                          n=self.n_dev, mask=st.grad_mask)
+            gp = sb.GrowParams(seed=1000 + t, grad_mask=st.grad_mask, duplicate=st.duplicate,
+                               **GROW)
+            arr.filter_grow(self.balls, self.grads, self.n_dev, mode=sb.GROW, grow=gp,
+                            extra=[self.mom])
+
+    def level_mean_R(self, sb, counts):
+        """Mean radius of the live cloud entering each level's iteration
+        (one untimed step)."""
+        import torch
+
+        self.R_log = {}
+        self.step(sb, keep_R=True)
+        torch.cuda.synchronize()
+        out = {k: float(self.R_log[k][:int(counts[k])].double().mean().item())
+               for k in range(self.nl)}
+        self.R_log = None
+        return out
+
+    def close(self):
+        self.arr.close()
+
+
+def measure_step(args, sb, ctx, local, tune=True, graph=True, clocks=True):
+    """Times K steps of `ctx`'s workload (after W warm-up steps), eager and
+    replayed from a CUDA graph captured once, with an L2 flush before every
+    timed step; per-call device times of the hot kernels come from the eager
+    pass. Returns the measurement and the clock record."""
     import torch
 
-    import __graft_entry__ as ge
-
-    ge.build()
-    from paper_2601_00551_gb300 import slingbag as sb
-
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    wl = make_workload(args.workload)
-    M = wl.sensors.M
-    n0 = wl.init.n
-    n_cap = 2 * n0
-    arr = sb.SensorArray(wl.sensors.pos, wl.sensors.normal, wl.c, wl.fs_mhz, wl.T, wl.levels,
-                         n_cap=n_cap)
-    nl = len(wl.levels)
-
-    # measured traces: the phantom rendered at the finest level plus 1% noise
-    import workloads
-
-    truth = torch.from_numpy(wl.truth.stack()).to(dev)
-    arr.set_sampling_level(nl - 1)
-    y_clean = arr.forward(truth).cpu().numpy()
-    y_host = workloads.add_noise(y_clean)
-    y_full = torch.from_numpy(y_host).to(dev)
-    del truth
-
-    init = torch.zeros((5, n_cap), dtype=torch.float32, device=dev)
-    init[:, :n0] = torch.from_numpy(wl.init.stack()).to(dev)
-    n_init = torch.tensor([n0], dtype=torch.int32, device=dev)
-    balls = torch.empty_like(init)
-    n_dev = torch.empty_like(n_init)
-    grads = torch.zeros((5, n_cap), dtype=torch.float32, device=dev)
-    mom = torch.zeros((10, n_cap), dtype=torch.float32, device=dev)
-    mom0 = torch.zeros_like(mom)
-    yk = {k: torch.empty((M, arr.level_info(k)[0]), dtype=torch.float32, device=dev)
-          for k in range(nl)}
-    S = {k: torch.empty_like(yk[k]) for k in range(nl)}
-    G = {k: torch.empty_like(yk[k]) for k in range(nl)}
-    loss = torch.zeros(nl, dtype=torch.float64, device=dev)
-    n_log = torch.zeros(nl, dtype=torch.int32, device=dev)
-    stages = stages_for(sb, wl)
-    adam = sb.AdamParams()
+    wl, arr, M, nl = ctx.wl, ctx.arr, ctx.M, ctx.nl
+    dev = ctx.init.device
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    ev = {name: [] for name in ("fwd", "adj", "zero")}
-
-    def step(record):
-        balls.copy_(init)
-        n_dev.copy_(n_init)
-        mom.copy_(mom0)
-        zl = 0
-        arr.set_sampling_level(zl, y_full, out=yk[zl])
-        arr.residual(None, yk[zl], G=G[zl], want_loss=False)
-        if record:
-            z0 = torch.cuda.Event(enable_timing=True)
-            z0.record(stream)
-        arr.adjoint(balls, G[zl], n=n_dev, mask=sb.MASK_P0, out=grads)
-        if record:
-            z1 = torch.cuda.Event(enable_timing=True)
-            z1.record(stream)
-            ev["zero"].append((zl, z0, z1))
-        arr.filter_grow(balls, grads, n_dev, mode=sb.KEEP_NEG, extra=[mom])
-        for t, st in enumerate(stages, start=1):
-            k = st.level
-            arr.set_sampling_level(k, y_full, out=yk[k])
-            n_log[t - 1:t].copy_(n_dev)
-            if record:
-                e0 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-            arr.forward(balls, n=n_dev, out=S[k])
-            if record:
-                e1 = torch.cuda.Event(enable_timing=True)
-                e1.record(stream)
-            arr.residual(S[k], yk[k], G=G[k], loss=loss[t - 1:t])
-            if record:
-                e2 = torch.cuda.Event(enable_timing=True)
-                e2.record(stream)
-            arr.adjoint(balls, G[k], n=n_dev, mask=st.grad_mask, out=grads)
-            if record:
-                e3 = torch.cuda.Event(enable_timing=True)
-                e3.record(stream)
-                ev["fwd"].append((k, e0, e1))
-                ev["adj"].append((k, e2, e3))
-            arr.adam_step(balls, grads, mom[:5], mom[5:], t, adam, n=n_dev, mask=st.grad_mask)
-            gp = sb.GrowParams(seed=1000 + t, grad_mask=st.grad_mask, duplicate=st.duplicate,
-                               **GROW)
-            arr.filter_grow(balls, grads, n_dev, mode=sb.GROW, grow=gp, extra=[mom])
-
-    # tiles per level, tuned (untimed) on the initial cloud
     tiles = {}
-    if not args.no_autotune:
+    if tune:  # tiles per level, tuned (untimed) on the initial cloud
         for k in range(nl):
             arr.set_sampling_level(k)
-            tiles[k] = arr.autotune(init, n=n_init)
+            tiles[k] = arr.autotune(ctx.init, n=ctx.n_init)
 
     # warm-up; the workload is deterministic, so every step sees the same counts
     for _ in range(max(0, args.warmup)):
-        step(False)
+        ctx.step(sb)
     torch.cuda.synchronize()
-    counts = n_log.cpu().numpy().astype(np.int64)
+    counts = ctx.n_log.cpu().numpy().astype(np.int64)
     pairs_per_step = float(counts.sum()) * M
     if arr.sync_status() != 0:
         raise RuntimeError("device status latched during warm-up: " + sb.load_library()
                            .sbp_last_error().decode())
+    mean_R = ctx.level_mean_R(sb, counts)
 
-    clocks = ClockSampler(local, enabled=not (args.no_clocks or args.profile))
+    sampler = ClockSampler(local, enabled=clocks)
     barrier()
     torch.cuda.synchronize()
     launches0 = sb.launch_count()
+    for v in ctx.ev.values():
+        v.clear()
     times = []
     for _ in range(args.steps):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        step(True)
+        ctx.step(sb, record=True)
         b.record(stream)
         times.append((a, b))
     torch.cuda.synchronize()
     barrier()
     launches = sb.launch_count() - launches0
-    step_ms = [a.elapsed_time(b) for a, b in times]
-    total_s = sum(step_ms) / 1e3
-    if not np.array_equal(n_log.cpu().numpy(), counts):
+    total_s = sum(a.elapsed_time(b) for a, b in times) / 1e3
+    if not np.array_equal(ctx.n_log.cpu().numpy(), counts):
         raise RuntimeError("ball counts changed between steps; the step is not reproducible")
     if arr.sync_status() != 0:
         raise RuntimeError("device status latched during the timed steps")
@@ -363,13 +401,13 @@ def run_native(args, rank, world, local):
 
     # the same step replayed from a CUDA graph (one launch per step from the
     # host; the kernels and their order are unchanged)
-    graph = None
-    if not args.profile:
+    replay = None
+    if graph:
         try:
             g = torch.cuda.CUDAGraph()
             torch.cuda.synchronize()
             with torch.cuda.graph(g):
-                step(False)
+                ctx.step(sb)
             gt = []
             for it in range(max(3, args.warmup) + args.steps):
                 flush.zero_()
@@ -381,43 +419,39 @@ def run_native(args, rank, world, local):
                 if it >= max(3, args.warmup):
                     gt.append((a, b))
             torch.cuda.synchronize()
-            if not np.array_equal(n_log.cpu().numpy(), counts) or arr.sync_status() != 0:
+            if not np.array_equal(ctx.n_log.cpu().numpy(), counts) or arr.sync_status() != 0:
                 raise RuntimeError("graph replay changed the step's ball counts")
-            g_ms = statistics.mean(a.elapsed_time(b) for a, b in gt)
-            g_max_s, _ = aggregate(g_ms * 1e-3 * args.steps, pairs_per_step * args.steps)
-            graph = {"ms_per_step": g_max_s * 1e3 / args.steps,
-                     "value": all_pairs / g_max_s}
+            g_s = sum(a.elapsed_time(b) for a, b in gt) / 1e3
+            g_max_s, _ = aggregate(g_s, pairs_per_step * args.steps)
+            replay = {"ms_per_step": g_max_s * 1e3 / args.steps, "value": all_pairs / g_max_s}
             del g
         except Exception as exc:  # the eager measurement stands on its own
-            graph = {"error": f"{type(exc).__name__}: {exc}"}
-    clk = clocks.stop()
+            replay = {"error": f"{type(exc).__name__}: {exc}"}
+    clk = sampler.stop()
     eager = {"ms_per_step": max_s * 1e3 / args.steps, "value": value}
     launch_mode = "eager"
-    if graph is not None and "value" in graph:
-        value, max_s, launch_mode = graph["value"], graph["ms_per_step"] * 1e-3 * args.steps, \
-            "cuda_graph"
+    if replay is not None and "value" in replay:
+        value, max_s, launch_mode = replay["value"], \
+            replay["ms_per_step"] * 1e-3 * args.steps, "cuda_graph"
 
-    # per-call device times of the hot kernels, over the timed region
     def per_level(name):
         out = {}
-        for k, e0, e1 in ev[name]:
+        for k, e0, e1 in ctx.ev[name]:
             out.setdefault(k, []).append(e0.elapsed_time(e1))
         return {k: statistics.mean(v) for k, v in out.items()}
 
     fwd_ms, adj_ms, zero_ms = per_level("fwd"), per_level("adj"), per_level("zero")
-    result = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded vessel-tree phantom, random initial cloud)",
+    res = {
+        "value": value, "ms_per_step": max_s * 1e3 / args.steps, "eager": eager,
+        "graph_replay": replay,
         "config": {
-            "workload": wl.name, "balls_init": n0, "sensors": M,
+            "workload": wl.name, "balls_init": ctx.n0, "sensors": M,
             "levels_mhz": [wl.fs_mhz / f for f in wl.levels],
             "T": [arr.level_info(k)[0] for k in range(nl)],
             "balls_per_iteration": counts.tolist(),
+            "mean_R_per_iteration_mm": [round(mean_R[k], 6) for k in range(nl)],
             "pairs_per_step": pairs_per_step,
             "l2": "flushed before every timed step (512 MB write)",
-            "parallelism": f"replicas x{world}",
             "launch": launch_mode,
             "tiles": ({f"{wl.fs_mhz / wl.levels[k]:g}MHz": {"forward_balls_per_cta": c or "default",
                                                            "adjoint_ctas_per_chunk": sp or "default"}
@@ -428,11 +462,158 @@ def run_native(args, rank, world, local):
                       "adjoint": {str(k): v for k, v in adj_ms.items()},
                       "zero_gradient_adjoint": {str(k): v for k, v in zero_ms.items()}},
     }
+    levels = [{"mhz": wl.fs_mhz / wl.levels[k], "h_mm": wl.c * wl.levels[k] / wl.fs_mhz,
+               "pairs": float(counts[k]) * M, "mean_R_mm": mean_R[k],
+               "forward_ms": fwd_ms[k], "adjoint_ms": adj_ms[k]} for k in range(nl)]
+    zero = {"pairs": float(ctx.n0) * M, "ms": zero_ms.get(0)}
+    return res, clk, levels, zero
+
+
+# The method's minimum arithmetic per ball-sensor pair with the closed form
+# per cell, in thread-level FP32 operations: the forward takes about 25 for
+# the set-up (offset, distance with its square root and reciprocal, weight,
+# window bounds, amplitude) plus 6 per sample it writes, the adjoint about 40
+# for the set-up and chain rule plus 8 per sample it reads, and the two
+# together about 80 + 14 per sample. A pair touches s = 2 R / h + 1 samples
+# on average (R the mean radius of the live cloud, h = c dt_k the sample
+# spacing of the level). This is the count the roofline fraction is taken
+# against; the kernels' own executed instruction counts come from ncu.
+def samples_per_pair(mean_R, h):
+    return 2.0 * mean_R / h + 1.0
+
+
+def algorithmic_ops(kind, s):
+    return {"forward": 25.0 + 6.0 * s, "adjoint": 40.0 + 8.0 * s,
+            "forward+adjoint": 80.0 + 14.0 * s}[kind]
+
+
+# One ncu capture per hot kernel, of its launch at the finest level of the
+# large configuration (1M balls x 1024 sensors, 80 MHz), run by
+# `python bench.py --profile-large`: DRAM bytes (dram__bytes_read.sum +
+# dram__bytes_write.sum) and executed thread instructions per pair
+# (smsp__thread_inst_executed.sum / pairs). A record holds only while the
+# kernel's sources hash to the value it was taken with (the SHA-256 prefix
+# below); after any change both figures read null.
+NCU_RECORD = {
+    "forward": {"sources": ["paper_2601_00551_gb300/csrc/sbp_forward.cu",
+                            "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
+                "sha256": None, "bytes": None, "thread_inst_per_pair": None},
+    "adjoint": {"sources": ["paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
+                            "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
+                "sha256": None, "bytes": None, "thread_inst_per_pair": None},
+}
+
+
+def sources_sha(name):
+    import hashlib
+
+    m = hashlib.sha256()
+    for src in NCU_RECORD[name]["sources"]:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            m.update(f.read())
+    return m.hexdigest()[:16]
+
+
+def ncu_record(name):
+    """(DRAM bytes per launch, executed thread instructions per pair) of the
+    kernel's ncu record, or (None, None) once its sources have changed."""
+    rec = NCU_RECORD[name]
+    try:
+        ok = rec["sha256"] is not None and sources_sha(name) == rec["sha256"]
+    except OSError:
+        ok = False
+    return (rec["bytes"], rec["thread_inst_per_pair"]) if ok else (None, None)
+
+
+def alu_peak_gops(clk):
+    """152 SMs x 4 schedulers x 32 lanes issue one thread operation per lane
+    and cycle: 152 x 128 x the median SM clock sampled during the timed steps
+    (the MEASURED_PEAKS clock under load, else 1492 MHz, if none)."""
+    peaks = measured_peaks()
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get(
+        "sm_mhz_median") or 1492.0
+    return 152 * 128 * sm_mhz * 1e6 / 1e9, sm_mhz
+
+
+def roofline(levels, clk, probes):
+    """Roofline of the step's dominant kernel (forward or adjoint: the one
+    with the larger device time over the step), taken at its finest-level
+    launch. Neither kernel is a contraction or memory bound (a few bytes of
+    DRAM traffic per pair): both are bound by FP32/INT issue on the SMs.
+    achieved = the algorithmic operations of the launch (pairs x the count
+    above at the live cloud's mean radius) / its average device time."""
+    peak, sm_mhz = alu_peak_gops(clk)
+    tot = {"forward": sum(lv["forward_ms"] for lv in levels),
+           "adjoint": sum(lv["adjoint_ms"] for lv in levels)}
+    name = max(tot, key=tot.get)
+    per_level = []
+    for lv in levels:
+        s = samples_per_pair(lv["mean_R_mm"], lv["h_mm"])
+        row = {"mhz": lv["mhz"], "pairs": lv["pairs"], "samples_per_pair": s}
+        for kind, ms in (("forward", lv["forward_ms"]), ("adjoint", lv["adjoint_ms"])):
+            a = lv["pairs"] * algorithmic_ops(kind, s) / (ms * 1e-3) / 1e9
+            row[kind] = {"ms": ms, "ops_per_pair": algorithmic_ops(kind, s),
+                         "achieved_Gop_s": a, "frac": a / peak}
+        t = (lv["forward_ms"] + lv["adjoint_ms"]) * 1e-3
+        a = lv["pairs"] * algorithmic_ops("forward+adjoint", s) / t / 1e9
+        row["forward+adjoint"] = {"pairs_per_s": lv["pairs"] / t,
+                                  "ceiling_pairs_per_s": peak * 1e9 /
+                                  algorithmic_ops("forward+adjoint", s),
+                                  "frac": a / peak}
+        per_level.append(row)
+    fine = per_level[-1]
+    top = fine[name]
+    traffic, inst = ncu_record(name)
+    ops_all = sum(r["pairs"] * algorithmic_ops("forward+adjoint", r["samples_per_pair"])
+                  for r in per_level)
+    t_all = sum((lv["forward_ms"] + lv["adjoint_ms"]) * 1e-3 for lv in levels)
+    out = {"bound": "alu", "kernel": f"{name} at {fine['mhz']:g} MHz (finest level)",
+           "achieved": top["achieved_Gop_s"], "peak": peak, "unit": "Gop/s",
+           "frac": top["frac"], "traffic": traffic,
+           "ops_per_pair": top["ops_per_pair"], "samples_per_pair": fine["samples_per_pair"],
+           "pairs_per_launch": fine["pairs"], "ms_per_launch": top["ms"],
+           "executed_thread_inst_per_pair": inst,
+           "ops_basis": "forward 25 + 6 s, adjoint 40 + 8 s, forward+adjoint 80 + 14 s FP32 "
+                        "operations per pair, s = 2 R/h + 1 at the live cloud's mean R",
+           "peak_basis": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock sampled "
+                         "during the timed steps; recipe unit counts)",
+           "forward_adjoint_frac_step": ops_all / t_all / 1e9 / peak,
+           "per_level": per_level}
+    if probes:
+        out["measured_issue_peak_Gop_s"] = probes["warp_inst_per_s"] * 32 / 1e9
+        out["frac_of_measured_issue"] = top["achieved_Gop_s"] / out["measured_issue_peak_Gop_s"]
+    return out
+
+
+def run_native(args, rank, world, local):
+    import torch
+
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_2601_00551_gb300 import slingbag as sb
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = make_workload(args.workload)
+    ctx = StepContext(sb, wl, dev)
+    meas, clk, levels, zero = measure_step(args, sb, ctx, local, tune=not args.no_autotune,
+                                           graph=not args.profile,
+                                           clocks=not (args.no_clocks or args.profile))
+    result = {
+        "metric": METRIC, "value": meas["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": meas["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": f"synthetic (seeded vessel-tree phantom, random initial cloud: {wl.name})",
+        "config": dict(meas["config"], parallelism=f"replicas x{world}"),
+        "gpu_launches": meas["gpu_launches"],
+        "kernel_ms": meas["kernel_ms"],
+    }
     if clk is not None:
         result["clocks"] = clk
-    result["eager"] = eager
-    if graph is not None:
-        result["graph_replay"] = graph
+    result["eager"] = meas["eager"]
+    if meas["graph_replay"] is not None:
+        result["graph_replay"] = meas["graph_replay"]
     probes = None
     if not args.profile:
         try:
@@ -440,126 +621,74 @@ def run_native(args, rank, world, local):
             result["probes"] = {k: float(f"{v:.4g}") for k, v in probes.items()}
         except Exception as exc:  # a probe failure must not hide the measurement
             result["probes"] = {"error": str(exc)}
-    mean_R = float(np.mean(wl.init.R))
-    h_fine = wl.c * wl.levels[-1] / wl.fs_mhz
-    result["roofline"] = roofline(fwd_ms, adj_ms, counts, M, clk, mean_R, h_fine, probes)
-
+    result["roofline"] = roofline(levels, clk, probes)
+    if zero["ms"]:
+        result["zero_gradient_adjoint"] = {
+            "pairs": zero["pairs"], "ms": zero["ms"],
+            "pairs_per_s": zero["pairs"] / (zero["ms"] * 1e-3)}
     if not (args.no_e2e or args.profile):
-        result["e2e"] = run_e2e(args, sb, arr, wl, y_host, init, n0, n_cap, stages, adam,
-                                pairs_per_step, dev)
-    if not args.profile and args.workload == "vessel":
-        result["time_to_residual"] = time_to_residual(sb, arr, wl, y_full, init, n0)
+        result["e2e"] = run_e2e(args, sb, ctx.arr, wl, ctx.y_host, ctx.init, ctx.n0,
+                                ctx.n_cap, ctx.stages, ctx.adam, float(
+                                    np.sum(meas["config"]["balls_per_iteration"])) * ctx.M,
+                                dev)
+    head_y = ctx.y_host
+    ctx.close()
+    del ctx
+    torch.cuda.empty_cache()
+
+    extras = not args.profile and args.workload == "large"
+    vctx = None
+    if extras:
+        # the 200k-ball x 512-sensor vessel workload: its own step line, and
+        # the host of the schedule, learned-proposal and autograd measurements
+        vctx = StepContext(sb, make_workload("vessel"), dev)
+        vm, vclk, vlevels, vzero = measure_step(args, sb, vctx, local,
+                                                tune=not args.no_autotune, graph=True,
+                                                clocks=not args.no_clocks)
+        result["vessel_step"] = {
+            "value": vm["value"], "unit": UNIT, "ms_per_step": vm["ms_per_step"],
+            "eager": vm["eager"], "config": vm["config"], "kernel_ms": vm["kernel_ms"],
+            "clocks": vclk, "roofline": roofline(vlevels, vclk, probes),
+            "zero_gradient_adjoint": {"pairs": vzero["pairs"], "ms": vzero["ms"]}}
+        vwl = vctx.wl
+        result["time_to_residual"] = time_to_residual(sb, vctx.arr, vwl, vctx.y_full,
+                                                      vctx.init, vctx.n0)
         if not args.no_learned:
             try:
                 result["learned_init"] = learned_init(
-                    sb, arr, wl, y_full, init, result["time_to_residual"]["pro"]["seconds"], dev)
+                    sb, vctx.arr, vwl, vctx.y_full, vctx.init,
+                    result["time_to_residual"]["pro"]["seconds"], dev)
             except Exception as exc:  # keep the main measurement if this part fails
                 result["learned_init"] = {"error": f"{type(exc).__name__}: {exc}"}
-    if not (args.profile or args.no_frames) and args.workload == "vessel":
         try:
-            result["batched_frames"] = batched_frames(args, sb, dev)
-        except Exception as exc:  # keep the main measurement if this part fails
-            result["batched_frames"] = {"error": f"{type(exc).__name__}: {exc}"}
-    if not args.profile and args.workload == "vessel":
-        try:
-            result["autograd_memory"] = autograd_memory(sb, arr, wl, init, n0, dev)
+            result["autograd_memory"] = autograd_memory(sb, vctx.arr, vwl, vctx.init,
+                                                        vctx.n0, dev)
         except Exception as exc:  # keep the main measurement if this part fails
             result["autograd_memory"] = {"error": f"{type(exc).__name__}: {exc}"}
-        if not args.no_large:
-            try:
-                result["large_config"] = large_config(sb, dev, tune=not args.no_autotune)
-            except Exception as exc:  # keep the main measurement if this part fails
-                result["large_config"] = {"error": f"{type(exc).__name__}: {exc}"}
         try:
-            result["gaussian_radiator"] = gaussian_radiator(sb, arr, wl, init, n0, dev)
+            result["gaussian_radiator"] = gaussian_radiator(sb, vctx.arr, vwl, vctx.init,
+                                                            vctx.n0, dev)
         except Exception as exc:  # keep the main measurement if this part fails
             result["gaussian_radiator"] = {"error": f"{type(exc).__name__}: {exc}"}
-    if not (args.profile or args.no_envelope) and args.workload == "vessel":
-        try:
-            result["envelope_init_voxel"] = envelope_init_voxel(sb, dev)
-        except Exception as exc:  # keep the main measurement if this part fails
-            result["envelope_init_voxel"] = {"error": f"{type(exc).__name__}: {exc}"}
+        vessel_y = vctx.y_host
+        vctx.close()
+        del vctx
+        torch.cuda.empty_cache()
+        if not args.no_frames:
+            try:
+                result["batched_frames"] = batched_frames(args, sb, dev)
+            except Exception as exc:  # keep the main measurement if this part fails
+                result["batched_frames"] = {"error": f"{type(exc).__name__}: {exc}"}
+        if not args.no_envelope:
+            try:
+                result["envelope_init_voxel"] = envelope_init_voxel(sb, dev)
+            except Exception as exc:  # keep the main measurement if this part fails
+                result["envelope_init_voxel"] = {"error": f"{type(exc).__name__}: {exc}"}
+    else:
+        vessel_y = None
     if world == 1 and rank == 0 and not (args.no_cpu_baseline or args.profile):
-        result["cpu_baseline"] = cpu_baseline(wl, y_host, counts, n0, seconds=15.0)
-    arr.close()
+        result["cpu_baseline"] = cpu_baseline(wl, head_y, vessel_y)
     return result, rank
-
-
-# Thread-level arithmetic operations per pair of the two hot kernels, counted
-# from the per-pair code of the algorithm (FP32 and integer arithmetic,
-# compares and conversions; loads, stores, branches and loop control are not
-# counted; a packed two-pair instruction counts once per pair). Forward: exact
-# distance 55, inside test 2, window 42, weight 6, K 3, coefficients 15, range
-# test 11, conversions 4, impulses 11, high words 6, bounds and addresses 8,
-# shared atomics 12. Adjoint: distance 55, window 42, direction and weight 8,
-# tests and bounds 11, chain rule 40, plus the window sums: 3 operations per
-# ramp cell beyond the first and 2 more, with L = 2 R / h cells on average.
-FWD_OPS_PER_PAIR = 175
-
-
-def adj_ops_per_pair(mean_R, h):
-    L = 2.0 * mean_R / h
-    return 156.0 + 3.0 * max(0.0, L - 1.0) + 2.0
-
-
-# DRAM bytes (read + write) of one launch at the 40 MHz level of the vessel
-# workload, from one ncu capture of the kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum). A record holds only while the kernel's sources hash
-# to the value it was taken with (the SHA-256 prefix below); after any change
-# the traffic is reported as null.
-NCU_TRAFFIC = {
-    "forward": {"sources": ["paper_2601_00551_gb300/csrc/sbp_forward.cu",
-                            "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "492ec1fc8c88f6a4", "bytes": 5.261824e6},
-    "adjoint": {"sources": ["paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
-                            "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "0fa46a80c8fb55ce", "bytes": 3.762432e6},
-}
-
-
-def _traffic(name):
-    import hashlib
-
-    rec = NCU_TRAFFIC[name]
-    if not rec["sha256"] or rec["bytes"] is None:
-        return None
-    m = hashlib.sha256()
-    try:
-        for src in rec["sources"]:
-            with open(os.path.join(ROOT, src), "rb") as f:
-                m.update(f.read())
-    except OSError:
-        return None
-    return rec["bytes"] if m.hexdigest()[:16] == rec["sha256"] else None
-
-
-def roofline(fwd_ms, adj_ms, counts, M, clk, mean_R, h_fine, probes):
-    """Roofline of the dominant call at the finest level. Both hot kernels
-    are bound by instruction issue on the SMs (their DRAM traffic is a few
-    bytes per pair); the peak is 152 SMs x 128 lanes x the median SM clock
-    sampled during the timed steps (4 schedulers x 32 lanes per SM issue one
-    thread operation per lane and cycle), the achieved rate is the per-pair
-    operation count of the algorithm x pairs / average call time."""
-    k = max(fwd_ms)
-    ops = {"forward": FWD_OPS_PER_PAIR, "adjoint": adj_ops_per_pair(mean_R, h_fine)}
-    calls = {"forward": fwd_ms[k], "adjoint": adj_ms[k]}
-    name = max(calls, key=calls.get)
-    pairs = float(counts[k]) * M
-    ms = calls[name]
-    achieved = pairs * ops[name] / (ms * 1e-3) / 1e9  # Gop/s
-    peaks = measured_peaks()
-    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get(
-        "sm_mhz_median") or 1492.0
-    peak = 152 * 128 * sm_mhz * 1e6 / 1e9
-    out = {"bound": "alu", "kernel": f"{name} call at the finest level", "achieved": achieved,
-           "peak": peak, "unit": "Gop/s", "frac": achieved / peak, "traffic": _traffic(name),
-           "ops_per_pair": ops[name], "pairs_per_launch": pairs, "ms_per_launch": ms,
-           "peak_basis": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock sampled "
-                         "during the timed steps; recipe unit counts)"}
-    if probes:
-        out["measured_issue_peak_Gop_s"] = probes["warp_inst_per_s"] * 32 / 1e9
-        out["frac_of_measured_issue"] = achieved / out["measured_issue_peak_Gop_s"]
-    return out
 
 
 def pro_segments(nl, seg):
@@ -1254,8 +1383,9 @@ def large_config(sb, dev, reps=3, tune=True):
         res["forward_pairs_per_s"] = pairs / (res["forward_ms"] * 1e-3)
         res["adjoint_pairs_per_s"] = pairs / (res["adjoint_ms"] * 1e-3)
         peak = 152 * 128 * 2070e6
-        res["forward_frac"] = pairs * FWD_OPS_PER_PAIR / (res["forward_ms"] * 1e-3) / peak
-        res["adjoint_frac"] = pairs * adj_ops_per_pair(mean_R, h) / (res["adjoint_ms"] * 1e-3) / peak
+        s = samples_per_pair(mean_R, h)
+        res["forward_frac"] = pairs * algorithmic_ops("forward", s) / (res["forward_ms"] * 1e-3) / peak
+        res["adjoint_frac"] = pairs * algorithmic_ops("adjoint", s) / (res["adjoint_ms"] * 1e-3) / peak
         out["levels"][f"{wl.fs_mhz / f:g}MHz"] = res
     if arr.sync_status() != 0:
         raise RuntimeError("device status latched in the large configuration")
@@ -1375,25 +1505,105 @@ def oracle_step(wl, y_host, balls, threads):
     return float(np.sum(counts)) * wl.sensors.M
 
 
-def cpu_baseline(wl, y_host, counts, n0, seconds=15.0):
+def _timed_loop(fn, seconds, max_reps=50):
+    """Runs fn() (which returns the pairs it processed) until `seconds` have
+    passed (at least once); returns (pairs/s, repetitions, seconds)."""
+    t0 = time.perf_counter()
+    work, reps = 0.0, 0
+    while True:
+        work += fn()
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt > seconds or reps >= max_reps:
+            return work / dt, reps, dt
+
+
+def oracle_units(threads, vessel_y, seconds=1.0):
+    """The oracle's timed units, each single-threaded and on `threads` host
+    threads: one forward + adjoint of the 2,000-ball x 64-sensor case; one
+    forward + adjoint per level of a seeded 1/64 sample of the 200k-ball
+    vessel cloud x 512 sensors; one forward + adjoint of a 1/32 sample of one
+    frame of the batched workload (256 sensors, 40 MHz, T = 2048); the whole
+    50-iteration run of the 2,000-ball case (zero-gradient filtering, then
+    forward, adjoint, Adam and filter/grow per iteration)."""
+    import oracle
+    import workloads
+
+    def fwd_adj(wl, balls, f, y_k=None):
+        dt, Tk = f / wl.fs_mhz, (wl.T + f - 1) // f
+        S = oracle.forward(balls, wl.sensors.pos, wl.sensors.normal, wl.c, dt, Tk,
+                           threads=nt)
+        G = 2.0 * (S - y_k) if y_k is not None else 2.0 * S
+        oracle.adjoint(balls, wl.sensors.pos, wl.sensors.normal, wl.c, dt, Tk,
+                       G.astype(np.float32), threads=nt)
+        return float(balls.shape[1]) * wl.sensors.M
+
+    units = []
+    tiny = workloads.tiny()
+    y_tiny = workloads.add_noise(oracle.forward(
+        tiny.truth.stack(), tiny.sensors.pos, tiny.sensors.normal, tiny.c, 1.0 / tiny.fs_mhz,
+        tiny.T, threads=threads).astype(np.float32))
+    ves = workloads.vessel()
+    if vessel_y is None:
+        vessel_y = workloads.add_noise(oracle.forward(
+            ves.truth.stack(), ves.sensors.pos, ves.sensors.normal, ves.c,
+            1.0 / ves.fs_mhz, ves.T, threads=threads).astype(np.float32))
+    vs = oracle_sample(ves, None, 1.0 / 64)
+    fr = workloads.frames(n_frames=1)
+    frw = workloads.Workload(fr.name, fr.sensors, fr.inits[0], None, fr.fs_mhz, fr.T,
+                             fr.levels)
+    fs = oracle_sample(frw, None, 1.0 / 32)
+    st = [oracle.Stage(level=0, iterations=50, grad_mask=7, grow=True)]
+    gp = oracle.GrowParams(seed=1000, **GROW)
+
+    def tiny_run():
+        _, _, counts = oracle.reconstruct(tiny.init.stack(), tiny.sensors.pos,
+                                          tiny.sensors.normal, tiny.c, tiny.fs_mhz, tiny.T,
+                                          tiny.levels, y_tiny, st,
+                                          zero_grad_mode=oracle.KEEP_NEG, grow_params=gp,
+                                          threads=nt)
+        return float(np.sum(counts)) * tiny.sensors.M
+
+    jobs = [("2000 balls x 64 sensors, 40 MHz: forward + adjoint",
+             lambda: fwd_adj(tiny, tiny.init.stack(), 1, y_tiny))]
+    for f in ves.levels:
+        jobs.append((f"vessel 1/64 sample ({vs.shape[1]} balls) x 512 sensors, "
+                     f"{ves.fs_mhz / f:g} MHz: forward + adjoint",
+                     lambda f=f: fwd_adj(ves, vs, f, oracle.downsample(vessel_y, f))))
+    jobs.append((f"frame 0 of the batched workload, 1/32 sample ({fs.shape[1]} balls) x 256 "
+                 "sensors, 40 MHz: forward + adjoint (G = 2S)", lambda: fwd_adj(frw, fs, 1)))
+    jobs.append(("2000 balls x 64 sensors: the whole 50-iteration run", tiny_run))
+    for name, fn in jobs:
+        row = {"unit": name}
+        for nt_ in (1, threads):
+            nt = nt_
+            rate, reps, dt = _timed_loop(fn, seconds, max_reps=20)
+            row[f"pairs_per_s_{nt_}_threads"] = rate
+            row[f"seconds_{nt_}_threads"] = dt / reps
+        units.append(row)
+    return units
+
+
+def cpu_baseline(wl, y_host, vessel_y, seconds=8.0):
+    """The FP64 oracle timed on the host cores on a bounded sample of the
+    step's workload (the same pipeline as the GPU step), plus its timed units
+    (`oracle_units`)."""
     import oracle
 
     threads = oracle.num_procs()
-    frac = 1.0 / 4
+    frac = {"large": 1.0 / 256, "vessel": 1.0 / 4}.get(wl.name.split(":")[0], 1.0)
     balls = oracle_sample(wl, y_host, frac)
-    oracle_step(wl, y_host, balls[:, :256], threads)  # build and warm the library
-    t0 = time.perf_counter()
-    pairs, reps = 0.0, 0
-    while True:
-        pairs += oracle_step(wl, y_host, balls, threads)
-        reps += 1
-        if time.perf_counter() - t0 > seconds or reps >= 50:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": pairs / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{reps} step(s) of the same pipeline on a seeded 1/4 sample of the "
-                      f"initial cloud ({balls.shape[1]} balls) x {wl.sensors.M} sensors, "
-                      f"FP64, {threads} OpenMP threads, {dt:.1f} s"}
+    oracle_step(wl, y_host, balls[:, :64], threads)  # build and warm the library
+    value, reps, dt = _timed_loop(lambda: oracle_step(wl, y_host, balls, threads), seconds)
+    out = {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{reps} step(s) of the same pipeline on a seeded 1/{round(1 / frac)} "
+                     f"sample of the initial cloud ({balls.shape[1]} balls) x "
+                     f"{wl.sensors.M} sensors, FP64, {threads} OpenMP threads, {dt:.1f} s"}
+    try:
+        out["units"] = oracle_units(threads, vessel_y)
+    except Exception as exc:  # the step figure stands on its own
+        out["units"] = {"error": f"{type(exc).__name__}: {exc}"}
+    return out
 
 
 def run_reference(args, rank):
@@ -1410,7 +1620,7 @@ def run_reference(args, rank):
     y = oracle.forward(wl.truth.stack(), wl.sensors.pos, wl.sensors.normal, wl.c,
                        f_fine / wl.fs_mhz, wl.T, threads=threads).astype(np.float32)
     y_host = workloads.add_noise(y)
-    frac = 1.0 / 32 if args.workload == "vessel" else 1.0
+    frac = {"large": 1.0 / 256, "vessel": 1.0 / 32}.get(args.workload, 1.0)
     balls = oracle_sample(wl, y_host, frac)
     for _ in range(max(0, args.warmup)):
         oracle_step(wl, y_host, balls, threads)
@@ -1494,6 +1704,16 @@ def main(argv=None):
     args = parse_args(argv)
     if args.profile_large:
         print(json.dumps(profile_large()))
+        return 0
+    if args.large_calls:
+        import torch
+
+        import __graft_entry__ as ge
+
+        ge.build()
+        from paper_2601_00551_gb300 import slingbag as sb
+
+        print(json.dumps(large_config(sb, torch.device("cuda", 0), tune=not args.no_autotune)))
         return 0
     if args.learned_large:
         print(json.dumps(learned_large()))

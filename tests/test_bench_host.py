@@ -65,43 +65,58 @@ def test_reference_arm_non_zero_rank_does_nothing(capsys, monkeypatch):
     assert capsys.readouterr().out.strip() == ""
 
 
-def test_roofline_takes_the_slower_call_at_the_finest_level(monkeypatch):
+def _levels(fwd, adj, counts, M, mean_R, hs):
+    return [{"mhz": 40.0 / (2 ** (len(hs) - 1 - k)), "h_mm": hs[k], "pairs": counts[k] * M,
+             "mean_R_mm": mean_R[k], "forward_ms": fwd[k], "adjoint_ms": adj[k]}
+            for k in range(len(hs))]
+
+
+def test_roofline_counts_the_methods_operations_per_sample(monkeypatch):
+    """forward 25 + 6 s, adjoint 40 + 8 s, both together 80 + 14 s operations
+    per pair, s = 2 R / h + 1 at the live cloud's mean radius; the dominant
+    kernel is the one with the larger time over the step, taken at its
+    finest-level launch."""
     monkeypatch.setattr(bench, "measured_peaks", lambda: {})
-    fwd = {0: 0.30, 1: 0.31, 2: 0.35}
-    adj = {0: 0.33, 1: 0.34, 2: 0.40}
-    counts = [100_000, 99_000, 98_000]
     h = 1.5 / 40.0  # mm per cell at 40 MHz
-    r = bench.roofline(fwd, adj, counts, 512, {"sm_mhz": 2000.0}, 3.35 * h, h, None)
-    assert r["kernel"] == "adjoint call at the finest level"
+    hs = [4 * h, 2 * h, h]
+    R = [0.125, 0.13, 0.14]
+    counts = [100_000, 99_000, 98_000]
+    lv = _levels([0.30, 0.31, 0.35], [0.33, 0.34, 0.40], counts, 512, R, hs)
+    r = bench.roofline(lv, {"sm_mhz": 2000.0}, None)
+    assert r["kernel"].startswith("adjoint at 40 MHz")
     assert r["pairs_per_launch"] == 98_000 * 512 and r["ms_per_launch"] == 0.40
-    # 156 operations per pair, 3 per ramp cell past the first, 2 for the ends
-    assert r["ops_per_pair"] == pytest.approx(156 + 3 * (6.7 - 1) + 2)
+    s = 2 * 0.14 / h + 1
+    assert r["samples_per_pair"] == pytest.approx(s)
+    assert r["ops_per_pair"] == pytest.approx(40 + 8 * s)
     assert r["peak"] == pytest.approx(152 * 128 * 2000e6 / 1e9)
-    achieved = 98_000 * 512 * r["ops_per_pair"] / 0.40e-3 / 1e9
+    achieved = 98_000 * 512 * (40 + 8 * s) / 0.40e-3 / 1e9
     assert r["achieved"] == pytest.approx(achieved)
     assert r["frac"] == pytest.approx(achieved / r["peak"])
-    # the forward's count when its call is the slower one
-    r = bench.roofline({2: 0.5}, {2: 0.4}, [0, 0, 1000], 8, {"sm_mhz": 2070.0}, 0.1, h, None)
-    assert r["kernel"] == "forward call at the finest level"
-    assert r["ops_per_pair"] == bench.FWD_OPS_PER_PAIR
+    fa = r["per_level"][2]["forward+adjoint"]
+    assert fa["pairs_per_s"] == pytest.approx(98_000 * 512 / 0.75e-3)
+    assert fa["ceiling_pairs_per_s"] == pytest.approx(r["peak"] * 1e9 / (80 + 14 * s))
+    s0 = 2 * 0.125 / (4 * h) + 1
+    assert r["per_level"][0]["forward"]["ops_per_pair"] == pytest.approx(25 + 6 * s0)
+    step_ops = sum(counts[k] * 512 * (80 + 14 * (2 * R[k] / hs[k] + 1)) for k in range(3))
+    assert r["forward_adjoint_frac_step"] == pytest.approx(
+        step_ops / (sum([0.30, 0.31, 0.35, 0.33, 0.34, 0.40]) * 1e-3) / 1e9 / r["peak"])
+    # the forward when it takes longer over the step
+    lv = _levels([0.5, 0.5, 0.5], [0.4, 0.4, 0.4], [1, 1, 1000], 8, R, hs)
+    r = bench.roofline(lv, {"sm_mhz": 2070.0}, None)
+    assert r["kernel"].startswith("forward")
+    assert r["ops_per_pair"] == pytest.approx(25 + 6 * s)
 
 
-def test_traffic_record_holds_only_for_the_measured_sources(monkeypatch):
-    rec = dict(bench.NCU_TRAFFIC["adjoint"])
-    assert bench._traffic("adjoint") in (None, rec["bytes"])
-    import hashlib
-
-    m = hashlib.sha256()
-    for src in rec["sources"]:
-        with open(os.path.join(bench.ROOT, src), "rb") as f:
-            m.update(f.read())
-    good = dict(rec, sha256=m.hexdigest()[:16])
-    monkeypatch.setitem(bench.NCU_TRAFFIC, "adjoint", good)
-    assert bench._traffic("adjoint") == rec["bytes"]
-    monkeypatch.setitem(bench.NCU_TRAFFIC, "adjoint", dict(good, sha256="0" * 16))
-    assert bench._traffic("adjoint") is None
-    monkeypatch.setitem(bench.NCU_TRAFFIC, "adjoint", dict(good, bytes=None))
-    assert bench._traffic("adjoint") is None
+def test_ncu_record_holds_only_for_the_measured_sources(monkeypatch):
+    rec = dict(bench.NCU_RECORD["adjoint"])
+    assert bench.ncu_record("adjoint") in ((None, None),
+                                           (rec["bytes"], rec["thread_inst_per_pair"]))
+    good = dict(rec, sha256=bench.sources_sha("adjoint"), bytes=1.5e6,
+                thread_inst_per_pair=120.0)
+    monkeypatch.setitem(bench.NCU_RECORD, "adjoint", good)
+    assert bench.ncu_record("adjoint") == (1.5e6, 120.0)
+    monkeypatch.setitem(bench.NCU_RECORD, "adjoint", dict(good, sha256="0" * 16))
+    assert bench.ncu_record("adjoint") == (None, None)
 
 
 def test_stage_schedules():
