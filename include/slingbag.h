@@ -49,7 +49,8 @@ typedef enum {
     SBP_ERR_CUDA = -2,     /* a CUDA call or kernel launch failed */
     SBP_ERR_CAPACITY = -3, /* growth would exceed n_cap (device-latched) */
     SBP_ERR_LEVEL = -4,    /* level index out of range */
-    SBP_ERR_TIMEOUT = -5,  /* reserved: a bounded device wait gave up */
+    SBP_ERR_TIMEOUT = -5,  /* a bounded device wait gave up (sbp_cnn_status; the
+                              radiator path has no device waits) */
     SBP_ERR_NUMERIC = -6   /* non-finite input detected */
 } sbp_status;
 
@@ -159,13 +160,16 @@ int sbp_set_sampling_level(sbp_array arr, int k, const float* y_full_dev, float*
  * i.e. the average over sample cell [j dt_k, (j+1) dt_k) of the uniform-sphere
  * N-wave p0 w (d - c t)/(2 d) on |d - c t| < R. Pairs with d <= R contribute
  * nothing (counted, see sbp_get_inside_pairs); samples outside [0, T_k) are
- * dropped. flags: 0 or SBP_DETERMINISTIC. */
+ * dropped. A live ball with a non-finite x, y, z, R or p0 latches
+ * SBP_ERR_NUMERIC (reported by sbp_sync_status; its traces are then not
+ * meaningful). flags: 0 or SBP_DETERMINISTIC. */
 int sbp_forward(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap, float* S_dev,
                 unsigned flags, sbp_stream stream);
 
 /* sbp_forward without any device allocation, for callers that cannot call
- * cudaMalloc (code inside a stream capture or a host callback, or a host
- * that borrows every buffer from a framework owning all allocations). The
+ * cudaMalloc: a host that borrows every buffer from a framework owning all
+ * allocations (a serving runtime with its own pool), or one held to a fixed
+ * device-memory budget. The
  * paper has no counterpart; this is a deployment variant of sbp_forward.
  * It takes no array object: the caller passes the sensors, the level and all
  * inputs and outputs; the scratch (trace accumulators and state words) is a
@@ -176,8 +180,13 @@ int sbp_forward(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap, flo
  *   dt_us = f_k / fs (sampling interval of the level), T_k samples;
  *   weight_mode: SBP_W_*; balls, n_dev, n_cap, S_dev as in sbp_forward.
  * Returns SBP_ERR_ARG when M * T_k exceeds 2^21 cells (use sbp_forward then).
- * The first call on a device looks up the array's device address once
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress). Under lazy module loading that look-up loads the
+ * library's module, which allocates the 16 MiB array and the module's code:
+ * make that first call before any stream capture. The address is kept per
+ * device and per context, and looked up again (with the same caveat) when
+ * the calling thread's current context is not the one it was taken in, e.g.
+ * after cudaDeviceReset.
  * Every call clears the part of the array it uses, and all calls share it:
  * calls that overlap on the GPU (other streams, other host threads) race and
  * corrupt each other's traces; serialise them. */
@@ -496,7 +505,8 @@ int sbp_cnn_propose(sbp_cnn cnn, const float* vol_dev, float prob_threshold, uin
                     sbp_balls out, int n_cap, int* n_dev, sbp_stream stream);
 
 /* Synchronise `stream` and return (then clear) the convolution status:
- * 0 = fine, 1 = a bounded wait gave up. */
+ * 0 = fine, SBP_ERR_TIMEOUT = a bounded wait of the tensor-core
+ * convolution gave up (the CTA freed its tensor memory and returned). */
 int sbp_cnn_status(sbp_stream stream, int* status);
 
 /* Number of CUDA kernels this library has launched in this process. */

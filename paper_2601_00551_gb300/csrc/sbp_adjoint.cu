@@ -23,7 +23,7 @@
 // Kernels:
 //   downsample   y_k = block mean over f_k samples (zero padded)
 //   residual     G = 2 (S - y), L = sum (S - y)^2 (fixed-order last-block reduction)
-//   adj_group    kAdjSplit CTAs (grid.y) share one chunk of consecutive
+//   adj_group    kAdjSplit consecutive CTAs share one chunk of consecutive
 //                balls (one thread per ball) and split the sensors between
 //                them. Each CTA walks its sensors in groups. For each group
 //                it stages, per sensor, the window of G that the chunk's
@@ -55,7 +55,7 @@ namespace {
 
 constexpr int kAdjThreads = SBP_ADJ_CHUNK;  // balls (threads) per adjoint CTA
 constexpr int kAdjSplit = 8;      // default CTAs per chunk, each taking 1/split of the sensors
-constexpr int kAdjCap = 3584;     // cells per staging buffer (two buffers per CTA)
+constexpr int kAdjCap = 3072;     // cells per staging buffer (two buffers per CTA)
 constexpr int kAdjCapP0 = 1792;   // the same for the p0-only adjoint, which keeps more CTAs per SM
 constexpr int kAdjShare = 16;     // a CTA's share of the sensors is a multiple of this
 constexpr int kAdjMeta = 128;     // sensors whose set-up is held in shared memory at once
@@ -236,12 +236,12 @@ __device__ __forceinline__ void adj_window_sums(const float* __restrict__ sGrow,
 // P0_ONLY: only dL/dp0 is wanted (the zero-gradient pass), so the chain rule
 // for R and the centre is skipped. WMODE: the orientation weight (SBP_W_*),
 // fixed at compile time so that no pair branches on it.
-// gridDim.y CTAs share a chunk, each taking 1/gridDim.y of the sensors.
+// `split` CTAs share a chunk, each taking 1/split of the sensors.
 template <bool P0_ONLY, int WMODE>
-__global__ void __launch_bounds__(kAdjThreads, P0_ONLY ? 10 : 6)
+__global__ void __launch_bounds__(kAdjThreads, P0_ONLY ? 10 : 7)
 adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, LevelGeo g,
                  const float* __restrict__ G_all, unsigned mask, GradOut out,
-                 float* __restrict__ part_all, unsigned int* __restrict__ tickets) {
+                 float* __restrict__ part_all, unsigned int* __restrict__ tickets, int split) {
     // two staging buffers of kCap cells, each holding the windows of one
     // group of sensors packed one after another
     constexpr int kCap = P0_ONLY ? kAdjCapP0 : kAdjCap;
@@ -266,7 +266,12 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     __shared__ float s_red[(kAdjThreads / 32) * 7];
     __shared__ float s_box[7];
     static_assert(2 * kWin <= kCap, "a pair of staged windows must fit one buffer");
-    const int c0 = blockIdx.x * kAdjThreads;
+    // one-dimensional grid, chunk-major: the `split` CTAs of a chunk are
+    // consecutive, so they run at about the same time and the partial sums
+    // they leave for the chunk's last CTA are still in L2 when it reads them
+    const int chunk_id = (int)(blockIdx.x / (unsigned)split);
+    const int part = (int)blockIdx.x - chunk_id * split;
+    const int c0 = chunk_id * kAdjThreads;
     const FrameSlot fs = sbp_frame_of(ft, c0);
     if (c0 >= fs.end) return;  // uniform over the chunk's CTAs
     const int c1 = min(fs.end, c0 + kAdjThreads);
@@ -315,8 +320,6 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     const float hh2 = 2.0f * h * h;
     float2 gx2 = f2(0.f), gy2 = f2(0.f), gz2 = f2(0.f), gR2 = f2(0.f), gp2 = f2(0.f);
     // this CTA's share of the sensors, whole groups
-    const int part = (int)blockIdx.y;
-    const int split = (int)gridDim.y;
     const int per = ((M + split - 1) / split + kAdjShare - 1) / kAdjShare * kAdjShare;
     const int m_begin = min(M, part * per), m_end = min(M, m_begin + per);
     // The share is walked in blocks of up to kAdjMeta sensors whose positions,
@@ -567,7 +570,7 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
     // in rank order and writes every ball's gradients exactly once, so the
     // result does not depend on which CTA finishes last, and no CTA waits
     // for another.
-    const size_t chunk = blockIdx.x;
+    const size_t chunk = chunk_id;
     float* __restrict__ mine = part_all + (chunk * split + part) * 5 * kAdjThreads;
     if (valid) {  // stored under the ball's chunk-local index
         if (!P0_ONLY) {
@@ -661,11 +664,11 @@ int launch_adj(sbp_array_s* a, const FrameTable& ft, int total, int split, const
         sbp_set_error("adjoint: more balls than the array's capacity");
         return SBP_ERR_ARG;
     }
-    const dim3 grid(chunks, split);
+    const unsigned grid = (unsigned)chunks * (unsigned)split;
     auto go = [&](auto p0_only, auto wmode) {
         adj_group_kernel<decltype(p0_only)::value, decltype(wmode)::value>
             <<<grid, kAdjThreads, 0, st>>>(b, ft, a->d_sens, g, G, mask, o, a->d_adj_part,
-                                           a->d_adj_ticket);
+                                           a->d_adj_ticket, split);
     };
     auto by_mode = [&](auto p0_only) {
         if (g.wmode == SBP_W_NONE)

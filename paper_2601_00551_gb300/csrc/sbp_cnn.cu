@@ -779,7 +779,7 @@ int sbp_cnn_status(sbp_stream stream, int* status) {
     if (sbp_cuda_check(cudaMemcpyFromSymbol(&v, g_cnn_status, sizeof(int)), "cnn_status: read") ||
         sbp_cuda_check(cudaMemcpyToSymbol(g_cnn_status, &zero, sizeof(int)), "cnn_status: clear"))
         return SBP_ERR_CUDA;
-    *status = v;
+    *status = v ? SBP_ERR_TIMEOUT : 0;
     return SBP_OK;
 }
 

@@ -40,6 +40,7 @@
 //   fwd_finalize  CTA = one sensor; two block scans turn impulses into the
 //                 float32 trace and clear the accumulator row
 #include <algorithm>
+#include <cuda.h>
 #include <mutex>
 
 #include "sbp_internal.cuh"
@@ -57,18 +58,27 @@ static_assert(2LL * SBP_FRAME_ALIGN * (1LL << kLoBits) < (1LL << 32), "low word 
 constexpr int kFinalizeThreads = 1024;
 constexpr int kFracHeadroomBits = 34;  // F = 34 - ceil(log2 max|p0|)
 
-// pmax[f] = max |p0| over frame f (grid.y = frame).
-__global__ void fwd_pmax_kernel(const float* __restrict__ p0, FrameTable ft,
-                                unsigned int* __restrict__ pmax) {
+// pmax[f] = max |p0| over frame f (grid.y = frame). A live ball with a
+// non-finite coordinate, radius or pressure latches SBP_ERR_NUMERIC (its
+// pairs would otherwise be dropped silently: fmaxf ignores a NaN p0).
+__global__ void fwd_pmax_kernel(BallsDev b, FrameTable ft, unsigned int* __restrict__ pmax,
+                                SbpDevState* st) {
     const int f = blockIdx.y;
     const FrameSlot fs = sbp_frame_of(ft, ft.ball_off ? ft.ball_off[f] : 0);
     float m = 0.0f;
+    bool bad = false;
     for (int i = fs.off + blockIdx.x * blockDim.x + threadIdx.x; i < fs.end;
-         i += gridDim.x * blockDim.x)
-        m = fmaxf(m, fabsf(p0[i]));
+         i += gridDim.x * blockDim.x) {
+        const float p = b.p0[i];
+        // x * 0 is 0 for every finite x and NaN for an infinity or a NaN
+        const float z = (b.x[i] + b.y[i] + b.z[i] + b.R[i] + p) * 0.0f;
+        bad |= z != 0.0f;
+        m = fmaxf(m, fabsf(p));
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(&pmax[f], __float_as_uint(m));
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) sbp_latch(st, SBP_ERR_NUMERIC);
 }
 
 // Round a float to the nearest int64. Values below 2^31 in magnitude (nearly
@@ -415,7 +425,7 @@ int sbp_launch_forward(sbp_array_s* a, const BallsDev& b, const int* n_dev, int 
         return SBP_ERR_CUDA;
     const FrameTable ft{1, nullptr, n_dev, n_cap};
     fwd_pmax_kernel<<<std::max(1, std::min(4 * a->sm_count, (n_cap + 255) / 256)), 256, 0,
-                      st>>>(b.p0, ft, &a->d_state->pmax_bits);
+                      st>>>(b, ft, &a->d_state->pmax_bits, a->d_state);
     if (sbp_cuda_check(cudaGetLastError(), "forward: pmax launch")) return SBP_ERR_CUDA;
     const unsigned grid = (unsigned)(((long long)n_cap + chunk - 1) / chunk * groups);
     fwd_group_for(g.wmode)<<<grid, kGroupWarps * 32, smem, st>>>(
@@ -449,7 +459,7 @@ int sbp_launch_forward_frames(sbp_array_s* a, const BallsDev& b, const int* n_de
         return SBP_ERR_CUDA;
     const FrameTable ft{F, a->d_frame_off, n_dev, total};
     const int pmax_blocks = std::max(1, std::min(4 * a->sm_count / F, total / F / 256 + 1));
-    fwd_pmax_kernel<<<dim3(pmax_blocks, F), 256, 0, st>>>(b.p0, ft, a->d_frame_pmax);
+    fwd_pmax_kernel<<<dim3(pmax_blocks, F), 256, 0, st>>>(b, ft, a->d_frame_pmax, a->d_state);
     if (sbp_cuda_check(cudaGetLastError(), "forward_frames: pmax launch")) return SBP_ERR_CUDA;
     const unsigned grid = (unsigned)(((long long)total + chunk - 1) / chunk * groups);
     fwd_group_for(g.wmode)<<<grid, kGroupWarps * 32, smem, st>>>(b, ft, a->d_sens, g, chunk,
@@ -467,10 +477,10 @@ int sbp_launch_forward_frames(sbp_array_s* a, const BallsDev& b, const int* n_de
 // ---------------------------------------------------------------------------
 // Forward without allocation (sbp_forward_static).
 //
-// Some callers cannot allocate device memory at all: code that runs where
-// cudaMalloc is forbidden or unsafe (inside a host callback or a stream
-// capture that must not change the allocation state, or a host process that
-// only borrows buffers from a larger framework that owns every allocation).
+// Some callers cannot allocate device memory at all: a host process that
+// only borrows buffers from a larger framework owning every allocation (a
+// serving runtime with its own memory pool), or one held to a fixed device
+// memory budget that a cudaMalloc behind its back could break.
 // For them this entry point renders the same traces as sbp_forward without
 // an array object: its scratch (the int64 trace accumulators and the state
 // words) lives in one file-scope device array that every GPU loading this
@@ -492,28 +502,75 @@ static __device__ __align__(256) unsigned long long g_static_scratch[kStaticStat
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mutex;
 unsigned long long* g_static_ptr[kMaxDevices] = {};  // device address, per device
+unsigned long long g_static_ctx[kMaxDevices] = {};   // ID of the context it was taken in
 int g_static_sms[kMaxDevices] = {};
 
-// One-time set-up per device (with that device current): the device address
-// of the scratch array. A host-side reference to g_static_scratch is only a
-// stand-in, never a usable device pointer, so kernels get this address.
+// The unique ID of the calling thread's current context (0 when none is
+// current), through the driver's cuCtxGetCurrent / cuCtxGetId reached from
+// the runtime. A context that is destroyed and created again (cudaDeviceReset,
+// or a framework that releases the primary context) gets a new ID.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+int current_ctx_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_cur = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_cur || !get_id) {
+        void* p1 = nullptr;
+        void* p2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p1, 12000, cudaEnableDefault,
+                                             &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &p2, 12000, cudaEnableDefault,
+                                             &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
+            sbp_set_error("forward_static: the driver offers no context ID");
+            return SBP_ERR_CUDA;
+        }
+        get_cur = reinterpret_cast<CtxGetCurrentFn>(p1);
+        get_id = reinterpret_cast<CtxGetIdFn>(p2);
+    }
+    CUcontext ctx = nullptr;
+    *id = 0;
+    if (get_cur(&ctx) != CUDA_SUCCESS) {
+        sbp_set_error("forward_static: cuCtxGetCurrent failed");
+        return SBP_ERR_CUDA;
+    }
+    if (ctx && get_id(ctx, id) != CUDA_SUCCESS) {
+        sbp_set_error("forward_static: cuCtxGetId failed");
+        return SBP_ERR_CUDA;
+    }
+    return SBP_OK;
+}
+
+// Set-up per device and context (with that device current): the device
+// address of the scratch array. A host-side reference to g_static_scratch is
+// only a stand-in, never a usable device pointer, so kernels get this
+// address. It is looked up again whenever the current context is not the one
+// it was taken in, since a new context loads the module, and with it the
+// array, at a new address.
 int static_scratch(int dev, unsigned long long** out, int* sms) {
     if (dev < 0 || dev >= kMaxDevices) {
         sbp_set_error("forward_static: device index out of range");
         return SBP_ERR_ARG;
     }
     std::lock_guard<std::mutex> lock(g_static_mutex);
-    if (!g_static_ptr[dev]) {
+    unsigned long long ctx = 0;
+    if (int e = current_ctx_id(&ctx)) return e;
+    if (!g_static_ptr[dev] || ctx == 0 || ctx != g_static_ctx[dev]) {
         void* p = nullptr;
         if (sbp_cuda_check(cudaGetSymbolAddress(&p, g_static_scratch),
                            "forward_static: scratch address"))
             return SBP_ERR_CUDA;
+        // the look-up made the device's context current if none was
+        if (int e = current_ctx_id(&ctx)) return e;
         int n = 0;
         if (sbp_cuda_check(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev),
                            "forward_static: SM count"))
             return SBP_ERR_CUDA;
         g_static_sms[dev] = n > 0 ? n : 1;
         g_static_ptr[dev] = static_cast<unsigned long long*>(p);
+        g_static_ctx[dev] = ctx;
     }
     *out = g_static_ptr[dev];
     *sms = g_static_sms[dev];
@@ -575,7 +632,7 @@ extern "C" int sbp_forward_static(const float* sensors_dev, int M, double c_mm_p
         return SBP_ERR_CUDA;
     const FrameTable ft{1, nullptr, n_dev, n_cap};
     fwd_pmax_kernel<<<std::max(1, std::min(4 * sms, (n_cap + 255) / 256)), 256, 0, st>>>(
-        b.p0, ft, &state->pmax_bits);
+        b, ft, &state->pmax_bits, state);
     if (sbp_cuda_check(cudaGetLastError(), "forward_static: pmax launch")) return SBP_ERR_CUDA;
     const unsigned grid = (unsigned)(((long long)n_cap + chunk - 1) / chunk * groups);
     fwd_group_for(g.wmode)<<<grid, kGroupWarps * 32, smem, st>>>(b, ft, sensors_dev, g, chunk,

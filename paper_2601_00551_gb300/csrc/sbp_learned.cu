@@ -2,7 +2,7 @@
 // Algorithm 1; the paper itself initialises at random and filters by zero
 // gradients, Section 4.2):
 //   * delay-and-sum volume of the measured traces on a voxel grid;
-//   * a small 3D CNN on that volume, 1 -> 16 -> 32 -> 32 channels of 3x3x3
+//   * a small 3D CNN on that volume, 1 -> 16 -> 32 -> 64 channels of 3x3x3
 //     convolutions with ReLU (tcgen05 implicit GEMMs, sbp_cnn.cu) and a
 //     1x1x1 head with two outputs per voxel: the logit of "a source lies
 //     here" and its pressure;
@@ -53,14 +53,14 @@ struct sbp_cnn_s {
     float* p = nullptr;  // [kParams] masters, then m, v, grads: 4 blocks
     __nv_bfloat16* w1 = nullptr;   // [16][64]
     __nv_bfloat16* w2 = nullptr;   // [32][padded_k(16)]
-    __nv_bfloat16* w3 = nullptr;   // [32][padded_k(32)]
+    __nv_bfloat16* w3 = nullptr;   // [64][padded_k(32)]
     __nv_bfloat16* w2t = nullptr;  // dgrad of conv2: [16][padded_k(32)]
-    __nv_bfloat16* w3t = nullptr;  // dgrad of conv3: [32][padded_k(32)]
+    __nv_bfloat16* w3t = nullptr;  // dgrad of conv3: [32][padded_k(64)]
     __nv_bfloat16* x0 = nullptr;   // [V] scaled input
     __nv_bfloat16* h1 = nullptr;   // [V][16]
     __nv_bfloat16* h2 = nullptr;   // [V][32]
-    __nv_bfloat16* h3 = nullptr;   // [V][32]
-    __nv_bfloat16* g3 = nullptr;   // [V][32] gradient before conv3's ReLU
+    __nv_bfloat16* h3 = nullptr;   // [V][64]
+    __nv_bfloat16* g3 = nullptr;   // [V][64] gradient before conv3's ReLU
     __nv_bfloat16* g2 = nullptr;   // [V][32]
     __nv_bfloat16* g1 = nullptr;   // [V][16]
     float* out = nullptr;          // [V][2]

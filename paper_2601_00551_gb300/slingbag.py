@@ -23,6 +23,9 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libslingbag.so")
 
 SBP_OK = 0
+# status codes of include/slingbag.h
+SBP_ERR_ARG, SBP_ERR_CUDA, SBP_ERR_CAPACITY = -1, -2, -3
+SBP_ERR_LEVEL, SBP_ERR_TIMEOUT, SBP_ERR_NUMERIC = -4, -5, -6
 W_MODES = {"clamp": 0, "none": 1, "cos": 2}
 MASK_P0, MASK_R, MASK_XYZ, MASK_ALL = 1, 2, 4, 7
 SOFTPLUS_R = 8  # optimise R through R = softplus(a) (positivity-constrained refinement)
@@ -638,23 +641,32 @@ def forward_static(sensors: torch.Tensor, c: float, dt_us: float, T_k: int,
                    balls: torch.Tensor, n: torch.Tensor | None = None,
                    out: torch.Tensor | None = None, weight_mode: str = "clamp") -> torch.Tensor:
     """Traces S (M, T_k) without an array object (sbp_forward_static): the
-    library allocates nothing, so the call may sit in a stream capture.
-    sensors: (6, M) float32 CUDA tensor, positions then unit normals; balls:
-    (5, N); n: None (all N balls) or an int32 CUDA tensor holding the live
-    count; M * T_k must stay within the library's static scratch (2^21 cells)."""
+    library allocates no device memory for the call (`out` is allocated here
+    when not given). sensors: (6, M) float32 CUDA tensor, positions then unit
+    normals; balls: (5, N); n: None (all N balls) or an int32 CUDA tensor
+    holding the live count; M * T_k must stay within the library's static
+    scratch (2^21 cells). Every tensor must sit on the current CUDA device."""
     if sensors.dim() != 2 or sensors.shape[0] != 6 or sensors.dtype != torch.float32 or \
             not sensors.is_cuda or not sensors.is_contiguous():
         raise ValueError("sensors must be a contiguous (6, M) float32 CUDA tensor")
     M = sensors.shape[1]
     if out is None:
         out = torch.empty((M, int(T_k)), dtype=torch.float32, device=sensors.device)
-    if out.shape != (M, int(T_k)) or out.dtype != torch.float32 or not out.is_contiguous():
-        raise ValueError(f"out must be a contiguous ({M}, {T_k}) float32 tensor")
-    if n is not None and (n.dtype != torch.int32 or not n.is_cuda):
+    if out.shape != (M, int(T_k)) or out.dtype != torch.float32 or not out.is_cuda or \
+            not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous ({M}, {T_k}) float32 CUDA tensor")
+    if n is not None and (n.dtype != torch.int32 or not n.is_cuda or n.numel() < 1):
         raise ValueError("n must be an int32 CUDA tensor")
+    rows = _rows(balls)
+    devs = {t.device for t in (sensors, balls, out) + ((n,) if n is not None else ())}
+    if len(devs) != 1:
+        raise ValueError("sensors, balls, out and n must be on one CUDA device")
+    if sensors.device.index != torch.cuda.current_device():
+        raise ValueError("the tensors must be on the current CUDA device "
+                         f"(cuda:{torch.cuda.current_device()}), not {sensors.device}")
     lib = load_library()
     _check("sbp_forward_static", lib.sbp_forward_static(
-        _dptr(sensors), M, float(c), float(dt_us), int(T_k), W_MODES[weight_mode], _rows(balls),
+        _dptr(sensors), M, float(c), float(dt_us), int(T_k), W_MODES[weight_mode], rows,
         _dptr(n), balls.shape[1], _dptr(out), _stream()))
     return out
 

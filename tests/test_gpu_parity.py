@@ -114,6 +114,27 @@ def test_forward_edge_cases(sb):
     assert arr.inside_pairs() > 0
 
 
+def test_forward_latches_non_finite_balls(sb):
+    """A live ball with a NaN or infinite value latches SBP_ERR_NUMERIC (read
+    and cleared by sbp_sync_status); the same ball past the live count does
+    not."""
+    wl = workloads.tiny(M=8, T=256)
+    b = wl.init.stack()[:, :300].copy()
+    arr = make_array(sb, wl, (1,), b.shape[1])
+    balls = torch.from_numpy(b).cuda()
+    arr.forward(balls)
+    assert arr.sync_status() == 0
+    for row, bad in ((4, np.nan), (0, np.inf), (3, -np.inf)):
+        b2 = b.copy()
+        b2[row, 123] = bad
+        bd = torch.from_numpy(b2).cuda()
+        arr.forward(bd)
+        assert arr.sync_status() == sb.SBP_ERR_NUMERIC, (row, bad)
+        assert arr.sync_status() == 0  # cleared by the read
+        arr.forward(bd, n=torch.tensor([100], dtype=torch.int32, device="cuda"))
+        assert arr.sync_status() == 0
+
+
 def test_forward_vessel_sampled_sensors(sb):
     """Full-size vessel workload (200k balls, 512 sensors, T = 4096 at 40 MHz and
     the 10 / 20 MHz levels) in the benchmark's launch configuration; the oracle
@@ -314,6 +335,10 @@ def test_zero_gradient_filter_vessel(sb):
     assert (gpu_keep ^ ref_keep) <= amb_set
     assert n_new == len(gpu_keep)
     assert len(amb_set) <= 1e-3 * n
+    # the compacted cloud, element by element and in order: the oracle's
+    # survivors, with the GPU's own decision for the ambiguous balls
+    order = np.array(sorted((ref_keep - amb_set) | (gpu_keep & amb_set)), dtype=np.int64)
+    np.testing.assert_array_equal(balls[:, :n_new].cpu().numpy(), b[:, order])
 
 
 def _grow_case(rng, n):

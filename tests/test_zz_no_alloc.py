@@ -1,6 +1,7 @@
 """sbp_forward_static, the forward for callers that cannot allocate device
-memory (inside a stream capture or a host callback, or a host that borrows all
-its buffers), against the regular sbp_forward through the C ABI.
+memory (a process that borrows every buffer from a framework owning all
+allocations, or one held to a fixed device-memory budget), against the
+regular sbp_forward through the C ABI.
 
 Collected last on purpose: it uses the library's one static scratch array,
 and the rest of the suite has already run if it fails."""
@@ -41,23 +42,49 @@ def sensors_6xM(pos, nrm):
     return np.concatenate([pos.T.astype(np.float32), n.T.astype(np.float32)]).copy()
 
 
-def test_static_forward_matches_regular_forward_twice(sb):
+def level_dt(c, f, fs):
+    """A sampling interval dt with c * dt equal, in double, to the array's own
+    spacing c * f / fs, so that both entry points round the same h."""
+    h = c * f / fs
+    dt = h / c
+    for _ in range(8):
+        if c * dt == h:
+            return dt
+        dt = np.nextafter(dt, np.inf if c * dt < h else -np.inf)
+    raise AssertionError("no dt reproduces the level spacing")
+
+
+@pytest.mark.parametrize("wmode", ["clamp", "none", "cos"])
+def test_static_forward_matches_regular_forward_twice(sb, wmode):
+    """Both entry points run the same exact-integer kernels, so the traces
+    agree bit for bit: for every weight mode, at two levels, with all balls
+    and with a ragged live count held on the device, on two calls in a row
+    (which share, and clear, the static scratch)."""
     wl = workloads.tiny()
     b = wl.init.stack()
     n = b.shape[1]
     arr = sb.SensorArray(wl.sensors.pos, wl.sensors.normal, wl.c, wl.fs_mhz, wl.T, (4, 1),
-                         n_cap=n)
+                         n_cap=n, weight_mode=wmode)
     balls = torch.from_numpy(b).cuda()
     sens = torch.from_numpy(sensors_6xM(wl.sensors.pos, wl.sensors.normal)).cuda()
+    ragged = torch.tensor([n - 37], dtype=torch.int32, device="cuda")
     for k, f in enumerate((4, 1)):
         arr.set_sampling_level(k)
-        ref = arr.forward(balls).cpu().numpy()
         Tk = wl.T // f
-        for _ in range(2):  # two calls in a row share (and clear) the static scratch
-            out = torch.full((wl.sensors.M, Tk), float("nan"), device="cuda")
-            got = sb.forward_static(sens, wl.c, f / wl.fs_mhz, Tk, balls, out=out).cpu().numpy()
-            assert np.all(np.isfinite(got))
-            assert rel_l2(got, ref) <= TRACE_TOL
+        dt = level_dt(wl.c, f, wl.fs_mhz)
+        for n_dev in (None, ragged):
+            ref = arr.forward(balls, n=n_dev).cpu().numpy()
+            assert np.count_nonzero(ref) > 0
+            for _ in range(2):
+                out = torch.full((wl.sensors.M, Tk), float("nan"), device="cuda")
+                got = sb.forward_static(sens, wl.c, dt, Tk, balls, n=n_dev, out=out,
+                                        weight_mode=wmode).cpu().numpy()
+                np.testing.assert_array_equal(got, ref)
+        # the ragged count leaves the last 37 balls out
+        full = arr.forward(balls).cpu().numpy()
+        part = arr.forward(balls, n=ragged).cpu().numpy()
+        assert not np.array_equal(full, part)
+        assert rel_l2(part, arr.forward(balls[:, :n - 37].contiguous()).cpu().numpy()) <= TRACE_TOL
 
 
 def test_static_forward_rejects_sizes_beyond_its_scratch(sb):
@@ -70,3 +97,17 @@ def test_static_forward_rejects_sizes_beyond_its_scratch(sb):
                                 None, 4, out.data_ptr(), None)
     assert rc == -1
     assert b"exceeds the static scratch" in lib.sbp_last_error()
+
+
+def test_static_forward_binding_rejects_host_buffers(sb):
+    """An output or a live count in host memory is refused before the
+    library is called (the kernels would write through a host pointer)."""
+    wl = workloads.tiny(M=8, T=64)
+    sens = torch.from_numpy(sensors_6xM(wl.sensors.pos, wl.sensors.normal)).cuda()
+    balls = torch.from_numpy(wl.init.stack()).cuda()
+    with pytest.raises(ValueError):
+        sb.forward_static(sens, wl.c, 0.025, 64, balls, out=torch.zeros((8, 64)))
+    with pytest.raises(ValueError):
+        sb.forward_static(sens, wl.c, 0.025, 64, balls, n=torch.tensor([3], dtype=torch.int32))
+    with pytest.raises(ValueError):
+        sb.forward_static(sens, wl.c, 0.025, 64, balls.cpu())
