@@ -84,6 +84,10 @@ def parse_args(argv=None):
                          "several minutes)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned initial proposal (CNN training and comparison)")
+    ap.add_argument("--profile-frames", action="store_true",
+                    help="only one batched step over the 32 frames after two warm-up steps, "
+                         "inside an NVTX range named frames_step (a short command for a "
+                         "profiler)")
     ap.add_argument("--large-calls", action="store_true",
                     help="only time one forward and one adjoint call of the 1M-ball initial "
                          "cloud per level, default and tuned tiles")
@@ -1077,7 +1081,7 @@ def learned_large(n_train=2000, epochs=4, n_phantom=100_000, grid=64, full_iters
     }
 
 
-def batched_frames(args, sb, dev, steps=8, warmup=3):
+def batched_frames(args, sb, dev, steps=8, warmup=3, profile=False):
     """Batched dynamic imaging (32 frames of the moving vessel phantom, 20k-200k
     balls per frame, 256 sensors, 10/20/40 MHz, T = 512/1024/2048): the same
     step as the main measurement (zero-gradient filtering, then one
@@ -1166,6 +1170,20 @@ def batched_frames(args, sb, dev, steps=8, warmup=3):
     restore_batched()
     arr.set_sampling_level_frames(nl - 1)
     chunk, split = arr.autotune_frames(balls, n_dev)
+    if profile:  # a short command for a profiler: warm-up, then one marked step
+        for _ in range(2):
+            restore_batched()
+            run_batched()
+        restore_batched()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("frames_step")
+        run_batched()
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        ok = arr.sync_status() == 0
+        arr.close()
+        single.close()
+        return {"profile_frames": True, "tiles": [chunk, split], "status_ok": ok}
 
     def capture(restore, run):
         restore()
@@ -1704,6 +1722,17 @@ def main(argv=None):
     args = parse_args(argv)
     if args.profile_large:
         print(json.dumps(profile_large()))
+        return 0
+    if args.profile_frames:
+        import torch
+
+        import __graft_entry__ as ge
+
+        ge.build()
+        from paper_2601_00551_gb300 import slingbag as sb
+
+        torch.cuda.set_device(0)
+        print(json.dumps(batched_frames(args, sb, torch.device("cuda", 0), profile=True)))
         return 0
     if args.large_calls:
         import torch

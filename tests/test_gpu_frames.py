@@ -1,5 +1,6 @@
 """Batched frames: every batched step equals the single-cloud step applied to
-each frame, and a frame's traces match the FP64 oracle."""
+each frame, and every frame matches the FP64 oracle on its own (traces,
+gradients, filter/grow and the whole reconstruction loop)."""
 import numpy as np
 import pytest
 import torch
@@ -189,3 +190,92 @@ def test_reconstruct_frames_replays_in_cuda_graph(sb):
         for f in range(F):
             m = int(n_dev[f].item())
             assert torch.equal(packed[:, off[f]:off[f] + m], eager[0][:, off[f]:off[f] + m])
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_frames_match_the_oracle_frame_by_frame(sb):
+    """Every frame of the batched calls against the FP64 oracle on that
+    frame alone (frames are independent reconstructions): traces and all
+    five gradients at both levels, one filter/grow pass (counts, order, R,
+    p0, gradients and carried state bit for bit, centres to 2e-6 mm), and a
+    whole batched reconstruction (zero-gradient filtering, coarse and fine
+    stages with growth): ball counts per iteration, losses and final clouds."""
+    wl, arr, single, off, packed, n_dev, clouds = setup(sb)
+    F, M = len(COUNTS), wl.sensors.M
+    pos, nrm = wl.sensors.pos, wl.sensors.normal
+    rng = np.random.default_rng(11)
+    nt = max(1, oracle.num_procs())
+    for k, f_k in enumerate((2, 1)):
+        arr.set_sampling_level(k)
+        Tk = arr.Tk
+        dt = f_k / wl.fs_mhz
+        S = arr.forward_frames(packed, n_dev).cpu().numpy()
+        G = rng.normal(size=(F, M, Tk)).astype(np.float32)
+        g = arr.adjoint_frames(packed, n_dev, torch.from_numpy(G).cuda()).cpu().numpy()
+        for f, b in enumerate(clouds):
+            ref = oracle.forward(b, pos, nrm, wl.c, dt, Tk, threads=nt)
+            assert rel_l2(S[f], ref) <= 1e-5, (k, f)
+            gref = oracle.adjoint(b, pos, nrm, wl.c, dt, Tk, G[f].astype(np.float64),
+                                  threads=nt)
+            n = b.shape[1]
+            for c in range(5):
+                assert rel_l2(g[c, off[f]:off[f] + n], gref[c]) <= 1e-4, (k, f, c)
+
+    # one filter/grow pass with duplication, frame by frame against oracle.grow
+    total = packed.shape[1]
+    grads = rng.normal(size=(5, total)).astype(np.float32)
+    grads[:, ::7] = 0.0
+    extra = rng.normal(size=(4, total)).astype(np.float32)
+    P0 = packed.clone()
+    Gd = torch.from_numpy(grads).cuda()
+    Ed = torch.from_numpy(extra).cuda()
+    nd = n_dev.clone()
+    gp = dict(seed=4321, R_max=0.3, duplicate=True, g_dup=1.5)
+    arr.filter_grow_frames(P0, Gd, nd, mode=sb.GROW, grow=sb.GrowParams(**gp), extra=[Ed])
+    assert arr.sync_status() == 0
+    counts = nd.cpu().numpy()
+    for f, b in enumerate(clouds):
+        n = b.shape[1]
+        s = slice(off[f], off[f] + n)
+        nb, ng, ne, _ = oracle.grow(b, grads[:, s], extra[:, s], oracle.GrowParams(**gp))
+        m = nb.shape[1]
+        assert counts[f] == m, f
+        t = slice(off[f], off[f] + m)
+        Bo = P0[:, t].cpu().numpy()
+        np.testing.assert_array_equal(Bo[3:], nb[3:])
+        np.testing.assert_allclose(Bo[:3], nb[:3], rtol=0, atol=2e-6)
+        np.testing.assert_array_equal(Gd[:, t].cpu().numpy(), ng)
+        np.testing.assert_array_equal(Ed[:, t].cpu().numpy(), ne)
+
+    # a whole batched reconstruction against the oracle's loop per frame
+    y_frames = []
+    for f in range(F):
+        truth = workloads.uniform_balls(200, 2.0, 0.05, 0.2, 0.5, 1.0, seed=170 + f).stack()
+        y = oracle.forward(truth, pos, nrm, wl.c, 1 / wl.fs_mhz, wl.T, threads=nt)
+        y_frames.append(workloads.add_noise(y.astype(np.float32), seed=180 + f))
+    Y = torch.from_numpy(np.stack(y_frames)).cuda()
+    st_o = [oracle.Stage(0, 2, 3, True, False), oracle.Stage(1, 2, 7, True, True)]
+    st_g = [sb.Stage(s.level, s.iterations, s.grad_mask, s.grow, s.duplicate) for s in st_o]
+    grow = dict(p_min=1e-3, R_min=0.02, R_max=0.3, g_dup=2.0, seed=31)
+    loss = torch.zeros(4 * F, dtype=torch.float64, device="cuda")
+    nlog = torch.zeros(4 * F, dtype=torch.int32, device="cuda")
+    arr.reconstruct_frames(Y, packed, n_dev, st_g, grow=sb.GrowParams(**grow), loss_log=loss,
+                           n_log=nlog)
+    assert arr.sync_status() == 0
+    loss = loss.cpu().numpy().reshape(4, F)
+    nlog = nlog.cpu().numpy().reshape(4, F)
+    for f, b in enumerate(clouds):
+        bo, losses, cnt = oracle.reconstruct(b, pos, nrm, wl.c, wl.fs_mhz, wl.T, (2, 1),
+                                             y_frames[f], st_o,
+                                             grow_params=oracle.GrowParams(**grow), threads=nt)
+        np.testing.assert_array_equal(nlog[:, f], cnt, err_msg=f"frame {f}")
+        np.testing.assert_allclose(loss[:, f], losses, rtol=1e-4, err_msg=f"frame {f}")
+        m = int(n_dev[f].item())
+        assert m == bo.shape[1], f
+        np.testing.assert_allclose(packed[:, off[f]:off[f] + m].cpu().numpy(), bo, rtol=0,
+                                   atol=1e-4, err_msg=f"frame {f}")
