@@ -88,6 +88,9 @@ def parse_args(argv=None):
                     help="only one batched step over the 32 frames after two warm-up steps, "
                          "inside an NVTX range named frames_step (a short command for a "
                          "profiler)")
+    ap.add_argument("--learned-batched", action="store_true",
+                    help="only the learned proposal + batched reconstruction against the plain "
+                         "method run to convergence (frames of the batched workload)")
     ap.add_argument("--large-calls", action="store_true",
                     help="only time one forward and one adjoint call of the 1M-ball initial "
                          "cloud per level, default and tuned tiles")
@@ -676,6 +679,10 @@ def run_native(args, rank, world, local):
             result["gaussian_radiator"] = {"error": f"{type(exc).__name__}: {exc}"}
         vessel_y = vctx.y_host
         vctx.close()
+        try:
+            result["unsorted_vessel"] = unsorted_vessel(sb, dev)
+        except Exception as exc:  # keep the main measurement if this part fails
+            result["unsorted_vessel"] = {"error": f"{type(exc).__name__}: {exc}"}
         del vctx
         torch.cuda.empty_cache()
         if not args.no_frames:
@@ -683,6 +690,11 @@ def run_native(args, rank, world, local):
                 result["batched_frames"] = batched_frames(args, sb, dev)
             except Exception as exc:  # keep the main measurement if this part fails
                 result["batched_frames"] = {"error": f"{type(exc).__name__}: {exc}"}
+        if not args.no_learned:
+            try:
+                result["learned_plus_batched"] = learned_plus_batched(sb, dev)
+            except Exception as exc:  # keep the main measurement if this part fails
+                result["learned_plus_batched"] = {"error": f"{type(exc).__name__}: {exc}"}
         if not args.no_envelope:
             try:
                 result["envelope_init_voxel"] = envelope_init_voxel(sb, dev)
@@ -938,6 +950,240 @@ def learned_init(sb, arr, wl, y_full, init, plain_seconds, dev, n_train=96, epoc
             "learned_seconds": total_final,
             "speedup": (plain_full["elapsed_seconds"] / total_final) if total_final else None,
         },
+    }
+
+
+def run_to_convergence(sb, arr, y_full, init, n0, segs, zero_filter, seg, max_iter, rel,
+                       tol=1e-4, settle=180):
+    """Runs `seg` iterations per (level, mask) of `segs` through sbp_reconstruct
+    from (init, n0) until the relative residual rel() changes by less than
+    `tol` (relative) over one segment, the test checked once the schedule has
+    run `settle` iterations (the end of its coarse passes), or until
+    `max_iter`. Device seconds of the reconstruction calls only."""
+    import torch
+
+    balls = init.clone()
+    n_dev = torch.tensor([n0], dtype=torch.int32, device=init.device)
+    t, it, prev, r, converged = 0.0, 0, None, 1.0, False
+    for j, (level, mask) in enumerate(segs):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        arr.reconstruct(y_full, balls, n_dev, [sb.Stage(level, seg, mask, True, False)],
+                        zero_grad_mode=(sb.KEEP_NEG if (zero_filter and j == 0) else None),
+                        zero_grad_level=0, grow=sb.GrowParams(seed=1000 + j, **GROW))
+        b.record()
+        torch.cuda.synchronize()
+        t += a.elapsed_time(b) / 1e3
+        it += seg
+        r = rel(balls, n_dev)
+        if it >= settle and prev is not None and abs(prev - r) <= tol * prev:
+            converged = True
+            break
+        prev = r
+        if it >= max_iter:
+            break
+    # SBP_ERR_CAPACITY (-3) here means growth ran out of room at some point
+    # and was skipped for that iteration (the cloud is left unchanged)
+    return {"seconds": t, "iterations": it, "final_rel_residual": r, "converged": converged,
+            "balls": int(n_dev.item()), "status": int(arr.sync_status())}
+
+
+def learned_plus_batched(sb, dev, frames=(0, 4, 8, 12, 16, 20, 24, 28), n_train=96, epochs=8,
+                         grid=64, seg=10, max_iter=3000, lr=1e-3, pos_weight=10.0,
+                         threshold=0.25, per_voxel=8, prop_cap=300_000, rand_frac=0.5):
+    """The second target: learned initial proposal plus batched reconstruction
+    against the plain method run to convergence, on frames of the batched
+    workload (moving vessel phantom, 256 sensors, 10 / 20 / 40 MHz,
+    T = 2048; the listed frames of the 32).
+
+    plain    per frame, its own sbp_reconstruct calls from the frame's
+             uniform random cloud: zero-gradient filtering, then the Pro
+             schedule, until the relative residual at 40 MHz changes by less
+             than 1e-4 over 10 iterations (after the schedule's coarse
+             passes), at most `max_iter` iterations. Its final residual r_f
+             is the frame's target.
+    learned  a CNN trained on `n_train` seeded phantoms measured by the same
+             array; per frame the delay-and-sum volume and the proposal
+             (`per_voxel` seeded balls of radius h / 4 in every voxel whose
+             occupancy probability exceeds `threshold`), joined by a uniform
+             random cloud of `rand_frac` of the frame's plain initial count
+             (the plain method as the fallback where the network sees
+             nothing); then ONE sbp_reconstruct_frames call per 10-iteration
+             segment over all frames (zero-gradient filtering in the first,
+             then the Pro schedule) until every frame's residual is at or
+             below its r_f.
+    Times are device seconds; the learned time includes the delay-and-sum
+    volumes and proposals (not the training, done once per array). The
+    residual checks between segments are not timed."""
+    import torch
+
+    import workloads
+
+    fw = workloads.frames()
+    F = len(frames)
+    M, nl, fine = fw.sensors.M, len(fw.levels), len(fw.levels) - 1
+    half = fw.half
+    dims = (grid, grid, grid)
+    h = 2.0 * half / grid
+    origin = (-half, -half, -half)
+    V = grid ** 3
+    align = 1024
+    cap1 = max(fw.inits[f].n for f in frames)
+    single = sb.SensorArray(fw.sensors.pos, fw.sensors.normal, fw.c, fw.fs_mhz, fw.T, fw.levels,
+                            n_cap=max(4 * cap1, fw.truths[0].n))
+    single.set_sampling_level(fine)
+    Y = []
+    for f in frames:
+        B = torch.from_numpy(fw.truths[f].stack()).to(dev)
+        Y.append(torch.from_numpy(workloads.add_noise(single.forward(B).cpu().numpy(),
+                                                      seed=3000 + f)).to(dev))
+    ynorm = [float((y.double() ** 2).sum().item()) for y in Y]
+
+    # plain: per frame to convergence
+    plain = []
+    for q, f in enumerate(frames):
+        b0 = fw.inits[f]
+        init = torch.zeros((5, 4 * cap1), dtype=torch.float32, device=dev)
+        init[:, :b0.n] = torch.from_numpy(b0.stack()).to(dev)
+
+        def rel(balls, n_dev, q=q):
+            single.set_sampling_level(fine)
+            S = single.forward(balls, n=n_dev)
+            _, L = single.residual(S, Y[q])
+            return float(L.item()) / ynorm[q]
+
+        plain.append(run_to_convergence(sb, single, Y[q], init, b0.n, pro_segments(nl, seg),
+                                        True, seg, max_iter, rel))
+    plain_s = sum(p["seconds"] for p in plain)
+
+    # learned: train on phantoms measured by the same array
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5)
+    scratch = torch.zeros(V + 1, dtype=torch.int64, device=dev)
+
+    def targets(B):
+        ones = torch.ones(B.shape[1], dtype=torch.float32, device=dev)
+        cnt = sb.voxelize(B, origin, h, dims, values=ones, scratch=scratch).reshape(-1).clone()
+        psum = sb.voxelize(B, origin, h, dims, scratch=scratch).reshape(-1)
+        occ = (cnt > 0.5).float()
+        return occ, torch.where(occ > 0, psum / cnt.clamp(min=1.0), torch.zeros_like(psum))
+
+    t0 = time.perf_counter()
+    vols, occs, p0s = [], [], []
+    for i in range(n_train):
+        ph = workloads.vessel_tree(fw.truths[0].n, half=half, seed=5000 + i)
+        B = torch.from_numpy(ph.stack()).to(dev)
+        S = single.forward(B)
+        S = S + torch.randn(S.shape, generator=gen, device=dev) * (0.01 * S.abs().max())
+        vols.append(single.das_volume(S.contiguous(), origin, h, dims).reshape(-1).clone())
+        occ, p0t = targets(B)
+        occs.append(occ)
+        p0s.append(p0t)
+    torch.cuda.synchronize()
+    data_s = time.perf_counter() - t0
+    net = sb.VolumeCNN(dims, seed=1)
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    for _ in range(epochs):
+        for i in rng.permutation(n_train):
+            net.train_step(vols[i], occs[i], p0s[i], lr=lr, pos_weight=pos_weight)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    if sb.cnn_status() != 0:
+        raise RuntimeError("a tensor-core wait gave up during training")
+
+    # proposals of every frame (timed: delay-and-sum + CNN + compaction)
+    props = [torch.zeros((5, prop_cap), dtype=torch.float32, device=dev) for _ in range(F)]
+    n_props = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in range(F)]
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    for rep in range(2):  # the first pass allocates the proposal scratch
+        a.record()
+        for q in range(F):
+            vol = single.das_volume(Y[q], origin, h, dims).reshape(-1)
+            net.propose(vol, origin, h, threshold=threshold, seed=7 + q, R=0.25 * h,
+                        p_range=(0.05, 1.0), out=props[q], n_dev=n_props[q], per_voxel=per_voxel)
+        b.record()
+        torch.cuda.synchronize()
+    infer_s = a.elapsed_time(b) / 1e3
+    counts = [int(n.item()) for n in n_props]
+    prec, rec = [], []
+    for q, f in enumerate(frames):
+        occ_t, _ = targets(torch.from_numpy(fw.truths[f].stack()).to(dev))
+        zthr = float(np.log(threshold / (1.0 - threshold)))
+        pred = net.forward(single.das_volume(Y[q], origin, h, dims).reshape(-1))[:, 0] > zthr
+        tp = float((pred & (occ_t > 0)).sum().item())
+        prec.append(tp / max(1.0, float(pred.sum().item())))
+        rec.append(tp / max(1.0, float(occ_t.sum().item())))
+    net.close()
+
+    # the fallback: a uniform random cloud beside each proposal (set-up, not
+    # timed, like the plain method's random initial cloud)
+    rand = [workloads.uniform_balls(int(rand_frac * fw.inits[f].n), half, 0.05, 0.2, 0.0, 1.0,
+                                    seed=7000 + f) for f in frames]
+    rand = [r.take(workloads.morton_order(r, half)) for r in rand]
+    starts = [c + r.n for c, r in zip(counts, rand)]
+    # one batched reconstruction over all frames until each reaches its r_f
+    caps = [max(2 * align, 2 * s_, 2 * p["balls"]) for s_, p in zip(starts, plain)]
+    farr = sb.SensorArray(fw.sensors.pos, fw.sensors.normal, fw.c, fw.fs_mhz, fw.T, fw.levels,
+                          n_cap=sum((c + align - 1) // align * align for c in caps))
+    off = farr.set_frames(caps)
+    balls = torch.zeros((5, int(off[-1])), dtype=torch.float32, device=dev)
+    for q in range(F):
+        balls[:, off[q]:off[q] + counts[q]] = props[q][:, :counts[q]]
+        balls[:, off[q] + counts[q]:off[q] + starts[q]] = torch.from_numpy(rand[q].stack()).to(dev)
+    n_dev = torch.tensor(starts, dtype=torch.int32, device=dev)
+    Yf = torch.stack(Y).contiguous()
+    ynorm_t = torch.tensor(ynorm, dtype=torch.float64, device=dev)
+    target = torch.tensor([p["final_rel_residual"] for p in plain], dtype=torch.float64,
+                          device=dev)
+    losses = torch.zeros(F, dtype=torch.float64, device=dev)
+    t, it, done, r = 0.0, 0, False, None
+    for j, (level, mask) in enumerate(pro_segments(nl, seg)):
+        a.record()
+        farr.reconstruct_frames(Yf, balls, n_dev, [sb.Stage(level, seg, mask, True, False)],
+                                zero_grad_mode=(sb.KEEP_NEG if j == 0 else None),
+                                zero_grad_level=0, grow=sb.GrowParams(seed=2000 + j, **GROW))
+        b.record()
+        torch.cuda.synchronize()
+        t += a.elapsed_time(b) / 1e3
+        it += seg
+        farr.set_sampling_level_frames(fine)
+        S = farr.forward_frames(balls, n_dev)
+        farr.residual_frames(S, Yf, loss=losses)
+        r = (losses / ynorm_t).cpu().numpy()
+        if bool(np.all(r <= target.cpu().numpy())):
+            done = True
+            break
+        if it >= 2 * max_iter:
+            break
+    status = farr.sync_status()
+    if status not in (0, sb.SBP_ERR_CAPACITY) or single.sync_status() not in (0, sb.SBP_ERR_CAPACITY):
+        raise RuntimeError("device status latched in the learned + batched arm: " +
+                           sb.load_library().sbp_last_error().decode())
+    farr.close()
+    single.close()
+    learned_s = t + infer_s if done else None
+    return {
+        "workload": fw.name, "frames": list(frames), "sensors": M,
+        "plain": {"seconds": plain_s, "per_frame": plain,
+                  "all_converged": all(p["converged"] for p in plain),
+                  "rule": "relative residual change < 1e-4 over 10 iterations, checked after "
+                          "the Pro schedule's coarse passes (180 iterations)"},
+        "learned": {"train_phantoms": n_train, "epochs": epochs, "grid": list(dims),
+                    "threshold": threshold, "balls_per_voxel": per_voxel,
+                    "data_seconds": data_s, "train_seconds": train_s,
+                    "inference_seconds": infer_s, "proposal_balls": counts,
+                    "random_balls": [r.n for r in rand],
+                    "precision_mean": float(np.mean(prec)), "recall_mean": float(np.mean(rec)),
+                    "reconstruction_seconds": t, "iterations": it,
+                    "final_rel_residual": r.tolist() if r is not None else None,
+                    "reached_every_target": done, "status": int(status),
+                    "balls": n_dev.cpu().tolist()},
+        "learned_plus_batched_seconds": learned_s,
+        "speedup_vs_plain": (plain_s / learned_s) if learned_s else None,
+        "target": ">= 2x faster to the plain method's final residual",
     }
 
 
@@ -1411,6 +1657,59 @@ def large_config(sb, dev, reps=3, tune=True):
     return out
 
 
+def unsorted_vessel(sb, dev, steps=5, warmup=2):
+    """The vessel step (zero-gradient filtering, then one iteration per level
+    through sbp_reconstruct) on the initial cloud in its random generation
+    order, with and without the library's spatial sort (sort time
+    included), beside the same cloud pre-sorted on the host. Device ms per
+    step, L2 flushed before each."""
+    import torch
+
+    import workloads
+
+    out = {}
+    for name, sort_host, sort_dev in (("random_order_sorted_on_device", False, True),
+                                      ("random_order_unsorted", False, False),
+                                      ("host_morton_order", True, False)):
+        wl = workloads.vessel(sort=sort_host)
+        n0, M = wl.init.n, wl.sensors.M
+        arr = sb.SensorArray(wl.sensors.pos, wl.sensors.normal, wl.c, wl.fs_mhz, wl.T,
+                             wl.levels, n_cap=2 * n0)
+        arr.set_sampling_level(len(wl.levels) - 1)
+        y = workloads.add_noise(arr.forward(torch.from_numpy(wl.truth.stack()).to(dev))
+                                .cpu().numpy())
+        Y = torch.from_numpy(y).to(dev)
+        init = torch.zeros((5, 2 * n0), dtype=torch.float32, device=dev)
+        init[:, :n0] = torch.from_numpy(wl.init.stack()).to(dev)
+        balls = torch.empty_like(init)
+        n_dev = torch.empty(1, dtype=torch.int32, device=dev)
+        n_log = torch.zeros(len(wl.levels), dtype=torch.int32, device=dev)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        stages = stages_for(sb, wl)
+        gp = sb.GrowParams(seed=1000, **GROW)
+        ts = []
+        for it in range(warmup + steps):
+            balls.copy_(init)
+            n_dev.fill_(n0)
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            arr.reconstruct(Y, balls, n_dev, stages, grow=gp, n_log=n_log, spatial_sort=sort_dev)
+            b.record()
+            if it >= warmup:
+                ts.append((a, b))
+        torch.cuda.synchronize()
+        if arr.sync_status() != 0:
+            raise RuntimeError("device status latched in the unsorted-cloud step")
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ts)
+        counts = n_log.cpu().numpy().astype(np.int64)
+        out[name] = {"ms_per_step": ms, "balls_per_iteration": counts.tolist(),
+                     "pairs_per_s": float(counts.sum()) * M / (ms * 1e-3)}
+        arr.close()
+    return out
+
+
 def autograd_memory(sb, arr, wl, init, n0, dev):
     """Per-level trace checkpointing: the autograd Function saves only the
     cloud and recomputes the geometry in the adjoint. Peak device memory of
@@ -1733,6 +2032,17 @@ def main(argv=None):
 
         torch.cuda.set_device(0)
         print(json.dumps(batched_frames(args, sb, torch.device("cuda", 0), profile=True)))
+        return 0
+    if args.learned_batched:
+        import torch
+
+        import __graft_entry__ as ge
+
+        ge.build()
+        from paper_2601_00551_gb300 import slingbag as sb
+
+        torch.cuda.set_device(0)
+        print(json.dumps(learned_plus_batched(sb, torch.device("cuda", 0))))
         return 0
     if args.large_calls:
         import torch

@@ -281,6 +281,9 @@ typedef struct {
     double* loss_log_dev; /* optional: L of every iteration (device doubles) */
     int* n_log_dev;       /* optional: ball count entering every iteration */
     int log_capacity;     /* entries available in the logs */
+    int spatial_sort;     /* 1: put the live cloud in Morton order (sbp_sort_cloud) before
+                             zero-gradient filtering; single-cloud sbp_reconstruct only
+                             (sbp_reconstruct_frames returns SBP_ERR_ARG when it is set) */
 } sbp_recon_params;
 
 /* The point-cloud reconstruction loop of Algorithm 1 on the device.
@@ -301,6 +304,21 @@ typedef struct {
  *   "until converged" is read as a fixed iteration count per stage). */
 int sbp_reconstruct(sbp_array arr, const float* y_full_dev, sbp_balls balls, int* n_dev,
                     int n_cap, const sbp_recon_params* rp, sbp_stream stream);
+
+/* Spatial ordering (no counterpart in the paper; its random initialisation,
+ * Section 4.1, leaves the cloud in random order): puts the n_dev live balls
+ * in Morton (Z-curve) order of their centres, so that the forward's and the
+ * adjoint's chunks of consecutive balls are compact. The key quantises each
+ * axis to 10 bits over the live cloud's bounding cube: with lo the
+ * componentwise minimum and span the largest extent, q = min(1023,
+ * floor((c - lo) * (1024 / span))), each float32 operation rounded once
+ * (no fused multiply-add), and the key interleaves the bits of (q_x, q_y,
+ * q_z), x lowest. The order is stable (equal keys keep their index order).
+ * The n_extra rows of carried state (device float arrays of n_cap, e.g. Adam
+ * moments; n_extra <= 21) follow the same permutation. Allocates its key
+ * scratch on the first call; nothing synchronises. */
+int sbp_sort_cloud(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap,
+                   float* const* extra, int n_extra, sbp_stream stream);
 
 /* ---------------------------------------------------------------------- */
 /* Batched frames: many acquisitions (e.g. the frames of dynamic imaging) of
@@ -492,17 +510,26 @@ int sbp_cnn_forward(sbp_cnn cnn, const float* vol_dev, float* out_dev, sbp_strea
  *   mean_v [ pos_weight t log(1 + e^-z) + (1 - t) log(1 + e^z) ]
  *     + mean_v [ t (q - p)^2 ]
  * for targets t = occ_dev (0/1) and p = p0_dev (float [V]); loss_dev
- * (double [2]: the two terms) may be NULL. */
+ * (double [2]: the two terms) may be NULL. The weight gradients are GEMMs
+ * over voxels on the tensor cores, added in a fixed order: a step is
+ * reproducible bit for bit. */
 int sbp_cnn_train_step(sbp_cnn cnn, const float* vol_dev, const float* occ_dev, const float* p0_dev,
                        float pos_weight, float lr, double* loss_dev, sbp_stream stream);
-/* Proposal: forward pass, then one ball per voxel with sigmoid(z) >
- * prob_threshold, in voxel order, at a uniformly random point of the voxel
- * (SplitMix64 of `seed`, outputs 3v .. 3v+2), radius R, pressure q clamped
- * to [p_min, p_max]. Writes at most n_cap balls and their number to *n_dev
+/* The gradient of that loss with respect to every FP32 parameter, written to
+ * grad_dev (device, sbp_cnn_num_params floats, the layout of
+ * sbp_cnn_params), without changing the parameters; loss_dev as above (may
+ * be NULL). Reproducible bit for bit. */
+int sbp_cnn_grad(sbp_cnn cnn, const float* vol_dev, const float* occ_dev, const float* p0_dev,
+                 float pos_weight, double* loss_dev, float* grad_dev, sbp_stream stream);
+/* Proposal: forward pass, then per_voxel balls (1 .. 4096) in every voxel v
+ * with sigmoid(z) > prob_threshold, in voxel order, ball j of voxel v at a
+ * uniformly random point of the voxel (SplitMix64 of `seed`, outputs
+ * 3 (v per_voxel + j) .. + 2), radius R, pressure q clamped to
+ * [p_min, p_max]. Writes at most n_cap balls and their number to *n_dev
  * (device int). Allocates scratch on first use (synchronising then). */
 int sbp_cnn_propose(sbp_cnn cnn, const float* vol_dev, float prob_threshold, uint64_t seed,
                     const double* origin3, double spacing, float R, float p_min, float p_max,
-                    sbp_balls out, int n_cap, int* n_dev, sbp_stream stream);
+                    int per_voxel, sbp_balls out, int n_cap, int* n_dev, sbp_stream stream);
 
 /* Synchronise `stream` and return (then clear) the convolution status:
  * 0 = fine, SBP_ERR_TIMEOUT = a bounded wait of the tensor-core

@@ -356,6 +356,40 @@ def grow(balls, grads, extra, gp: GrowParams):
 
 
 # --------------------------------------------------------------------------
+# spatial ordering (no counterpart in the paper: the library's sbp_sort_cloud)
+# --------------------------------------------------------------------------
+
+def morton_key(balls) -> np.ndarray:
+    """The 30-bit Morton key of every ball, by its definition: lo = the
+    componentwise minimum of the centres, span = the largest extent over the
+    three axes, inv = 1024 / span, q = min(1023, floor((c - lo) * inv)) per
+    axis (clamped below at 0), each operation in float32 rounded once, and
+    the bits of (q_x, q_y, q_z) interleaved with x lowest."""
+    b = np.asarray(balls, dtype=np.float32).reshape(5, -1)
+    n = b.shape[1]
+    if n == 0:
+        return np.zeros(0, dtype=np.int64)
+    lo = b[:3].min(axis=1)
+    hi = b[:3].max(axis=1)
+    ext = (hi - lo).astype(np.float32)
+    span = np.float32(ext.max())
+    inv = np.float32(np.float32(1024.0) / span) if span > 0 else np.float32(0.0)
+    key = np.zeros(n, dtype=np.int64)
+    for a in range(3):
+        t = ((b[a] - lo[a]).astype(np.float32) * inv).astype(np.float32)
+        q = np.clip(np.floor(t), 0, 1023).astype(np.int64)
+        for bit in range(10):
+            key |= ((q >> bit) & 1) << (3 * bit + a)
+    return key
+
+
+def morton_permutation(balls) -> np.ndarray:
+    """Indices of the balls in ascending key order, equal keys in index
+    order (a stable sort)."""
+    return np.argsort(morton_key(balls), kind="stable")
+
+
+# --------------------------------------------------------------------------
 # Adam (reading: the paper names no optimizer)
 # --------------------------------------------------------------------------
 

@@ -123,12 +123,41 @@ def cnn_forward(p, vol, round_activations: bool = True) -> np.ndarray:
     return out.reshape(-1, 2)
 
 
-def cnn_loss_grad(p, vol, occ, p0, pos_weight: float):
+def cnn_loss_grad(p, vol, occ, p0, pos_weight: float, bf16_storage: bool = False):
     """Loss and its gradient with respect to the FP32 parameters, by torch
-    autograd in float64 on the CPU (activations not rounded; weights used
-    through their bf16 values, input bf16). Returns (loss0, loss1, grad)."""
+    autograd in float64 on the CPU (weights used through their bf16 values,
+    input bf16). Returns (loss0, loss1, grad).
+
+    With bf16_storage the tensors the network stores in bf16 are rounded to
+    bf16 at the points where they are stored, the precision the network is
+    specified in (BF16 storage, FP32 accumulation): the hidden activations
+    h1, h2, h3 after their ReLU; the gradient with respect to the third
+    convolution's output, after the ReLU mask; and the gradients with
+    respect to h2 and h1, before their ReLU masks. Every sum is still taken
+    in float64. Without it nothing is rounded past the input and weights."""
     import torch
     import torch.nn.functional as F
+
+    def to_bf16(a):
+        return a.float().bfloat16().double() if bf16_storage else a
+
+    class Store(torch.autograd.Function):  # rounds the stored value
+        @staticmethod
+        def forward(ctx, a):
+            return to_bf16(a)
+
+        @staticmethod
+        def backward(ctx, g):
+            return g
+
+    class GradStore(torch.autograd.Function):  # rounds the stored gradient
+        @staticmethod
+        def forward(ctx, a):
+            return a.clone()
+
+        @staticmethod
+        def backward(ctx, g):
+            return to_bf16(g)
 
     P = unpack_params(p)
     x = torch.from_numpy(scaled_input(vol)[..., 0])[None, None]  # (1, 1, nz, ny, nx)
@@ -146,8 +175,11 @@ def cnn_loss_grad(p, vol, occ, p0, pos_weight: float):
         return w.permute(0, 2, 1).reshape(co, ci, 3, 3, 3)
 
     h = x
-    for k in (1, 2, 3):
-        h = torch.relu(F.conv3d(h, kern(leaves[f"w{k}"]), leaves[f"b{k}"], padding=1))
+    for k in (1, 2):
+        pre = F.conv3d(h, kern(leaves[f"w{k}"]), leaves[f"b{k}"], padding=1)
+        h = GradStore.apply(Store.apply(torch.relu(pre)))
+    pre = GradStore.apply(F.conv3d(h, kern(leaves["w3"]), leaves["b3"], padding=1))
+    h = Store.apply(torch.relu(pre))
     h = h[0].permute(1, 2, 3, 0).reshape(-1, P["wh"].shape[1])
     out = h @ leaves["wh"].T + leaves["bh"]
     z, q = out[:, 0], out[:, 1]

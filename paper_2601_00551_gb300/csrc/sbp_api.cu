@@ -66,6 +66,8 @@ void free_array(sbp_array_s* a) {
     cudaFree(a->d_fr_yk);
     cudaFree(a->d_fr_S);
     cudaFree(a->d_fr_G);
+    cudaFree(a->d_sort_keys);
+    cudaFree(a->d_sort_tmp);
     delete[] a->h_frame_off;
     delete a;
 }

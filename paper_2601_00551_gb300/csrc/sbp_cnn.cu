@@ -725,6 +725,309 @@ int launch_conv(const ConvArgs& a, bool relu, bool out_f32, long long V, cudaStr
     return launch_conv_t<CIN, COUT, false, false>(a, blocks, st);
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient of a 3x3x3 convolution on the tensor cores.
+//
+// GEMM view: D[m][n] = sum_k A[m][k] B[n][k] with m = tap * Cin + c (the
+// weight's input side), n = output channel, k = voxel:
+//   A[m][v] = x[v + off(tap)][c] (the layer's input, shifted by the tap,
+//   zero outside the volume), B[n][v] = g[v][n] (the loss gradient with
+//   respect to the layer's output before its ReLU). Row m = 27 Cin
+//   of A is all ones over the volume, so D's row 27 Cin is the bias gradient
+//   sum_v g[v][n]. The reduction runs over voxels, but both tensors are
+//   stored channels-last, so every staged 8 x 8 block (8 voxels x 8
+//   channels, one 16-byte load per voxel) is transposed in registers into 8
+//   rows of 8 voxels (one byte permute per output word) and stored in the
+//   canonical K-major, non-swizzled layout of conv3d_tc_kernel.
+// One CTA = one 128-row tile of m x one run of K-steps; a K-step is 64
+// voxels of one x-row (x0 .. x0 + 63 at fixed y, z; columns past nx are
+// zero). Every CTA writes its FP32 tile to partial[chunk][m][n]; a second
+// kernel adds the chunks in chunk order (no atomics: the weight gradient is
+// the same bit for bit on every run).
+// ---------------------------------------------------------------------------
+
+constexpr int kWgRows = 128;   // rows of m per CTA (the MMA's M)
+constexpr int kWgBK = 64;      // voxels per K-step
+
+// out[c] = the 8 channel-c values of the 8 voxels in[0..7] (8 bf16 each)
+__device__ __forceinline__ void wg_transpose8(const uint4 (&in)[8], uint4 (&out)[8]) {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(in);  // w[4 j + c / 2]
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint32_t sel = (c & 1) ? 0x7632u : 0x5410u;
+        uint32_t o[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            o[q] = __byte_perm(w[4 * (2 * q) + (c >> 1)], w[4 * (2 * q + 1) + (c >> 1)], sel);
+        out[c] = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+// Stores the 8 rows r0 .. r0 + 7 (r0 a multiple of 8) of voxel chunk k8 of
+// a K-major tile.
+__device__ __forceinline__ void wg_store8(uint8_t* tile, int r0, int k8, const uint4 (&rows)[8]) {
+    uint8_t* p = tile + ((r0 >> 3) * 8 + k8) * 128;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4*>(p + c * 16) = rows[c];
+}
+
+struct WgradArgs {
+    const __nv_bfloat16* g;  // [V][Cout]
+    const __nv_bfloat16* x;  // [V][Cin]
+    float* partial;          // [chunks][m_pad][Cout]
+    int nx, ny, nz;
+    int xblocks;             // ceil(nx / 64)
+    int steps;               // nz * ny * xblocks
+    int steps_per_chunk;
+    int m_pad;               // row tiles * 128
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(WgradArgs a) {
+    static_assert(COUT % 16 == 0 && COUT >= 16 && COUT <= kTcCols, "Cout must be 16, 32 or 64");
+    static_assert(CIN == 1 || CIN % 8 == 0, "Cin must be 1 or a multiple of 8");
+    extern __shared__ __align__(1024) uint8_t s_dyn[];
+    constexpr int kABytes = kWgRows * kWgBK * 2, kBBytes = COUT * kWgBK * 2;
+    constexpr int kRowsUsed = 27 * CIN + 1;  // weight rows and the bias row
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int mt = blockIdx.x;
+    const int s0 = blockIdx.y * a.steps_per_chunk;
+    const int s1 = min(a.steps, s0 + a.steps_per_chunk);
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    constexpr uint32_t idesc = umma_idesc_bf16(kWgRows, COUT);
+    uint32_t phase[2] = {0u, 0u};
+    bool ok = true;
+    // this thread's 8 x 8 block of each stage: rows r8 * 8 .. + 7, voxels k8 * 8 .. + 7
+    const int r8 = tid >> 3, k8 = tid & 7;
+    const int nsteps = s1 - s0;
+
+    for (int it = 0; it < nsteps; ++it) {
+        const int st = it & 1;
+        if (it >= 2) {  // the MMAs that read this stage two steps ago must be done
+            if (!mbar_wait(&bar[st], phase[st])) ok = false;
+            phase[st] ^= 1u;
+        }
+        if (!__syncthreads_and(ok)) break;
+        const int s = s0 + it;
+        const int xb = s % a.xblocks;
+        const int y = (s / a.xblocks) % a.ny;
+        const int z = s / (a.xblocks * a.ny);
+        const int xv = xb * kWgBK + k8 * 8;  // first voxel of this thread's 8
+        uint8_t* tileA = s_dyn + st * kABytes;
+        uint8_t* tileB = s_dyn + 2 * kABytes + st * kBBytes;
+        // A: rows m0 .. m0 + 7 of the layer input shifted by the row's tap
+        const int m0 = mt * kWgRows + r8 * 8;
+        uint4 blk[8], rows[8];
+        if constexpr (CIN % 8 == 0) {
+            const int tap = m0 / CIN, c0 = m0 - tap * CIN;
+            const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
+            const int yy = y + dy, zz = z + dz;
+            const bool row_in = m0 < 27 * CIN && yy >= 0 && yy < a.ny && zz >= 0 && zz < a.nz;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int xx = xv + j + dx;
+                blk[j] = make_uint4(0u, 0u, 0u, 0u);
+                if (row_in && xv + j < a.nx && xx >= 0 && xx < a.nx)
+                    blk[j] = *reinterpret_cast<const uint4*>(
+                        a.x + (((long long)zz * a.ny + yy) * a.nx + xx) * CIN + c0);
+            }
+            wg_transpose8(blk, rows);
+            if (m0 == 27 * CIN) {  // the bias row: ones over the volume, then zero rows
+                uint32_t o[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    o[q] = (xv + 2 * q < a.nx ? 0x3F80u : 0u) |
+                           (xv + 2 * q + 1 < a.nx ? 0x3F800000u : 0u);
+                rows[0] = make_uint4(o[0], o[1], o[2], o[3]);
+            }
+        } else {  // one input channel: row m is tap m, read voxel by voxel
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int m = m0 + i;
+                uint32_t o[4] = {0u, 0u, 0u, 0u};
+                if (m < 27) {
+                    const int dx = m % 3 - 1, dy = (m / 3) % 3 - 1, dz = m / 9 - 1;
+                    const int yy = y + dy, zz = z + dz;
+                    if (yy >= 0 && yy < a.ny && zz >= 0 && zz < a.nz) {
+                        const unsigned short* rowp = reinterpret_cast<const unsigned short*>(a.x) +
+                                                     ((long long)zz * a.ny + yy) * a.nx;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int xx = xv + j + dx;
+                            const uint32_t h = (xv + j < a.nx && xx >= 0 && xx < a.nx) ? rowp[xx] : 0u;
+                            o[j >> 1] |= h << (16 * (j & 1));
+                        }
+                    }
+                } else if (m == 27) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        o[q] = (xv + 2 * q < a.nx ? 0x3F80u : 0u) |
+                               (xv + 2 * q + 1 < a.nx ? 0x3F800000u : 0u);
+                }
+                rows[i] = make_uint4(o[0], o[1], o[2], o[3]);
+            }
+        }
+        wg_store8(tileA, r8 * 8, k8, rows);
+        // B: the output gradient, rows = output channels
+        if (r8 < COUT / 8) {
+            const long long vrow = ((long long)z * a.ny + y) * a.nx;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                blk[j] = make_uint4(0u, 0u, 0u, 0u);
+                if (xv + j < a.nx)
+                    blk[j] = *reinterpret_cast<const uint4*>(a.g + (vrow + xv + j) * COUT + r8 * 8);
+            }
+            wg_transpose8(blk, rows);
+            wg_store8(tileB, r8 * 8, k8, rows);
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(tileA), b0 = smem_u32(tileB);
+#pragma unroll
+            for (int ks = 0; ks < kWgBK / 16; ++ks)  // K = 16 per MMA: two core matrices
+                tc_mma(tmem, umma_desc(a0 + ks * 256, 128, 1024), umma_desc(b0 + ks * 256, 128, 1024),
+                       idesc, (it > 0 || ks > 0) ? 1u : 0u);
+            tc_commit(&bar[st]);
+        }
+    }
+
+    // wait for the last commit of each stage still outstanding
+    if (ok) {
+        for (int s = 0; s < 2; ++s) {
+            const int uses = nsteps > s ? (nsteps - 1 - s) / 2 + 1 : 0;  // commits made on stage s
+            const int waited = uses > 0 ? uses - 1 : 0;                 // of them already waited on
+            if (uses > waited && !mbar_wait(&bar[s], phase[s])) ok = false;
+        }
+    }
+    tc_fence_after();
+    const int row = mt * kWgRows + warp * 32 + (tid & 31);
+    float* out = a.partial + ((size_t)blockIdx.y * a.m_pad + row) * COUT;
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicExch(&g_cnn_status, 1);
+    } else if (nsteps > 0) {
+        // lane = row m, columns = output channels (every lane takes part in
+        // the warp-wide tcgen05.ld)
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
+            float v[16];
+            tc_ld16(taddr + c0, v);
+            if (row < kRowsUsed) {
+                float4* o = reinterpret_cast<float4*>(out + c0);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            }
+        }
+    } else if (row < kRowsUsed) {
+        for (int c = 0; c < COUT; ++c) out[c] = 0.0f;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTcCols)
+                     : "memory");
+}
+
+// dW[n][tap][c] = sum over chunks (in chunk order) of row tap * Cin + c,
+// db[n] = the same for the bias row 27 Cin.
+template <int CIN, int COUT>
+__global__ void wgrad_reduce_kernel(const float* __restrict__ partial, int chunks, int m_pad,
+                                    float* __restrict__ dW, float* __restrict__ db) {
+    constexpr int kOut = (27 * CIN + 1) * COUT;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < kOut; t += gridDim.x * blockDim.x) {
+        const int m = t / COUT, n = t - m * COUT;
+        float s = 0.0f;
+        for (int k = 0; k < chunks; ++k) s += partial[((size_t)k * m_pad + m) * COUT + n];
+        if (m < 27 * CIN) {
+            const int tap = m / CIN, c = m - tap * CIN;
+            dW[((size_t)n * 27 + tap) * CIN + c] = s;
+        } else {
+            db[n] = s;
+        }
+    }
+}
+
+// Chunks of K-steps for a layer: enough CTAs to fill the GPU about four
+// times over, every chunk non-empty.
+void wgrad_plan(int nx, int ny, int nz, int cin, int sms, int& xblocks, int& steps,
+                int& steps_per, int& chunks, int& m_pad) {
+    xblocks = (nx + kWgBK - 1) / kWgBK;
+    steps = nz * ny * xblocks;
+    const int tiles = (27 * cin + 1 + kWgRows - 1) / kWgRows;
+    m_pad = tiles * kWgRows;
+    const int want = std::max(1, (4 * sms + tiles - 1) / tiles);
+    steps_per = std::max(1, (steps + want - 1) / want);
+    chunks = (steps + steps_per - 1) / steps_per;
+}
+
+template <int CIN, int COUT>
+int launch_wgrad_t(const WgradArgs& a, int chunks, float* dW, float* db, cudaStream_t st) {
+    constexpr int smem = 2 * (kWgRows + COUT) * kWgBK * 2;
+    auto k = wgrad_tc_kernel<CIN, COUT>;
+    if (sbp_cuda_check(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                       "cnn wgrad: smem attribute"))
+        return SBP_ERR_CUDA;
+    const dim3 grid((unsigned)(a.m_pad / kWgRows), (unsigned)chunks);
+    k<<<grid, kTcThreads, smem, st>>>(a);
+    constexpr int kOut = (27 * CIN + 1) * COUT;
+    wgrad_reduce_kernel<CIN, COUT><<<(kOut + 255) / 256, 256, 0, st>>>(a.partial, chunks, a.m_pad,
+                                                                       dW, db);
+    sbp_count_launches(2);
+    return sbp_cuda_check(cudaGetLastError(), "cnn wgrad launch") ? SBP_ERR_CUDA : SBP_OK;
+}
+
+}  // namespace
+
+// Weight and bias gradients of a 3x3x3 convolution (Cin, Cout) in (1, 16),
+// (16, 32), (32, 64): see wgrad_tc_kernel. `partial` holds
+// sbp_wgrad_scratch_floats(...) floats.
+long long sbp_wgrad_scratch_floats(int nx, int ny, int nz, int cin, int cout, int sms) {
+    int xb, steps, per, chunks, m_pad;
+    wgrad_plan(nx, ny, nz, cin, sms, xb, steps, per, chunks, m_pad);
+    return (long long)chunks * m_pad * cout;
+}
+
+int sbp_wgrad_bf16(const void* g_dev, const void* x_dev, int nx, int ny, int nz, int cin,
+                   int cout, int sms, float* partial, float* dW, float* db, cudaStream_t st) {
+    WgradArgs a;
+    int chunks;
+    wgrad_plan(nx, ny, nz, cin, sms, a.xblocks, a.steps, a.steps_per_chunk, chunks, a.m_pad);
+    a.g = static_cast<const __nv_bfloat16*>(g_dev);
+    a.x = static_cast<const __nv_bfloat16*>(x_dev);
+    a.partial = partial;
+    a.nx = nx;
+    a.ny = ny;
+    a.nz = nz;
+    if (cin == 1 && cout == 16) return launch_wgrad_t<1, 16>(a, chunks, dW, db, st);
+    if (cin == 16 && cout == 32) return launch_wgrad_t<16, 32>(a, chunks, dW, db, st);
+    if (cin == 32 && cout == 64) return launch_wgrad_t<32, 64>(a, chunks, dW, db, st);
+    sbp_set_error("cnn wgrad: unsupported (cin, cout)");
+    return SBP_ERR_ARG;
+}
+
+namespace {
+
 }  // namespace
 
 extern "C" {

@@ -194,8 +194,8 @@ int sbp_reconstruct_frames(sbp_array arr, const float* y_full_dev, sbp_balls bal
     if (int e = check_frames(arr, "reconstruct_frames")) return e;
     if (!rp || !y_full_dev || !n_dev || !balls_ok(balls) || rp->n_stages < 0 ||
         rp->n_stages > SBP_MAX_STAGES || rp->zero_grad_mode < -1 ||
-        rp->zero_grad_mode > SBP_DROP_ZERO) {
-        sbp_set_error("reconstruct_frames: invalid argument");
+        rp->zero_grad_mode > SBP_DROP_ZERO || rp->spatial_sort != 0) {
+        sbp_set_error("reconstruct_frames: invalid argument (spatial_sort is single-cloud only)");
         return SBP_ERR_ARG;
     }
     if (rp->zero_grad_mode >= 0 &&

@@ -140,6 +140,11 @@ struct sbp_array_s {
     float* d_adj_part;
     unsigned int* d_adj_ticket;
     int adj_chunks;  // chunks the two hold
+    // spatial sort (allocated by its first use): keys and indices in and out
+    // (4 n_cap words) and the box (8 words); the radix sort's temporary storage
+    unsigned int* d_sort_keys;
+    void* d_sort_tmp;
+    size_t sort_tmp_bytes;
 };
 
 // ----------------------------------------------------------------------------
@@ -183,6 +188,17 @@ int sbp_launch_adam_frames(sbp_array_s* a, sbp_balls balls, sbp_grads grads, sbp
                            unsigned mask, cudaStream_t st);
 int sbp_launch_downsample_rows(sbp_array_s* a, int k, int rows, const float* y_full,
                                float* y_k, cudaStream_t st);
+
+// Morton order of the live balls of a single cloud, carrying `nrows` float
+// rows (the five ball rows first, then any state) through the permutation
+// (sbp_sort.cu); nrows <= SBP_FG_ARRAYS.
+int sbp_launch_sort(sbp_array_s* a, float* const* rows, int nrows, const int* n_dev, int n_cap,
+                    cudaStream_t st);
+
+// weight gradient of the proposal CNN's convolutions on the tensor cores (sbp_cnn.cu)
+long long sbp_wgrad_scratch_floats(int nx, int ny, int nz, int cin, int cout, int sms);
+int sbp_wgrad_bf16(const void* g_dev, const void* x_dev, int nx, int ny, int nz, int cin,
+                   int cout, int sms, float* partial, float* dW, float* db, cudaStream_t st);
 
 // ----------------------------------------------------------------------------
 // device helpers

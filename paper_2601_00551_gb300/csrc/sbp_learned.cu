@@ -10,8 +10,10 @@
 //     positive-class weight), squared error on the pressure of occupied
 //     voxels, backpropagation (the data gradient of a convolution is the
 //     convolution of the output gradient with the flipped, transposed
-//     weights, on the tensor cores again; weight gradients are reductions
-//     over voxels on the CUDA cores) and Adam on FP32 master weights;
+//     weights, on the tensor cores again; the weight gradients are GEMMs
+//     over voxels on the tensor cores too, sbp_wgrad_bf16, reduced in a
+//     fixed order so that a training step is reproducible bit for bit) and
+//     Adam on FP32 master weights;
 //   * the proposal: one ball per voxel whose occupancy probability exceeds a
 //     threshold, at a seeded random point of the voxel, in voxel order.
 #include <cuda_bf16.h>
@@ -69,6 +71,9 @@ struct sbp_cnn_s {
     double* loss = nullptr;        // [2]: data term sums
     int* cnt = nullptr;            // proposal scratch: per-block counts ([blocks + 1])
     long long cnt_cap = 0;
+    int sms = 1;                   // SMs of the device (sizes the weight-gradient grids)
+    float* wg_part = nullptr;      // weight-gradient partial tiles (largest layer)
+    float* hd_part = nullptr;      // head parameter-gradient partials [blocks][kWh + kBh]
 };
 
 namespace {
@@ -245,10 +250,11 @@ __global__ void head_bwd_data_kernel(const __nv_bfloat16* __restrict__ h3,
 // head backward, parameter part: dWh[j][c] = sum_v dout[v][j] h3[v][c] and
 // dbh[j] = sum_v dout[v][j]. A block takes `chunk` voxels; thread j kC3 + c
 // sums its weight over them (reading a voxel's channels coalesced), threads
-// 2 kC3 and 2 kC3 + 1 the biases; one atomic per thread and block.
+// 2 kC3 and 2 kC3 + 1 the biases, into the block's row of partials; the
+// rows are then added in block order (head_param_reduce_kernel).
 __global__ void head_bwd_param_kernel(const __nv_bfloat16* __restrict__ h3,
                                       const float* __restrict__ dout, long long V, int chunk,
-                                      float* __restrict__ G) {
+                                      float* __restrict__ part) {
     const int t = threadIdx.x;
     if (t >= kWh + kBh) return;
     const long long v0 = (long long)blockIdx.x * chunk, v1 = min(V, v0 + chunk);
@@ -258,7 +264,16 @@ __global__ void head_bwd_param_kernel(const __nv_bfloat16* __restrict__ h3,
         const float d = dout[2 * v + j];
         acc = t < kWh ? fmaf(d, __bfloat162float(h3[v * kC3 + c]), acc) : acc + d;
     }
-    atomicAdd(&G[kOWh + t], acc);
+    part[(size_t)blockIdx.x * (kWh + kBh) + t] = acc;
+}
+
+__global__ void head_param_reduce_kernel(const float* __restrict__ part, int blocks,
+                                         float* __restrict__ G) {
+    const int t = threadIdx.x;
+    if (t >= kWh + kBh) return;
+    float s = 0.0f;
+    for (int b = 0; b < blocks; ++b) s += part[(size_t)b * (kWh + kBh) + t];
+    G[kOWh + t] = s;
 }
 
 // g[v][c] *= [h[v][c] > 0] (the ReLU of the layer that produced h)
@@ -267,72 +282,6 @@ __global__ void relu_mask_kernel(__nv_bfloat16* __restrict__ g, const __nv_bfloa
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         if (!(__bfloat162float(h[i]) > 0.f)) g[i] = __float2bfloat16(0.0f);
-}
-
-// Weight gradient of a 3x3x3 convolution for one tap (blockIdx.y) over a
-// chunk of voxels (blockIdx.x): dW[n][tap][c] += sum_v g[v][n] x[v + off][c],
-// and for the centre tap the bias gradient sum_v g[v][n]. Voxels are staged
-// 64 at a time; each thread accumulates a fixed set of (n, c) pairs.
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(256)
-wgrad_kernel(const __nv_bfloat16* __restrict__ g, const __nv_bfloat16* __restrict__ x, int nx,
-             int ny, int nz, int chunk, float* __restrict__ dW, float* __restrict__ db) {
-    constexpr int kV = 64;
-    constexpr int kPairs = CIN * COUT;
-    constexpr int kPer = (kPairs + 255) / 256;
-    __shared__ float sg[kV][COUT];
-    __shared__ float sx[kV][CIN];
-    const int tap = blockIdx.y;
-    const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
-    const long long V = (long long)nx * ny * nz;
-    const long long v0 = (long long)blockIdx.x * chunk;
-    const long long v1 = min(V, v0 + chunk);
-    float acc[kPer];
-    float bacc = 0.f;
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) acc[q] = 0.f;
-    for (long long b = v0; b < v1; b += kV) {
-        const int cnt = (int)min((long long)kV, v1 - b);
-        __syncthreads();
-        for (int t = threadIdx.x; t < kV * COUT; t += blockDim.x) {
-            const int i = t / COUT, n = t % COUT;
-            sg[i][n] = i < cnt ? __bfloat162float(g[(b + i) * COUT + n]) : 0.0f;
-        }
-        for (int t = threadIdx.x; t < kV * CIN; t += blockDim.x) {
-            const int i = t / CIN, c = t % CIN;
-            float xv = 0.f;
-            if (i < cnt) {
-                const long long v = b + i;
-                const int ix = (int)(v % nx) + dx, iy = (int)((v / nx) % ny) + dy;
-                const int iz = (int)(v / ((long long)nx * ny)) + dz;
-                if (ix >= 0 && ix < nx && iy >= 0 && iy < ny && iz >= 0 && iz < nz)
-                    xv = __bfloat162float(x[(((long long)iz * ny + iy) * nx + ix) * CIN + c]);
-            }
-            sx[i][c] = xv;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const int pr = threadIdx.x + q * 256;
-            if (pr < kPairs) {
-                const int n = pr / CIN, c = pr % CIN;
-                float a = acc[q];
-                for (int i = 0; i < kV; ++i) a = fmaf(sg[i][n], sx[i][c], a);
-                acc[q] = a;
-            }
-        }
-        if (tap == 13 && threadIdx.x < COUT)
-            for (int i = 0; i < kV; ++i) bacc += sg[i][threadIdx.x];
-    }
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-        const int pr = threadIdx.x + q * 256;
-        if (pr < kPairs) {
-            const int n = pr / CIN, c = pr % CIN;
-            atomicAdd(&dW[((size_t)n * 27 + tap) * CIN + c], acc[q]);
-        }
-    }
-    if (tap == 13 && threadIdx.x < COUT) atomicAdd(&db[threadIdx.x], bacc);
 }
 
 // forward weights [cout][27][cin] -> bf16 [cout][kp]; dgrad weights
@@ -409,26 +358,34 @@ __global__ void propose_scan_kernel(int* __restrict__ cnt, int nb) {
     if (threadIdx.x == 0) cnt[nb] = (int)carry;
 }
 
+// Occupied voxel number q (in voxel order) gets balls q k .. q k + k - 1, ball
+// j at the seeded uniform point of counter outputs 3 (v k + j) .. + 2.
 __global__ void propose_write_kernel(const float* __restrict__ out, long long V, float zthr,
                                      const int* __restrict__ off, VoxGeo g, uint64_t seed, float R,
-                                     float p_min, float p_max, sbp_balls balls, int n_cap,
+                                     float p_min, float p_max, int k, sbp_balls balls, int n_cap,
                                      int* __restrict__ n_dev) {
     __shared__ long long warp_tot[32];
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int on = (v < V && out[2 * v] > zthr) ? 1 : 0;
     long long tot;
     const long long incl = sbp_block_incl_scan(on, warp_tot, tot);
-    const long long pos = off[blockIdx.x] + incl - on;
-    if (on && pos < n_cap) {
+    const long long q = off[blockIdx.x] + incl - on;
+    if (on) {
         const int ix = (int)(v % g.n[0]), iy = (int)((v / g.n[0]) % g.n[1]);
         const int iz = (int)(v / ((long long)g.n[0] * g.n[1]));
-        balls.x[pos] = g.o[0] + ((float)ix + unit24(seed, 3 * v)) * g.h;
-        balls.y[pos] = g.o[1] + ((float)iy + unit24(seed, 3 * v + 1)) * g.h;
-        balls.z[pos] = g.o[2] + ((float)iz + unit24(seed, 3 * v + 2)) * g.h;
-        balls.R[pos] = R;
-        balls.p0[pos] = fminf(fmaxf(out[2 * v + 1], p_min), p_max);
+        const float p = fminf(fmaxf(out[2 * v + 1], p_min), p_max);
+        for (int j = 0; j < k; ++j) {
+            const long long pos = q * k + j, c = 3 * (v * k + j);
+            if (pos >= n_cap) break;
+            balls.x[pos] = g.o[0] + ((float)ix + unit24(seed, c)) * g.h;
+            balls.y[pos] = g.o[1] + ((float)iy + unit24(seed, c + 1)) * g.h;
+            balls.z[pos] = g.o[2] + ((float)iz + unit24(seed, c + 2)) * g.h;
+            balls.R[pos] = R;
+            balls.p0[pos] = p;
+        }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *n_dev = min(off[gridDim.x], n_cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *n_dev = (int)min((long long)off[gridDim.x] * k, (long long)n_cap);
 }
 
 int blocks_for(long long n, int threads = 256, int cap = 4096) {
@@ -543,6 +500,16 @@ int sbp_cnn_create(int nx, int ny, int nz, uint64_t seed, sbp_cnn* out) {
     alloc((void**)&c->dout, sizeof(float) * 2 * V);
     alloc((void**)&c->vmax, sizeof(unsigned int));
     alloc((void**)&c->loss, sizeof(double) * 2);
+    {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        c->sms = sms > 0 ? sms : 1;
+        const long long wg = std::max({sbp_wgrad_scratch_floats(nx, ny, nz, 1, kC1, c->sms),
+                                       sbp_wgrad_scratch_floats(nx, ny, nz, kC1, kC2, c->sms),
+                                       sbp_wgrad_scratch_floats(nx, ny, nz, kC2, kC3, c->sms)});
+        alloc((void**)&c->wg_part, sizeof(float) * (size_t)wg);
+        alloc((void**)&c->hd_part, sizeof(float) * (size_t)((V + 511) / 512) * (kWh + kBh));
+    }
     if (!ok) {
         sbp_cnn_destroy(c);
         return SBP_ERR_CUDA;
@@ -584,7 +551,8 @@ int sbp_cnn_destroy(sbp_cnn c) {
     if (!c) return SBP_OK;
     cudaDeviceSynchronize();
     void* ptrs[] = {c->p,  c->w1, c->w2, c->w3,  c->w2t, c->w3t, c->x0,   c->h1,   c->h2, c->h3,
-                    c->g3, c->g2, c->g1, c->out, c->dout, c->vmax, c->loss, c->cnt};
+                    c->g3, c->g2, c->g1, c->out, c->dout, c->vmax, c->loss, c->cnt,
+                    c->wg_part, c->hd_part};
     for (void* q : ptrs) cudaFree(q);
     delete c;
     return SBP_OK;
@@ -628,14 +596,13 @@ int sbp_cnn_forward(sbp_cnn c, const float* vol_dev, float* out_dev, sbp_stream 
     return SBP_OK;
 }
 
-int sbp_cnn_train_step(sbp_cnn c, const float* vol_dev, const float* occ_dev, const float* p0_dev,
-                       float pos_weight, float lr, double* loss_dev, sbp_stream stream) {
-    if (int e = check(c, "cnn_train_step")) return e;
-    if (!vol_dev || !occ_dev || !p0_dev || !(lr > 0.f) || !(pos_weight > 0.f)) {
-        sbp_set_error("cnn_train_step: invalid argument");
-        return SBP_ERR_ARG;
-    }
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+namespace {
+
+// Forward, loss and backward of one volume: every parameter's gradient is
+// written (not accumulated) into the gradient block G = p + 3 kParams, in a
+// fixed order of additions, and the two loss terms into c->loss.
+int backward(sbp_cnn c, const float* vol_dev, const float* occ_dev, const float* p0_dev,
+             float pos_weight, cudaStream_t st) {
     void* s = reinterpret_cast<void*>(st);
     const long long V = c->V;
     const int nx = c->nx, ny = c->ny, nz = c->nz;
@@ -647,32 +614,51 @@ int sbp_cnn_train_step(sbp_cnn c, const float* vol_dev, const float* occ_dev, co
                                                c->loss);
     head_bwd_data_kernel<<<blocks_for(V * kC3), 256, 0, st>>>(c->h3, c->dout, V, c->p, c->g3);
     static_assert(kWh + kBh <= 256, "one thread per head parameter");
-    head_bwd_param_kernel<<<(unsigned)((V + 511) / 512), 256, 0, st>>>(c->h3, c->dout, V, 512, G);
-    // conv3: weights, then the data gradient into g2 (masked by conv2's ReLU)
-    const int chunk = 4096;
-    const unsigned nchunk = (unsigned)((V + chunk - 1) / chunk);
-    wgrad_kernel<kC2, kC3><<<dim3(nchunk, 27), 256, 0, st>>>(c->g3, c->h2, nx, ny, nz, chunk,
-                                                           G + kOW3, G + kOB3);
+    const unsigned hb = (unsigned)((V + 511) / 512);
+    head_bwd_param_kernel<<<hb, 256, 0, st>>>(c->h3, c->dout, V, 512, c->hd_part);
+    head_param_reduce_kernel<<<1, 256, 0, st>>>(c->hd_part, (int)hb, G);
     sbp_count_launches(4);
+    // conv3: weights (tensor cores), then the data gradient into g2 (masked by conv2's ReLU)
+    if (int e = sbp_wgrad_bf16(c->g3, c->h2, nx, ny, nz, kC2, kC3, c->sms, c->wg_part, G + kOW3,
+                               G + kOB3, st))
+        return e;
     if (int e = sbp_conv3d_bf16(c->g3, nx, ny, nz, kC3, c->w3t, padded_k(kC3), nullptr, kC2, 0,
                                 c->g2, 0, s))
         return e;
     relu_mask_kernel<<<blocks_for(V * kC2), 256, 0, st>>>(c->g2, c->h2, V * kC2);
-    wgrad_kernel<kC1, kC2><<<dim3(nchunk, 27), 256, 0, st>>>(c->g2, c->h1, nx, ny, nz, chunk,
-                                                           G + kOW2, G + kOB2);
-    sbp_count_launches(2);
+    sbp_count_launches(1);
+    if (int e = sbp_wgrad_bf16(c->g2, c->h1, nx, ny, nz, kC1, kC2, c->sms, c->wg_part, G + kOW2,
+                               G + kOB2, st))
+        return e;
     if (int e = sbp_conv3d_bf16(c->g2, nx, ny, nz, kC2, c->w2t, padded_k(kC2), nullptr, kC1, 0,
                                 c->g1, 0, s))
         return e;
     relu_mask_kernel<<<blocks_for(V * kC1), 256, 0, st>>>(c->g1, c->h1, V * kC1);
-    wgrad_kernel<1, kC1><<<dim3(nchunk, 27), 256, 0, st>>>(c->g1, c->x0, nx, ny, nz, chunk,
-                                                         G + kOW1, G + kOB1);
+    sbp_count_launches(1);
+    if (int e = sbp_wgrad_bf16(c->g1, c->x0, nx, ny, nz, 1, kC1, c->sms, c->wg_part, G + kOW1,
+                               G + kOB1, st))
+        return e;
+    return sbp_cuda_check(cudaGetLastError(), "cnn backward") ? SBP_ERR_CUDA : SBP_OK;
+}
+
+}  // namespace
+
+int sbp_cnn_train_step(sbp_cnn c, const float* vol_dev, const float* occ_dev, const float* p0_dev,
+                       float pos_weight, float lr, double* loss_dev, sbp_stream stream) {
+    if (int e = check(c, "cnn_train_step")) return e;
+    if (!vol_dev || !occ_dev || !p0_dev || !(lr > 0.f) || !(pos_weight > 0.f)) {
+        sbp_set_error("cnn_train_step: invalid argument");
+        return SBP_ERR_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (int e = backward(c, vol_dev, occ_dev, p0_dev, pos_weight, st)) return e;
+    float* G = c->p + 3 * kParams;
     ++c->step;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - std::pow(b1, (float)c->step), c2 = 1.0f - std::pow(b2, (float)c->step);
     adam_flat_kernel<<<64, 256, 0, st>>>(c->p, c->p + kParams, c->p + 2 * kParams, G, kParams, lr,
                                          b1, b2, 1e-8f, c1, c2);
-    sbp_count_launches(3);
+    sbp_count_launches(1);
     if (int e = pack_all(c, st)) return e;
     if (loss_dev && sbp_cuda_check(cudaMemcpyAsync(loss_dev, c->loss, sizeof(double) * 2,
                                                    cudaMemcpyDeviceToDevice, st),
@@ -681,13 +667,33 @@ int sbp_cnn_train_step(sbp_cnn c, const float* vol_dev, const float* occ_dev, co
     return sbp_cuda_check(cudaGetLastError(), "cnn_train_step") ? SBP_ERR_CUDA : SBP_OK;
 }
 
+int sbp_cnn_grad(sbp_cnn c, const float* vol_dev, const float* occ_dev, const float* p0_dev,
+                 float pos_weight, double* loss_dev, float* grad_dev, sbp_stream stream) {
+    if (int e = check(c, "cnn_grad")) return e;
+    if (!vol_dev || !occ_dev || !p0_dev || !grad_dev || !(pos_weight > 0.f)) {
+        sbp_set_error("cnn_grad: invalid argument");
+        return SBP_ERR_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (int e = backward(c, vol_dev, occ_dev, p0_dev, pos_weight, st)) return e;
+    if (sbp_cuda_check(cudaMemcpyAsync(grad_dev, c->p + 3 * kParams, sizeof(float) * kParams,
+                                       cudaMemcpyDeviceToDevice, st),
+                       "cnn_grad: copy"))
+        return SBP_ERR_CUDA;
+    if (loss_dev && sbp_cuda_check(cudaMemcpyAsync(loss_dev, c->loss, sizeof(double) * 2,
+                                                   cudaMemcpyDeviceToDevice, st),
+                                   "cnn_grad: loss copy"))
+        return SBP_ERR_CUDA;
+    return SBP_OK;
+}
+
 int sbp_cnn_propose(sbp_cnn c, const float* vol_dev, float prob_threshold, uint64_t seed,
                     const double* origin3, double spacing, float R, float p_min, float p_max,
-                    sbp_balls out, int n_cap, int* n_dev, sbp_stream stream) {
+                    int per_voxel, sbp_balls out, int n_cap, int* n_dev, sbp_stream stream) {
     if (int e = check(c, "cnn_propose")) return e;
     if (!vol_dev || !origin3 || !(spacing > 0.0) || !n_dev || n_cap < 0 || !out.x || !out.y ||
         !out.z || !out.R || !out.p0 || !(prob_threshold > 0.f && prob_threshold < 1.f) ||
-        !(R > 0.f) || !(p_max >= p_min)) {
+        !(R > 0.f) || !(p_max >= p_min) || per_voxel < 1 || per_voxel > 4096) {
         sbp_set_error("cnn_propose: invalid argument");
         return SBP_ERR_ARG;
     }
@@ -714,7 +720,7 @@ int sbp_cnn_propose(sbp_cnn c, const float* vol_dev, float prob_threshold, uint6
     propose_count_kernel<<<nb, 256, 0, st>>>(c->out, V, zthr, c->cnt);
     propose_scan_kernel<<<1, 1024, 0, st>>>(c->cnt, nb);
     propose_write_kernel<<<nb, 256, 0, st>>>(c->out, V, zthr, c->cnt, g, seed, R, p_min, p_max,
-                                             out, n_cap, n_dev);
+                                             per_voxel, out, n_cap, n_dev);
     sbp_count_launches(3);
     return sbp_cuda_check(cudaGetLastError(), "cnn_propose") ? SBP_ERR_CUDA : SBP_OK;
 }

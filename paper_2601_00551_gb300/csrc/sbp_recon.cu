@@ -71,6 +71,11 @@ extern "C" int sbp_reconstruct(sbp_array arr, const float* y_full_dev, sbp_balls
         return sbp_launch_downsample(arr, k, y_full_dev, arr->d_rc_yk, cs);
     };
 
+    // spatial ordering of the initial cloud (its moments are still zero)
+    if (rp->spatial_sort) {
+        float* rows[5] = {balls.x, balls.y, balls.z, balls.R, balls.p0};
+        if (int e = sbp_launch_sort(arr, rows, 5, n_dev, n_cap, cs)) return e;
+    }
     // zero-gradient filtering (Section 4.2): all p0 = 0, so S = 0 and G = -2 y_k
     if (rp->zero_grad_mode >= 0) {
         if (int e = use_level(rp->zero_grad_level)) return e;

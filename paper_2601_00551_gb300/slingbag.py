@@ -73,7 +73,8 @@ class _ReconParams(ctypes.Structure):
     _fields_ = [("zero_grad_mode", ctypes.c_int), ("zero_grad_level", ctypes.c_int),
                 ("n_stages", ctypes.c_int), ("stages", _Stage * MAX_STAGES),
                 ("adam", _AdamParams), ("grow", _GrowParams), ("loss_log_dev", _P),
-                ("n_log_dev", _P), ("log_capacity", ctypes.c_int)]
+                ("n_log_dev", _P), ("log_capacity", ctypes.c_int),
+                ("spatial_sort", ctypes.c_int)]
 
 
 _lib = None
@@ -101,6 +102,7 @@ _SIGS = {
     "sbp_adam_step": (ctypes.c_int, [_P, _Balls, _Balls, _Balls, _Balls, _P, ctypes.c_int,
                                      ctypes.c_int, ctypes.POINTER(_AdamParams), ctypes.c_uint,
                                      _P]),
+    "sbp_sort_cloud": (ctypes.c_int, [_P, _Balls, _P, ctypes.c_int, _P, ctypes.c_int, _P]),
     "sbp_reconstruct": (ctypes.c_int, [_P, _P, _Balls, _P, ctypes.c_int,
                                        ctypes.POINTER(_ReconParams), _P]),
     "sbp_launch_count": (ctypes.c_longlong, []),
@@ -157,9 +159,11 @@ _SIGS = {
     "sbp_cnn_forward": (ctypes.c_int, [_P, _P, _P, _P]),
     "sbp_cnn_train_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_float, ctypes.c_float, _P,
                                           _P]),
+    "sbp_cnn_grad": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_float, _P, _P, _P]),
     "sbp_cnn_propose": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_uint64, _P,
                                        ctypes.c_double, ctypes.c_float, ctypes.c_float,
-                                       ctypes.c_float, _Balls, ctypes.c_int, _P, _P]),
+                                       ctypes.c_float, ctypes.c_int, _Balls, ctypes.c_int, _P,
+                                       _P]),
     "sbp_sync_status": (ctypes.c_int, [_P, _P]),
     "sbp_get_inside_pairs": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_longlong)]),
 }
@@ -442,9 +446,11 @@ class SensorArray:
     def reconstruct(self, y_full: torch.Tensor, balls: torch.Tensor, n_dev: torch.Tensor,
                     stages, zero_grad_mode: int = KEEP_NEG, zero_grad_level: int = 0,
                     adam: AdamParams | None = None, grow: GrowParams | None = None,
-                    loss_log: torch.Tensor | None = None, n_log: torch.Tensor | None = None):
+                    loss_log: torch.Tensor | None = None, n_log: torch.Tensor | None = None,
+                    spatial_sort: bool = False):
         """Algorithm 1 on the device (sbp_reconstruct): zero-gradient filtering
-        then the given stages; balls and n_dev are updated in place."""
+        then the given stages; balls and n_dev are updated in place. With
+        spatial_sort the live cloud is first put in Morton order (sbp_sort_cloud)."""
         self._check_traces(y_full, self.T)
         if len(stages) > MAX_STAGES:
             raise ValueError(f"at most {MAX_STAGES} stages")
@@ -469,6 +475,7 @@ class SensorArray:
             rp.n_log_dev = n_log.data_ptr()
             cap = n_log.numel() if loss_log is None else min(cap, n_log.numel())
         rp.log_capacity = cap
+        rp.spatial_sort = int(bool(spatial_sort))
         _check("sbp_reconstruct", self._lib.sbp_reconstruct(
             self._h, _dptr(y_full), _rows(balls), _dptr(n_dev), balls.shape[1],
             ctypes.byref(rp), _stream()))
@@ -476,6 +483,21 @@ class SensorArray:
             self.level = stages[-1].level
         elif zero_grad_mode is not None and zero_grad_mode >= 0:
             self.level = zero_grad_level
+
+    def sort_cloud(self, balls: torch.Tensor, n: torch.Tensor | None = None, extra=()):
+        """Morton order of the live balls in place (sbp_sort_cloud); `extra`:
+        float32 CUDA tensors of rows (k, n_cap) carried through the permutation."""
+        nd = self._n(n, balls.shape[1])
+        rows = []
+        for e in extra:
+            if e.dtype != torch.float32 or not e.is_cuda or not e.is_contiguous() or \
+                    e.dim() != 2 or e.shape[1] != balls.shape[1]:
+                raise ValueError("extra rows must be contiguous (k, n_cap) float32 CUDA tensors")
+            rows += [e[r].data_ptr() for r in range(e.shape[0])]
+        ptrs = (ctypes.c_void_p * max(1, len(rows)))(*rows)
+        _check("sbp_sort_cloud", self._lib.sbp_sort_cloud(
+            self._h, _rows(balls), _dptr(nd), balls.shape[1], ptrs if rows else None, len(rows),
+            _stream()))
 
     def forward_gauss(self, balls: torch.Tensor, n: torch.Tensor | None = None, out=None):
         """Gaussian-profile traces at the current level (sbp_forward_gauss);
@@ -886,17 +908,30 @@ class VolumeCNN:
             self._h, self._vol(vol), _dptr(occ), _dptr(p0), float(pos_weight), float(lr),
             _dptr(loss), _stream()))
 
+    def grad(self, vol, occ, p0, pos_weight: float = 10.0, loss=None) -> torch.Tensor:
+        """The loss gradient with respect to every parameter (sbp_cnn_grad),
+        as a float32 CUDA tensor of n_params; the parameters are unchanged."""
+        for t in (occ, p0):
+            if t.dtype != torch.float32 or not t.is_cuda or t.numel() != self.V:
+                raise ValueError("targets must be float32 CUDA tensors of nx*ny*nz")
+        out = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
+        _check("sbp_cnn_grad", self._lib.sbp_cnn_grad(
+            self._h, self._vol(vol), _dptr(occ), _dptr(p0), float(pos_weight), _dptr(loss),
+            _dptr(out), _stream()))
+        return out
+
     def propose(self, vol, origin, spacing: float, threshold: float = 0.5, seed: int = 1,
-                R: float = 0.1, p_range=(0.05, 2.0), out=None, n_dev=None):
+                R: float = 0.1, p_range=(0.05, 2.0), out=None, n_dev=None, per_voxel: int = 1):
         if out is None:
-            out = torch.zeros((5, self.V), dtype=torch.float32, device=self.device)
+            out = torch.zeros((5, self.V * int(per_voxel)), dtype=torch.float32,
+                              device=self.device)
         if n_dev is None:
             n_dev = torch.zeros(1, dtype=torch.int32, device=self.device)
         org = (ctypes.c_double * 3)(*[float(v) for v in origin])
         _check("sbp_cnn_propose", self._lib.sbp_cnn_propose(
             self._h, self._vol(vol), float(threshold), int(seed) & (2 ** 64 - 1), org,
-            float(spacing), float(R), float(p_range[0]), float(p_range[1]), _rows(out),
-            out.shape[1], _dptr(n_dev), _stream()))
+            float(spacing), float(R), float(p_range[0]), float(p_range[1]), int(per_voxel),
+            _rows(out), out.shape[1], _dptr(n_dev), _stream()))
         return out, n_dev
 
     def close(self):

@@ -130,3 +130,62 @@ def test_cnn_gradient_matches_central_differences():
         lp = sum(cnn.cnn_loss_grad(p + e, vol, occ, p0, 5.0)[:2])
         lm = sum(cnn.cnn_loss_grad(p - e, vol, occ, p0, 5.0)[:2])
         assert g[i] == pytest.approx((lp - lm) / 2e-6, rel=1e-5, abs=1e-9)
+
+
+def _bf16_forward_states(p, vol):
+    """Hidden activations of the network with bf16 storage, from the pinned
+    pieces (conv3d, bf16_round, scaled_input)."""
+    P = cnn.unpack_params(p)
+    r = lambda a: cnn.bf16_round(a.astype(np.float32)).astype(np.float64)
+    h = cnn.scaled_input(vol)
+    hs, pres = [h], []
+    for k in (1, 2, 3):
+        pre = cnn.conv3d(h, r(P[f"w{k}"]), P[f"b{k}"])
+        h = r(np.maximum(pre, 0.0))
+        pres.append(pre)
+        hs.append(h)
+    return P, hs, pres
+
+
+def test_cnn_gradient_with_bf16_storage_head_and_last_convolution():
+    """With bf16 storage the head's gradient is dout^T h3 with h3 the rounded
+    activation, and the third convolution's weight gradient is
+    sum_v g3[v][n] h2[v + off(tap)][c] with g3 = bf16([h3 > 0] (dout Wh)) and
+    h2 rounded: both written out directly from the pinned forward pieces.
+    Without storage rounding the same gradient differs from it."""
+    pytest.importorskip("torch")
+    rng = np.random.default_rng(12)
+    vol = rng.normal(size=(4, 5, 6))
+    V = vol.size
+    p = random_params(2)
+    occ = (rng.uniform(size=V) < 0.3).astype(np.float64)
+    q0 = rng.uniform(0.2, 1.0, size=V)
+    pw = 5.0
+    _, _, g = cnn.cnn_loss_grad(p, vol, occ, q0, pw, bf16_storage=True)
+    P, hs, pres = _bf16_forward_states(p, vol)
+    h3 = hs[3].reshape(V, -1)
+    out = h3 @ P["wh"].T + P["bh"]
+    z, q = out[:, 0], out[:, 1]
+    sg = 1.0 / (1.0 + np.exp(-z))
+    dout = np.stack([(pw * occ * (sg - 1.0) + (1.0 - occ) * sg) / V,
+                     2.0 * occ * (q - q0) / V], axis=1)
+    names = [n for n, _ in cnn.PARAM_SHAPES]
+    offs = np.cumsum([0] + [int(np.prod(s)) for _, s in cnn.PARAM_SHAPES])
+    blk = lambda n: g[offs[names.index(n)]:offs[names.index(n) + 1]]
+    np.testing.assert_allclose(blk("wh"), (dout.T @ h3).reshape(-1), rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(blk("bh"), dout.sum(axis=0), rtol=1e-10, atol=1e-14)
+    g3 = (dout @ P["wh"]) * (pres[2].reshape(V, -1) > 0)
+    g3 = cnn.bf16_round(g3.astype(np.float32)).astype(np.float64)
+    h2 = hs[2]
+    nz, ny, nx, cin = h2.shape
+    hp = np.zeros((nz + 2, ny + 2, nx + 2, cin))
+    hp[1:-1, 1:-1, 1:-1] = h2
+    dw3 = np.zeros(P["w3"].shape)
+    for tap in range(27):
+        dz, dy, dx = tap // 9 - 1, (tap // 3) % 3 - 1, tap % 3 - 1
+        sl = hp[1 + dz:1 + dz + nz, 1 + dy:1 + dy + ny, 1 + dx:1 + dx + nx].reshape(V, cin)
+        dw3[:, tap, :] = g3.T @ sl
+    np.testing.assert_allclose(blk("w3"), dw3.reshape(-1), rtol=1e-9, atol=1e-14)
+    np.testing.assert_allclose(blk("b3"), g3.sum(axis=0), rtol=1e-9, atol=1e-14)
+    _, _, g_exact = cnn.cnn_loss_grad(p, vol, occ, q0, pw)
+    assert not np.allclose(g_exact, g, rtol=1e-6, atol=0)

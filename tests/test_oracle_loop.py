@@ -248,3 +248,39 @@ def test_growth_in_the_loop_uses_the_step_count_as_seed():
                        dataclasses.replace(gpar, seed=101, grad_mask=mask))[0]
     assert out.shape[1] > 16
     np.testing.assert_array_equal(out, want)
+
+
+# ------------------------------------------------------- spatial ordering
+
+def test_morton_key_of_the_cube_corners_and_bits():
+    """The corners of a 4 mm cube: a coordinate at the far side quantises to
+    1023 (floor(4 * 1024 / 4) clamped), so corner (x, y, z) in {0, 1}^3 gets
+    all ten bits of each set axis, x lowest: the octal digits of its key are
+    all x + 2y + 4z. A point halfway along x alone is q_x = 512: bit 27."""
+    corners = [(x, y, z) for z in (0, 1) for y in (0, 1) for x in (0, 1)]
+    b = np.zeros((5, 8), np.float32)
+    b[:3] = 4.0 * np.array(corners, np.float32).T
+    want = [int(str(x + 2 * y + 4 * z) * 10, 8) for x, y, z in corners]
+    np.testing.assert_array_equal(oracle.morton_key(b), want)
+    b2 = np.zeros((5, 3), np.float32)
+    b2[:3, 1] = [4.0, 4.0, 4.0]
+    b2[:3, 2] = [2.0, 0.0, 0.0]
+    k = oracle.morton_key(b2)
+    assert k[0] == 0 and k[1] == (1 << 30) - 1 and k[2] == 1 << 27
+
+
+def test_morton_permutation_is_stable_and_orders_the_keys():
+    rng = np.random.default_rng(40)
+    b = np.zeros((5, 500), np.float32)
+    b[:3] = rng.integers(0, 4, size=(3, 500)).astype(np.float32)  # many equal keys
+    b[3:] = rng.uniform(size=(2, 500))
+    perm = oracle.morton_permutation(b)
+    np.testing.assert_array_equal(np.sort(perm), np.arange(500))
+    k = oracle.morton_key(b)[perm]
+    assert np.all(np.diff(k) >= 0)
+    for key in np.unique(k):  # equal keys keep their index order
+        same = perm[k == key]
+        assert np.all(np.diff(same) > 0)
+    # the order depends on the centres only, and brute force agrees
+    brute = sorted(range(500), key=lambda i: (int(oracle.morton_key(b)[i]), i))
+    np.testing.assert_array_equal(perm, brute)
