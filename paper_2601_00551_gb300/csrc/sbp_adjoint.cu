@@ -241,7 +241,8 @@ template <bool P0_ONLY, int WMODE>
 __global__ void __launch_bounds__(kAdjThreads, P0_ONLY ? 10 : 7)
 adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, LevelGeo g,
                  const float* __restrict__ G_all, unsigned mask, GradOut out,
-                 float* __restrict__ part_all, unsigned int* __restrict__ tickets, int split) {
+                 float* __restrict__ part_all, unsigned int* __restrict__ tickets, int split,
+                 bool vec) {
     // two staging buffers of kCap cells, each holding the windows of one
     // group of sensors packed one after another
     constexpr int kCap = P0_ONLY ? kAdjCapP0 : kAdjCap;
@@ -342,7 +343,11 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
             sbp_box_cells(sx, sy, sz, s_box, g, jlo, jhi);
             // staged through the box's last cell even past the record (zeros there)
             jhi = max(jhi, adj_box_hi(sx, sy, sz, s_box, g));
+            // with 16-byte copies a window starts on a 4-cell boundary and
+            // holds a multiple of 4 cells
+            if (vec) jlo &= ~3;
             int len = max(0, jhi - jlo + 1);
+            if (vec) len = (len + 3) & ~3;
             if (len > kWin) len = 0;
             q0f[at(t, 0)] = sx;
             q0f[at(t, 1)] = sy;
@@ -431,11 +436,27 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
                 const float* row = G + (size_t)(mb + s) * Tk + jlo;
                 float* d = dst + qoi[s];
                 const int inrec = min(len, Tk - jlo);  // cells before the record's end
-                for (int r = lane; r < len; r += 32) {
-                    if (r < inrec)
-                        __pipeline_memcpy_async(d + r, row + r, sizeof(float));
-                    else
-                        d[r] = 0.0f;
+                if (vec) {
+                    for (int r = 4 * lane; r < len; r += 128) {
+                        if (r + 4 <= inrec) {
+                            __pipeline_memcpy_async(d + r, row + r, 16);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                if (r + c < inrec)
+                                    __pipeline_memcpy_async(d + r + c, row + r + c, sizeof(float));
+                                else
+                                    d[r + c] = 0.0f;
+                            }
+                        }
+                    }
+                } else {
+                    for (int r = lane; r < len; r += 32) {
+                        if (r < inrec)
+                            __pipeline_memcpy_async(d + r, row + r, sizeof(float));
+                        else
+                            d[r] = 0.0f;
+                    }
                 }
             }
         };
@@ -665,10 +686,12 @@ int launch_adj(sbp_array_s* a, const FrameTable& ft, int total, int split, const
         return SBP_ERR_ARG;
     }
     const unsigned grid = (unsigned)chunks * (unsigned)split;
+    // 16-byte staging copies need every residual row 16-byte aligned
+    const bool vec = (g.Tk % 4 == 0) && ((reinterpret_cast<uintptr_t>(G) & 15u) == 0);
     auto go = [&](auto p0_only, auto wmode) {
         adj_group_kernel<decltype(p0_only)::value, decltype(wmode)::value>
             <<<grid, kAdjThreads, 0, st>>>(b, ft, a->d_sens, g, G, mask, o, a->d_adj_part,
-                                           a->d_adj_ticket, split);
+                                           a->d_adj_ticket, split, vec);
     };
     auto by_mode = [&](auto p0_only) {
         if (g.wmode == SBP_W_NONE)

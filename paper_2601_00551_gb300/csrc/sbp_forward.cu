@@ -49,7 +49,7 @@
 namespace {
 
 constexpr int kGroupWarps = 16;     // warps per forward CTA
-constexpr int kWindow = 384;        // cells per sensor held in shared memory
+constexpr int kWindow = 416;        // cells per sensor held in shared memory
 constexpr int kChunk = 512;         // largest number of balls per CTA
 constexpr int kLoBits = 20;         // 2 * kChunk * 2^kLoBits < 2^32
 static_assert(2LL * kChunk * (1LL << kLoBits) < (1LL << 32), "low word could overflow");
