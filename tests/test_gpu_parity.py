@@ -462,6 +462,49 @@ def test_reconstruct_matches_oracle_loop(sb):
     np.testing.assert_allclose(out, bo, rtol=0, atol=1e-4)
 
 
+def test_fifty_iteration_run_matches_the_oracle_loop(sb):
+    """The 2,000-ball x 64-sensor configuration as its survey states it:
+    zero-gradient filtering, then 50 Adam iterations of forward, adjoint and
+    filter/grow at 40 MHz, through sbp_reconstruct against the oracle's loop.
+    Ball counts per iteration are compared exactly; losses within 1e-3 (float32
+    against float64 over 50 coupled iterations). The final cloud is compared
+    in units of the learning rate (1e-3 mm for the position and radius, 1e-2
+    for p0), the size of one Adam step, lr m_hat / sqrt(v_hat): where a
+    component's gradient sits near zero, round-off can flip the sign of a
+    step, so single elements may differ by a few steps (bound: five); the
+    root-mean-square difference of every row stays within a tenth of one."""
+    wl = workloads.tiny()
+    b = wl.init.stack()
+    n = b.shape[1]
+    y = _measured(wl, 1)
+    arr = make_array(sb, wl, (1,), 2 * n)
+    st_o = [oracle.Stage(0, 50, 7, True, False)]
+    st_g = [sb.Stage(0, 50, 7, True, False)]
+    grow = dict(p_min=1e-3, R_min=0.02, R_max=0.3, g_dup=5.0, seed=5)
+    bo, losses, counts = oracle.reconstruct(b, wl.sensors.pos, wl.sensors.normal, wl.c,
+                                            wl.fs_mhz, wl.T, (1,), y, st_o,
+                                            grow_params=oracle.GrowParams(**grow),
+                                            threads=threads())
+    balls = torch.zeros((5, 2 * n), device="cuda")
+    balls[:, :n] = torch.from_numpy(b)
+    n_dev = torch.tensor([n], dtype=torch.int32, device="cuda")
+    loss = torch.zeros(50, dtype=torch.float64, device="cuda")
+    n_log = torch.zeros(50, dtype=torch.int32, device="cuda")
+    arr.reconstruct(torch.from_numpy(y).cuda(), balls, n_dev, st_g, grow=sb.GrowParams(**grow),
+                    loss_log=loss, n_log=n_log)
+    assert arr.sync_status() == 0
+    np.testing.assert_array_equal(n_log.cpu().numpy(), counts)
+    np.testing.assert_allclose(loss.cpu().numpy(), losses, rtol=1e-3)
+    assert losses[-1] < 0.5 * losses[0]
+    assert int(n_dev.item()) == bo.shape[1]
+    out = balls[:, :bo.shape[1]].cpu().numpy()
+    lr = np.array(sb.AdamParams().lr)
+    for k in range(5):
+        d = out[k].astype(np.float64) - bo[k]
+        assert np.sqrt(np.mean(d * d)) <= 0.1 * lr[k], (k, np.sqrt(np.mean(d * d)))
+        np.testing.assert_allclose(out[k], bo[k], rtol=0, atol=5 * lr[k])
+
+
 # --------------------------------------------------------------- autograd
 
 def test_autograd_function_matches_oracle_adjoint(sb):
