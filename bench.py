@@ -364,10 +364,14 @@ def measure_step(args, sb, ctx, local, tune=True, graph=True, clocks=True):
     stream = torch.cuda.current_stream()
 
     tiles = {}
-    if tune:  # tiles per level, tuned (untimed) on the initial cloud
+    if tune:
+        # tiles per level, tuned (untimed) on the cloud one step leaves: the
+        # filtered cloud that every level's iteration works on, not the
+        # initial one (twice as dense, so its chunks span fewer cells)
+        ctx.step(sb)
         for k in range(nl):
             arr.set_sampling_level(k)
-            tiles[k] = arr.autotune(ctx.init, n=ctx.n_init)
+            tiles[k] = arr.autotune(ctx.balls, n=ctx.n_dev)
 
     # warm-up; the workload is deterministic, so every step sees the same counts
     for _ in range(max(0, args.warmup)):
@@ -464,7 +468,7 @@ def measure_step(args, sb, ctx, local, tune=True, graph=True, clocks=True):
             "pairs_per_step": pairs_per_step,
             "l2": "flushed before every timed step (512 MB write)",
             "launch": launch_mode,
-            "tiles": ({f"{wl.fs_mhz / wl.levels[k]:g}MHz": {"forward_balls_per_cta": c or "default",
+            "tiles": ({f"{wl.fs_mhz / wl.levels[k]:g}MHz": {**fwd_tile_desc(c),
                                                            "adjoint_ctas_per_chunk": sp or "default"}
                        for k, (c, sp) in tiles.items()} if tiles else "default"),
         },
@@ -489,6 +493,15 @@ def measure_step(args, sb, ctx, local, tune=True, graph=True, clocks=True):
 # on average (R the mean radius of the live cloud, h = c dt_k the sample
 # spacing of the level). This is the count the roofline fraction is taken
 # against; the kernels' own executed instruction counts come from ncu.
+def fwd_tile_desc(tile):
+    """A forward tile value (set_tiles / autotune) as report fields: balls
+    per CTA and the trace cells per sensor held in shared memory."""
+    if not tile:
+        return {"forward_balls_per_cta": "default"}
+    wide = bool(tile & 0x10000)
+    return {"forward_balls_per_cta": tile & 0xFFFF, "forward_window_cells": 832 if wide else 416}
+
+
 def samples_per_pair(mean_R, h):
     return 2.0 * mean_R / h + 1.0
 
@@ -542,10 +555,10 @@ def ncu_record(name):
 def alu_peak_gops(clk):
     """152 SMs x 4 schedulers x 32 lanes issue one thread operation per lane
     and cycle: 152 x 128 x the median SM clock sampled during the timed steps
-    (the MEASURED_PEAKS clock under load, else 1492 MHz, if none)."""
+    (if none was sampled, the largest SM clock of the measured peaks, else
+    2070 MHz: the higher clock, so that the fraction is not overstated)."""
     peaks = measured_peaks()
-    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get(
-        "sm_mhz_median") or 1492.0
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
     return 152 * 128 * sm_mhz * 1e6 / 1e9, sm_mhz
 
 
@@ -1524,7 +1537,7 @@ def batched_frames(args, sb, dev, steps=8, warmup=3, profile=False):
         "balls_init_range": [int(counts0.min()), int(counts0.max())],
         "pairs_per_step": pairs, "steps": steps, "warmup": warmup,
         "counts_identical_across_arms": bool(same),
-        "autotuned": {"forward_balls_per_cta": chunk, "adjoint_ctas_per_chunk": split},
+        "autotuned": {**fwd_tile_desc(chunk), "adjoint_ctas_per_chunk": split},
         "kernel_launches_per_step": launches,
         **out,
         "speedup_batched_graph_vs_per_frame": (out["per_frame"]["ms_per_step"] /
@@ -1667,8 +1680,7 @@ def large_config(sb, dev, reps=3, tune=True):
         res["default_tiles_ms"] = {"forward": res["forward_ms"], "adjoint": res["adjoint_ms"]}
         if tune:
             c, sp = arr.autotune(B, G=G)
-            res["tiles"] = {"forward_balls_per_cta": c or "default",
-                            "adjoint_ctas_per_chunk": sp or "default"}
+            res["tiles"] = {**fwd_tile_desc(c), "adjoint_ctas_per_chunk": sp or "default"}
             timed()
         h = wl.c * f / wl.fs_mhz
         res["forward_pairs_per_s"] = pairs / (res["forward_ms"] * 1e-3)

@@ -214,14 +214,20 @@ int sbp_adjoint(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap,
  * (a launch parameter only: the forward is bitwise identical for every
  * choice, the adjoint differs by float summation order). fwd_chunk: balls
  * per forward CTA, 0 (default: 512, fewer for small clouds) or a power of
- * two in [32, 1024]; adj_split: adjoint CTAs sharing a ball chunk, each
- * taking a share of the sensors, 0 (default 8), 1, 2, 4 or 8. SBP_ERR_ARG
- * for other values, SBP_ERR_LEVEL for k out of range. */
+ * two in [32, 1024], optionally or'ed with SBP_TILE_WIDE (each CTA holds
+ * 832 instead of 416 trace cells per sensor in shared memory and runs 32
+ * warps, one CTA per SM: fewer impulses spill to the global accumulators
+ * when a chunk spans many cells, at the finest sampling rates); adj_split:
+ * adjoint CTAs sharing a ball chunk, each taking a share of the sensors,
+ * 0 (default 8), 1, 2, 4 or 8. SBP_ERR_ARG for other values, SBP_ERR_LEVEL
+ * for k out of range. */
+enum { SBP_TILE_WIDE = 0x10000 };
 int sbp_set_tiles(sbp_array arr, int k, int fwd_chunk, int adj_split);
 int sbp_get_tiles(sbp_array arr, int k, int* fwd_chunk, int* adj_split);
 
 /* Tile autotuner for the current level: times sbp_forward with the default
- * tile and with 128, 256, 512 and 1024 balls per CTA, and sbp_adjoint (all
+ * tile and with 128, 256, 512 and 1024 balls per CTA and 512 and 1024 with
+ * SBP_TILE_WIDE, and sbp_adjoint (all
  * components) with the default and with 1, 2, 4 and 8 CTAs per ball chunk, on
  * the given cloud; keeps for this level (as sbp_set_tiles would) the
  * fastest choice of each if it beats the default by more than 3%, else the
@@ -370,7 +376,7 @@ int sbp_reconstruct_frames(sbp_array arr, const float* y_full_dev, sbp_balls pac
                            const sbp_recon_params* rp, sbp_stream stream);
 
 /* Tile autotuner for the batched path: times the forward with 256, 512 and
- * 1024 balls per CTA and the adjoint with 1, 2, 4 and 8 CTAs per ball chunk on
+ * 1024 balls per CTA and 1024 with SBP_TILE_WIDE, and the adjoint with 1, 2, 4 and 8 CTAs per ball chunk on
  * the given cloud at the current level (S_dev, G_dev: [F][M][T_k] scratch of
  * the caller, overwritten), keeps the fastest of each for later batched
  * calls and reports them. Synchronises. */

@@ -29,6 +29,13 @@
 //                 int64 accumulators with global atomics. Where a window is
 //                 longer than the shared buffer, the impulses past its end
 //                 go straight to the global accumulators.
+//                 Two shapes: narrow (416 cells per sensor, 16 warps, two
+//                 CTAs per SM) and wide (832 cells, 32 warps, one CTA per
+//                 SM). The flush costs about one global atomic per window
+//                 cell, i.e. (window cells) / (balls per chunk) per pair, and
+//                 the window grows with the chunk's extent in cells; at the
+//                 finest sampling rates the wide shape lets a chunk of 1024
+//                 balls keep its window on chip where the narrow one spills.
 //                 A 64-bit shared atomic add costs several times a 32-bit one
 //                 on this GPU, so each int64 impulse v is added as two 32-bit
 //                 words: v mod 2^32 and v >> kLoBits (signed). The high word
@@ -48,8 +55,10 @@
 
 namespace {
 
-constexpr int kGroupWarps = 16;     // warps per forward CTA
-constexpr int kWindow = 416;        // cells per sensor held in shared memory
+constexpr int kWarpsNarrow = 16;    // warps per forward CTA, narrow shape
+constexpr int kWindowNarrow = 416;  // cells per sensor held in shared memory, narrow shape
+constexpr int kWarpsWide = 32;      // the same for the wide shape
+constexpr int kWindowWide = 832;
 constexpr int kChunk = 512;         // largest number of balls per CTA
 constexpr int kLoBits = 20;         // 2 * kChunk * 2^kLoBits < 2^32
 static_assert(2LL * kChunk * (1LL << kLoBits) < (1LL << 32), "low word could overflow");
@@ -95,17 +104,19 @@ __device__ __forceinline__ long long fwd_f2ll(float x) {
 }
 
 // Adds the int64 impulse v to the split accumulator word pair at `lo` (the
-// high word sits kWindow * 32 words further on).
+// high word sits WIN * 32 words further on).
+template <int WIN>
 __device__ __forceinline__ void fwd_add(unsigned int* lo, long long v) {
     atomicAdd(lo, (unsigned int)v);
-    atomicAdd(lo + kWindow * 32, (unsigned int)(int)(v >> kLoBits));
+    atomicAdd(lo + WIN * 32, (unsigned int)(int)(v >> kLoBits));
 }
 
 // The same for an impulse that fits in 32 bits (its arithmetic shift gives
 // the same high word as the 64-bit one).
+template <int WIN>
 __device__ __forceinline__ void fwd_add32(unsigned int* lo, int v) {
     atomicAdd(lo, (unsigned int)v);
-    atomicAdd(lo + kWindow * 32, (unsigned int)(v >> kLoBits));
+    atomicAdd(lo + WIN * 32, (unsigned int)(v >> kLoBits));
 }
 
 // Adds one pair's six second-difference impulses to the lane's column of the
@@ -116,6 +127,7 @@ __device__ __forceinline__ void fwd_add32(unsigned int* lo, int v) {
 // inside the record (relative cells -base .. glim) are added straight to the
 // lane's global accumulator row grow (indexed relative to the window start);
 // cells past the record are dropped (they cannot reach a stored sample).
+template <int WIN>
 __device__ __forceinline__ void fwd_emit(unsigned int* col, unsigned long long* grow, int ra,
                                          int rb, int L, int lim, int base, int glim, float fa,
                                          float fe, float f1, float f2) {
@@ -128,13 +140,13 @@ __device__ __forceinline__ void fwd_emit(unsigned int* col, unsigned long long* 
         const int q1 = __float2int_rn(f1), q2 = __float2int_rn(f2);
         const int Lq2 = L * q2;
         unsigned int* a = col + ra * 32;
-        fwd_add32(a, qa);
-        fwd_add32(a + 32, q1 - 2 * qa);
-        fwd_add32(a + 64, qa - q1 + q2);
+        fwd_add32<WIN>(a, qa);
+        fwd_add32<WIN>(a + 32, q1 - 2 * qa);
+        fwd_add32<WIN>(a + 64, qa - q1 + q2);
         unsigned int* c = col + rb * 32;
-        fwd_add32(c, qe - q1 - Lq2);
-        fwd_add32(c + 32, q1 + Lq2 - q2 - 2 * qe);
-        fwd_add32(c + 64, qe);
+        fwd_add32<WIN>(c, qe - q1 - Lq2);
+        fwd_add32<WIN>(c + 32, q1 + Lq2 - q2 - 2 * qe);
+        fwd_add32<WIN>(c + 64, qe);
         return;
     }
     const long long qa = fwd_f2ll(fa), qe = fwd_f2ll(fe);
@@ -147,15 +159,15 @@ __device__ __forceinline__ void fwd_emit(unsigned int* col, unsigned long long* 
     const long long ib0 = qe - q1 - Lq2, ib1 = q1 + Lq2 - q2 - 2 * qe, ib2 = qe;
     auto put = [&](int r, long long v) {
         if (r >= 0 && r <= lim)
-            fwd_add(col + r * 32, v);
+            fwd_add<WIN>(col + r * 32, v);
         else if (r >= -base && r <= glim)
             atomicAdd(grow + r, (unsigned long long)v);
     };
     if (fast_a) {
         unsigned int* a = col + ra * 32;
-        fwd_add(a, ia0);
-        fwd_add(a + 32, ia1);
-        fwd_add(a + 64, ia2);
+        fwd_add<WIN>(a, ia0);
+        fwd_add<WIN>(a + 32, ia1);
+        fwd_add<WIN>(a + 64, ia2);
     } else {
         put(ra, ia0);
         put(ra + 1, ia1);
@@ -163,9 +175,9 @@ __device__ __forceinline__ void fwd_emit(unsigned int* col, unsigned long long* 
     }
     if (fast_b) {
         unsigned int* c = col + rb * 32;
-        fwd_add(c, ib0);
-        fwd_add(c + 32, ib1);
-        fwd_add(c + 64, ib2);
+        fwd_add<WIN>(c, ib0);
+        fwd_add<WIN>(c + 32, ib1);
+        fwd_add<WIN>(c + 64, ib2);
     } else {
         put(rb, ib0);
         put(rb + 1, ib1);
@@ -183,12 +195,14 @@ __device__ __forceinline__ int fwd_frac_bits(unsigned int pmax_bits) {
 }
 
 // WMODE: the orientation weight (SBP_W_*), fixed at compile time so that no
-// pair branches on it; fwd_group_for picks the instance.
-template <int WMODE>
-__global__ void __launch_bounds__(kGroupWarps * 32, 2)
+// pair branches on it; WIDE: the wide shape. FwdTile picks the instance.
+template <int WMODE, bool WIDE>
+__global__ void __launch_bounds__((WIDE ? kWarpsWide : kWarpsNarrow) * 32, WIDE ? 1 : 2)
 fwd_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, LevelGeo g,
                  int chunk, const unsigned int* __restrict__ pmax, SbpDevState* st,
                  unsigned long long* __restrict__ acc_all) {
+    constexpr int kGroupWarps = WIDE ? kWarpsWide : kWarpsNarrow;
+    constexpr int kWindow = WIDE ? kWindowWide : kWindowNarrow;
     extern __shared__ unsigned int sacc[];  // [2][kWindow][32]: low words, then high words
     __shared__ float s_red[kGroupWarps * 7];
     __shared__ float s_box[7];
@@ -308,27 +322,56 @@ fwd_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
         const float2 f1 = f2mul(f2mul(Ks, f2(h)), f2fma(f2(2.0f), b0, f2(-h)));
         const float2 fq = f2mul(Ks, f2(d2c));
         if (okA)
-            fwd_emit(col, grow, wa.jL - 1 - base, wa.jH - base, wa.jH - wa.jL, lim, base, glim,
+            fwd_emit<kWindow>(col, grow, wa.jL - 1 - base, wa.jH - base, wa.jH - wa.jL, lim, base, glim,
                      fa.x, fe.x, f1.x, fq.x);
         if (okB)
-            fwd_emit(col, grow, wb.jL - 1 - base, wb.jH - base, wb.jH - wb.jL, lim, base, glim,
+            fwd_emit<kWindow>(col, grow, wb.jL - 1 - base, wb.jH - base, wb.jH - wb.jL, lim, base, glim,
                      fa.y, fe.y, f1.y, fq.y);
     }
     __syncthreads();
-    // flush: lanes of a warp read 32 consecutive words (one cell of all 32
-    // sensors), recombine the two halves and add them to the global rows
-    for (int t = threadIdx.x; t < used; t += blockDim.x) {
-        const unsigned int wa = sacc[t];
-        const int hi = (int)sacc[kWindow * 32 + t];
-        if (wa | (unsigned)hi) {
-            // the low word holds the whole sum mod 2^32; the sum of the low
-            // kLoBits-bit parts lies in [0, 2^32), so it is that word minus
-            // hi * 2^kLoBits, mod 2^32
-            const unsigned int lo = wa - ((unsigned int)hi << kLoBits);
-            const long long v = (long long)hi * (1LL << kLoBits) + (long long)lo;
-            const int ln = t & 31, rel = t >> 5;
-            const int j = s_jlo[ln] + rel;
-            atomicAdd(acc + (size_t)(gid * 32 + ln) * Tk + j, (unsigned long long)v);
+    // Flush, one block of 32 window cells per warp at a time. The warp first
+    // transposes the block's 32 x 32 low words and 32 x 32 high words in
+    // place, from [cell][lane] to [lane][cell], so that it then adds each
+    // sensor's 32 consecutive cells to its global row with one coalesced
+    // instruction (straight from the [cell][lane] layout, every instruction
+    // would scatter over 32 rows, one 32-byte sector per 8-byte sum).
+    // The transpose swaps (r, r + k) with (r + k, r) for r = lane and
+    // k = 1 .. 16 (at k = 16 the lower 16 lanes take the pairs): every
+    // off-diagonal element moves once, and each step's 32 accesses fall in
+    // 32 distinct banks. kWindow is a multiple of 32, so the blocks stay
+    // inside the window; cells at or past `nrel` were never cleared and are
+    // not flushed.
+    static_assert(kWindow % 32 == 0, "the flush transposes whole 32-cell blocks");
+    const int nrel = min(wmax, kWindow);
+    for (int blk = warp; blk * 32 < nrel; blk += kGroupWarps) {
+        unsigned int* const blo = sacc + blk * 32 * 32;
+        unsigned int* const bhi = blo + kWindow * 32;
+#pragma unroll 4
+        for (int k = 1; k <= 16; ++k) {
+            if (k < 16 || lane < 16) {
+                const int c = (lane + k) & 31;
+                const int p = lane * 32 + c, q = c * 32 + lane;
+                const unsigned int l0 = blo[p], l1 = blo[q], h0 = bhi[p], h1 = bhi[q];
+                blo[p] = l1;
+                blo[q] = l0;
+                bhi[p] = h1;
+                bhi[q] = h0;
+            }
+        }
+        __syncwarp();
+        const int rel = blk * 32 + lane;
+        for (int x = 0; x < 32; ++x) {
+            const unsigned int wa = blo[x * 32 + lane];
+            const int hi = (int)bhi[x * 32 + lane];
+            if ((wa | (unsigned)hi) && rel < nrel) {
+                // the low word holds the whole sum mod 2^32; the sum of the
+                // low kLoBits-bit parts lies in [0, 2^32), so it is that word
+                // minus hi * 2^kLoBits, mod 2^32
+                const unsigned int lo = wa - ((unsigned int)hi << kLoBits);
+                const long long v = (long long)hi * (1LL << kLoBits) + (long long)lo;
+                atomicAdd(acc + (size_t)(gid * 32 + x) * Tk + s_jlo[x] + rel,
+                          (unsigned long long)v);
+            }
         }
     }
     if (inside) atomicAdd(&st->inside_pairs, (unsigned long long)inside);
@@ -394,11 +437,46 @@ fwd_finalize_kernel(unsigned long long* __restrict__ acc, int Tk,
 using FwdGroupKernel = void (*)(BallsDev, FrameTable, const float*, LevelGeo, int,
                                 const unsigned int*, SbpDevState*, unsigned long long*);
 
-// The accumulation kernel compiled for one orientation weight (SBP_W_*).
-static FwdGroupKernel fwd_group_for(int wmode) {
-    if (wmode == SBP_W_NONE) return fwd_group_kernel<SBP_W_NONE>;
-    if (wmode == SBP_W_COS) return fwd_group_kernel<SBP_W_COS>;
-    return fwd_group_kernel<SBP_W_CLAMP>;
+// The accumulation kernel compiled for one orientation weight (SBP_W_*) and
+// shape.
+template <bool WIDE>
+static FwdGroupKernel fwd_group_shape(int wmode) {
+    if (wmode == SBP_W_NONE) return fwd_group_kernel<SBP_W_NONE, WIDE>;
+    if (wmode == SBP_W_COS) return fwd_group_kernel<SBP_W_COS, WIDE>;
+    return fwd_group_kernel<SBP_W_CLAMP, WIDE>;
+}
+
+// A tile: balls per CTA and shape, decoded from a tile value (a power of
+// two in [32, SBP_FRAME_ALIGN], optionally or'ed with SBP_TILE_WIDE).
+struct FwdTile {
+    int chunk;
+    bool wide;
+    FwdGroupKernel kernel(int wmode) const {
+        return wide ? fwd_group_shape<true>(wmode) : fwd_group_shape<false>(wmode);
+    }
+    int threads() const { return 32 * (wide ? kWarpsWide : kWarpsNarrow); }
+    size_t smem() const {
+        return (size_t)2 * (wide ? kWindowWide : kWindowNarrow) * 32 * sizeof(unsigned int);
+    }
+};
+
+static int fwd_set_smem(const FwdTile& t, int wmode, const char* what) {
+    return sbp_cuda_check(cudaFuncSetAttribute(t.kernel(wmode),
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)t.smem()),
+                          what);
+}
+
+bool sbp_fwd_tile_valid(int tv) {
+    const int c = tv & ~SBP_TILE_WIDE;
+    return (tv & ~(SBP_TILE_WIDE | (2 * SBP_FRAME_ALIGN - 1))) == 0 && c >= 32 &&
+           c <= SBP_FRAME_ALIGN && !(c & (c - 1));
+}
+
+// The tile of a valid tile value, else `fallback`.
+static FwdTile fwd_tile_of(int tv, FwdTile fallback) {
+    return sbp_fwd_tile_valid(tv) ? FwdTile{tv & ~SBP_TILE_WIDE, (tv & SBP_TILE_WIDE) != 0}
+                                  : fallback;
 }
 
 int sbp_launch_forward(sbp_array_s* a, const BallsDev& b, const int* n_dev, int n_cap,
@@ -408,18 +486,13 @@ int sbp_launch_forward(sbp_array_s* a, const BallsDev& b, const int* n_dev, int 
     // consecutive balls per CTA: the level's tuned size if sbp_autotune chose
     // one, else kChunk, fewer for small clouds so that the grid still covers
     // the GPU
-    int chunk = a->fwd_chunk_lvl[a->level];
-    if (chunk < 32 || chunk > SBP_FRAME_ALIGN || (SBP_FRAME_ALIGN % chunk)) {
-        chunk = kChunk;
-        while (chunk > 32 && (long long)((n_cap + chunk - 1) / chunk) * groups < 4LL * a->sm_count)
-            chunk >>= 1;
-    }
-    const size_t smem = (size_t)2 * kWindow * 32 * sizeof(unsigned int);
-    if (sbp_cuda_check(cudaFuncSetAttribute(fwd_group_for(g.wmode),
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem),
-                       "forward: smem attribute"))
-        return SBP_ERR_CUDA;
+    FwdTile tile{kChunk, false};
+    while (tile.chunk > 32 &&
+           (long long)((n_cap + tile.chunk - 1) / tile.chunk) * groups < 4LL * a->sm_count)
+        tile.chunk >>= 1;
+    tile = fwd_tile_of(a->fwd_chunk_lvl[a->level], tile);
+    const int chunk = tile.chunk;
+    if (fwd_set_smem(tile, g.wmode, "forward: smem attribute")) return SBP_ERR_CUDA;
     if (sbp_cuda_check(cudaMemsetAsync(&a->d_state->pmax_bits, 0, sizeof(unsigned int), st),
                        "forward: reset pmax"))
         return SBP_ERR_CUDA;
@@ -428,7 +501,7 @@ int sbp_launch_forward(sbp_array_s* a, const BallsDev& b, const int* n_dev, int 
                       st>>>(b, ft, &a->d_state->pmax_bits, a->d_state);
     if (sbp_cuda_check(cudaGetLastError(), "forward: pmax launch")) return SBP_ERR_CUDA;
     const unsigned grid = (unsigned)(((long long)n_cap + chunk - 1) / chunk * groups);
-    fwd_group_for(g.wmode)<<<grid, kGroupWarps * 32, smem, st>>>(
+    tile.kernel(g.wmode)<<<grid, tile.threads(), tile.smem(), st>>>(
         b, ft, a->d_sens, g, chunk, &a->d_state->pmax_bits, a->d_state, a->d_acc);
     if (sbp_cuda_check(cudaGetLastError(), "forward: accumulate launch")) return SBP_ERR_CUDA;
     fwd_finalize_kernel<<<g.M, kFinalizeThreads, 0, st>>>(a->d_acc, g.Tk,
@@ -445,13 +518,9 @@ int sbp_launch_forward_frames(sbp_array_s* a, const BallsDev& b, const int* n_de
     const int F = a->frames;
     const int total = a->h_frame_off[F];
     const int groups = (g.M + 31) / 32;
-    if (chunk < 32 || chunk > SBP_FRAME_ALIGN || (SBP_FRAME_ALIGN % chunk)) chunk = kChunk;
-    const size_t smem = (size_t)2 * kWindow * 32 * sizeof(unsigned int);
-    if (sbp_cuda_check(cudaFuncSetAttribute(fwd_group_for(g.wmode),
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem),
-                       "forward_frames: smem attribute"))
-        return SBP_ERR_CUDA;
+    const FwdTile tile = fwd_tile_of(chunk, FwdTile{kChunk, false});
+    chunk = tile.chunk;
+    if (fwd_set_smem(tile, g.wmode, "forward_frames: smem attribute")) return SBP_ERR_CUDA;
     // one fixed-point scale per frame, so that every frame's traces equal
     // those of a single-cloud forward of that frame
     if (sbp_cuda_check(cudaMemsetAsync(a->d_frame_pmax, 0, sizeof(unsigned int) * F, st),
@@ -462,8 +531,8 @@ int sbp_launch_forward_frames(sbp_array_s* a, const BallsDev& b, const int* n_de
     fwd_pmax_kernel<<<dim3(pmax_blocks, F), 256, 0, st>>>(b, ft, a->d_frame_pmax, a->d_state);
     if (sbp_cuda_check(cudaGetLastError(), "forward_frames: pmax launch")) return SBP_ERR_CUDA;
     const unsigned grid = (unsigned)(((long long)total + chunk - 1) / chunk * groups);
-    fwd_group_for(g.wmode)<<<grid, kGroupWarps * 32, smem, st>>>(b, ft, a->d_sens, g, chunk,
-                                                           a->d_frame_pmax, a->d_state, a->d_acc);
+    tile.kernel(g.wmode)<<<grid, tile.threads(), tile.smem(), st>>>(
+        b, ft, a->d_sens, g, chunk, a->d_frame_pmax, a->d_state, a->d_acc);
     if (sbp_cuda_check(cudaGetLastError(), "forward_frames: accumulate launch"))
         return SBP_ERR_CUDA;
     fwd_finalize_kernel<<<dim3(g.M, F), kFinalizeThreads, 0, st>>>(a->d_acc, g.Tk,
@@ -622,21 +691,18 @@ extern "C" int sbp_forward_static(const float* sensors_dev, int M, double c_mm_p
                        "forward_static: clear scratch"))
         return SBP_ERR_CUDA;
     const int groups = (M + 31) / 32;
-    int chunk = kChunk;
-    while (chunk > 32 && (long long)((n_cap + chunk - 1) / chunk) * groups < 4LL * sms) chunk >>= 1;
-    const size_t smem = (size_t)2 * kWindow * 32 * sizeof(unsigned int);
-    if (sbp_cuda_check(cudaFuncSetAttribute(fwd_group_for(g.wmode),
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem),
-                       "forward_static: smem attribute"))
-        return SBP_ERR_CUDA;
+    FwdTile tile{kChunk, false};
+    while (tile.chunk > 32 && (long long)((n_cap + tile.chunk - 1) / tile.chunk) * groups < 4LL * sms)
+        tile.chunk >>= 1;
+    const int chunk = tile.chunk;
+    if (fwd_set_smem(tile, g.wmode, "forward_static: smem attribute")) return SBP_ERR_CUDA;
     const FrameTable ft{1, nullptr, n_dev, n_cap};
     fwd_pmax_kernel<<<std::max(1, std::min(4 * sms, (n_cap + 255) / 256)), 256, 0, st>>>(
         b, ft, &state->pmax_bits, state);
     if (sbp_cuda_check(cudaGetLastError(), "forward_static: pmax launch")) return SBP_ERR_CUDA;
     const unsigned grid = (unsigned)(((long long)n_cap + chunk - 1) / chunk * groups);
-    fwd_group_for(g.wmode)<<<grid, kGroupWarps * 32, smem, st>>>(b, ft, sensors_dev, g, chunk,
-                                                           &state->pmax_bits, state, acc);
+    tile.kernel(g.wmode)<<<grid, tile.threads(), tile.smem(), st>>>(
+        b, ft, sensors_dev, g, chunk, &state->pmax_bits, state, acc);
     if (sbp_cuda_check(cudaGetLastError(), "forward_static: accumulate launch"))
         return SBP_ERR_CUDA;
     fwd_finalize_kernel<<<M, kFinalizeThreads, 0, st>>>(acc, T_k, &state->pmax_bits, S_dev);

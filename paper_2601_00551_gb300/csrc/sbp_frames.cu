@@ -333,7 +333,7 @@ int sbp_autotune_frames(sbp_array arr, sbp_balls balls, const int* n_dev, float*
     int best_chunk = 512, best_split = 4;
     if (rc == SBP_OK) {
         float best = 1e30f;
-        for (int chunk : {256, 512, 1024}) {
+        for (int chunk : {256, 512, 1024, 1024 | SBP_TILE_WIDE}) {
             const float ms = time_it([&] {
                 sbp_launch_forward_frames(arr, bd, n_dev, S_dev, chunk, s);
             });

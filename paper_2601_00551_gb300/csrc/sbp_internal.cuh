@@ -159,6 +159,9 @@ int sbp_level_T(const sbp_array_s* a, int k);
 // ----------------------------------------------------------------------------
 // launchers (one per translation unit family); each returns an sbp_status
 // ----------------------------------------------------------------------------
+// A forward tile value: a power of two in [32, SBP_FRAME_ALIGN] balls per
+// CTA, optionally or'ed with SBP_TILE_WIDE.
+bool sbp_fwd_tile_valid(int tile);
 int sbp_launch_forward(sbp_array_s* a, const BallsDev& b, const int* n_dev, int n_cap,
                        float* S, cudaStream_t st);
 int sbp_launch_residual(sbp_array_s* a, const float* S, const float* y, float* G,

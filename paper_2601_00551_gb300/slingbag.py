@@ -30,6 +30,9 @@ W_MODES = {"clamp": 0, "none": 1, "cos": 2}
 MASK_P0, MASK_R, MASK_XYZ, MASK_ALL = 1, 2, 4, 7
 SOFTPLUS_R = 8  # optimise R through R = softplus(a) (positivity-constrained refinement)
 KEEP_NEG, KEEP_NONPOS, DROP_ZERO, GROW = 0, 1, 2, 3
+# or'ed into a forward tile (set_tiles): 832 trace cells per sensor in shared
+# memory and 32 warps per CTA instead of 416 and 16
+TILE_WIDE = 0x10000
 
 _P = ctypes.c_void_p
 

@@ -149,7 +149,7 @@ def test_autotune_frames_keeps_results(sb):
     arr.set_sampling_level(1)
     S0 = arr.forward_frames(packed, n_dev).clone()
     chunk, split = arr.autotune_frames(packed, n_dev)
-    assert chunk in (256, 512, 1024) and split in (1, 2, 4, 8)
+    assert chunk in (256, 512, 1024, 1024 | sb.TILE_WIDE) and split in (1, 2, 4, 8)
     assert torch.equal(arr.forward_frames(packed, n_dev), S0)
 
 

@@ -603,10 +603,12 @@ def test_reconstruct_with_softplus_refinement_matches_oracle(sb):
 # ------------------------------------------------------------- tile choices
 
 def test_tile_choices_and_autotune(sb):
-    """The forward's balls per CTA change only the launch: every choice gives
-    bitwise the same traces. Every adjoint cluster split is at parity with the
-    oracle. The autotuner keeps a valid choice per level and the results stay
-    the same."""
+    """The forward's balls per CTA and window shape change only the launch:
+    every choice gives bitwise the same traces, also on the cloud in random
+    order, where chunks span the whole region and impulses spill past the
+    shared window of either shape. Every adjoint cluster split is at parity
+    with the oracle. The autotuner keeps a valid choice per level and the
+    results stay the same."""
     wl = workloads.vessel(n_init=20000, n_truth=2000)
     b = wl.init.stack()
     arr = make_array(sb, wl, wl.levels, b.shape[1])
@@ -619,13 +621,21 @@ def test_tile_choices_and_autotune(sb):
         arr.set_tiles(0, 0, 3)
     with pytest.raises(sb.SlingbagError):
         arr.set_tiles(len(wl.levels), 256, 2)
+    with pytest.raises(sb.SlingbagError):
+        arr.set_tiles(0, 2048 | sb.TILE_WIDE, 0)
+    with pytest.raises(sb.SlingbagError):
+        arr.set_tiles(0, 512 | sb.TILE_WIDE | 0x20000, 0)
+    W = sb.TILE_WIDE
+    shuffled = balls[:, torch.from_numpy(np.random.default_rng(9).permutation(b.shape[1])).cuda()]
     for k, f in enumerate(wl.levels):
         Tk = wl.T // f
         arr.set_sampling_level(k)
         S0 = arr.forward(balls).clone()
-        for chunk in (32, 128, 256, 1024):
+        for chunk in (32, 128, 256, 1024, 32 | W, 512 | W, 1024 | W):
             arr.set_tiles(k, chunk, 0)
+            assert arr.get_tiles(k) == (chunk, 0)
             assert torch.equal(arr.forward(balls), S0), (f, chunk)
+            assert torch.equal(arr.forward(shuffled), S0), (f, chunk, "random order")
         G = rng.normal(size=(wl.sensors.M, Tk)).astype(np.float32)
         Gd = torch.from_numpy(G).cuda()
         ref = oracle.adjoint(b[:, pick], wl.sensors.pos, wl.sensors.normal, wl.c, dt_of(wl, f),
@@ -638,7 +648,7 @@ def test_tile_choices_and_autotune(sb):
                 assert rel_l2(g[c, pick], ref[c]) <= GRAD_TOL, (f, split, c)
         arr.set_tiles(k, 0, 0)
         chunk, split = arr.autotune(balls, G=Gd)
-        assert chunk in (0, 128, 256, 512, 1024) and split in (0, 1, 2, 4, 8)
+        assert chunk in (0, 128, 256, 512, 1024, 512 | W, 1024 | W) and split in (0, 1, 2, 4, 8)
         assert arr.get_tiles(k) == (chunk, split)
         assert torch.equal(arr.forward(balls), S0)
         g = arr.adjoint(balls, Gd).cpu().numpy()
