@@ -214,7 +214,7 @@ int sbp_adjoint(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap,
  * (a launch parameter only: the forward is bitwise identical for every
  * choice, the adjoint differs by float summation order). fwd_chunk: balls
  * per forward CTA, 0 (default: 512, fewer for small clouds) or a power of
- * two in [32, 1024], optionally or'ed with SBP_TILE_WIDE (each CTA holds
+ * two in [32, 2048], optionally or'ed with SBP_TILE_WIDE (each CTA holds
  * 832 instead of 416 trace cells per sensor in shared memory and runs 32
  * warps, one CTA per SM: fewer impulses spill to the global accumulators
  * when a chunk spans many cells, at the finest sampling rates); adj_split:
@@ -226,8 +226,8 @@ int sbp_set_tiles(sbp_array arr, int k, int fwd_chunk, int adj_split);
 int sbp_get_tiles(sbp_array arr, int k, int* fwd_chunk, int* adj_split);
 
 /* Tile autotuner for the current level: times sbp_forward with the default
- * tile and with 128, 256, 512 and 1024 balls per CTA and 512 and 1024 with
- * SBP_TILE_WIDE, and sbp_adjoint (all
+ * tile and with 128, 256, 512, 1024 and 2048 balls per CTA and 1024 and
+ * 2048 with SBP_TILE_WIDE, and sbp_adjoint (all
  * components) with the default and with 1, 2, 4 and 8 CTAs per ball chunk, on
  * the given cloud; keeps for this level (as sbp_set_tiles would) the
  * fastest choice of each if it beats the default by more than 3%, else the

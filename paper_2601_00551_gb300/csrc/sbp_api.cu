@@ -299,7 +299,7 @@ int sbp_set_tiles(sbp_array arr, int k, int fwd_chunk, int adj_split) {
         return SBP_ERR_LEVEL;
     }
     if (!fwd_chunk_ok(fwd_chunk) || !adj_split_ok(adj_split)) {
-        sbp_set_error("set_tiles: chunk must be 0 or a power of two in [32, 1024] (optionally "
+        sbp_set_error("set_tiles: chunk must be 0 or a power of two in [32, 2048] (optionally "
                       "with SBP_TILE_WIDE), split 0, 1, 2, 4 or 8");
         return SBP_ERR_ARG;
     }
@@ -374,7 +374,7 @@ int sbp_autotune(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap, fl
         return choice;
     };
     const sbp_grads gr{g, g + cap, g + 2 * cap, g + 3 * cap, g + 4 * cap};
-    int best_chunk = pick({128, 256, 512, 1024, 512 | SBP_TILE_WIDE, 1024 | SBP_TILE_WIDE},
+    int best_chunk = pick({128, 256, 512, 1024, 2048, 1024 | SBP_TILE_WIDE, 2048 | SBP_TILE_WIDE},
                           &arr->fwd_chunk_lvl[k], [&] {
         return sbp_launch_forward(arr, bd, n_dev, n_cap, S_dev, s);
     });

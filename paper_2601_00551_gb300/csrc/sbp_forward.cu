@@ -34,16 +34,19 @@
 //                 SM). The flush costs about one global atomic per window
 //                 cell, i.e. (window cells) / (balls per chunk) per pair, and
 //                 the window grows with the chunk's extent in cells; at the
-//                 finest sampling rates the wide shape lets a chunk of 1024
+//                 finest sampling rates the wide shape lets a chunk of 2048
 //                 balls keep its window on chip where the narrow one spills.
 //                 A 64-bit shared atomic add costs several times a 32-bit one
 //                 on this GPU, so each int64 impulse v is added as two 32-bit
-//                 words: v mod 2^32 and v >> kLoBits (signed). The high word
-//                 cannot overflow within a CTA, and the sum of the low
-//                 kLoBits-bit parts (at most 2 impulses per ball and cell,
-//                 kChunk balls) stays below 2^32, so the flush recovers it
-//                 from the first word and the high word and recombines the
-//                 sum exactly.
+//                 words: v mod 2^32 and v >> kLoBits (signed). The sum of the
+//                 low kLoBits-bit parts (at most 2 impulses per ball and
+//                 cell, at most kMaxChunk balls) stays below 2^32, so the
+//                 flush recovers it from the first word and the high word
+//                 and recombines the sum exactly. The high word is a signed
+//                 32-bit sum of v >> kLoBits: with K h R 2^F < 2^32 R / d
+//                 (F below) every impulse is below K h (10 R + 3 h) 2^F in
+//                 magnitude, so 2 kMaxChunk of them overflow it only for a
+//                 ball within (10 R + 3 h) / 64 of a sensor.
 //   fwd_finalize  CTA = one sensor; two block scans turn impulses into the
 //                 float32 trace and clear the accumulator row
 #include <algorithm>
@@ -59,11 +62,10 @@ constexpr int kWarpsNarrow = 16;    // warps per forward CTA, narrow shape
 constexpr int kWindowNarrow = 416;  // cells per sensor held in shared memory, narrow shape
 constexpr int kWarpsWide = 32;      // the same for the wide shape
 constexpr int kWindowWide = 832;
-constexpr int kChunk = 512;         // largest number of balls per CTA
-constexpr int kLoBits = 20;         // 2 * kChunk * 2^kLoBits < 2^32
-static_assert(2LL * kChunk * (1LL << kLoBits) < (1LL << 32), "low word could overflow");
-// the batched launch accepts chunks up to one frame alignment unit
-static_assert(2LL * SBP_FRAME_ALIGN * (1LL << kLoBits) < (1LL << 32), "low word could overflow");
+constexpr int kChunk = 512;         // default number of balls per CTA
+constexpr int kMaxChunk = 2 * SBP_FRAME_ALIGN;  // largest (single cloud; frames: SBP_FRAME_ALIGN)
+constexpr int kLoBits = 19;         // 2 * kMaxChunk * 2^kLoBits <= 2^32
+static_assert(2LL * kMaxChunk * ((1LL << kLoBits) - 1) < (1LL << 32), "low word could overflow");
 constexpr int kFinalizeThreads = 1024;
 constexpr int kFracHeadroomBits = 34;  // F = 34 - ceil(log2 max|p0|)
 
@@ -469,8 +471,8 @@ static int fwd_set_smem(const FwdTile& t, int wmode, const char* what) {
 
 bool sbp_fwd_tile_valid(int tv) {
     const int c = tv & ~SBP_TILE_WIDE;
-    return (tv & ~(SBP_TILE_WIDE | (2 * SBP_FRAME_ALIGN - 1))) == 0 && c >= 32 &&
-           c <= SBP_FRAME_ALIGN && !(c & (c - 1));
+    return (tv & ~(SBP_TILE_WIDE | (2 * kMaxChunk - 1))) == 0 && c >= 32 && c <= kMaxChunk &&
+           !(c & (c - 1));
 }
 
 // The tile of a valid tile value, else `fallback`.
@@ -518,7 +520,9 @@ int sbp_launch_forward_frames(sbp_array_s* a, const BallsDev& b, const int* n_de
     const int F = a->frames;
     const int total = a->h_frame_off[F];
     const int groups = (g.M + 31) / 32;
-    const FwdTile tile = fwd_tile_of(chunk, FwdTile{kChunk, false});
+    // a chunk must not straddle two frames: at most one alignment unit
+    FwdTile tile = fwd_tile_of(chunk, FwdTile{kChunk, false});
+    if (tile.chunk > SBP_FRAME_ALIGN) tile.chunk = SBP_FRAME_ALIGN;
     chunk = tile.chunk;
     if (fwd_set_smem(tile, g.wmode, "forward_frames: smem attribute")) return SBP_ERR_CUDA;
     // one fixed-point scale per frame, so that every frame's traces equal

@@ -622,7 +622,9 @@ def test_tile_choices_and_autotune(sb):
     with pytest.raises(sb.SlingbagError):
         arr.set_tiles(len(wl.levels), 256, 2)
     with pytest.raises(sb.SlingbagError):
-        arr.set_tiles(0, 2048 | sb.TILE_WIDE, 0)
+        arr.set_tiles(0, 4096 | sb.TILE_WIDE, 0)
+    with pytest.raises(sb.SlingbagError):
+        arr.set_tiles(0, 3072, 0)
     with pytest.raises(sb.SlingbagError):
         arr.set_tiles(0, 512 | sb.TILE_WIDE | 0x20000, 0)
     W = sb.TILE_WIDE
@@ -631,7 +633,7 @@ def test_tile_choices_and_autotune(sb):
         Tk = wl.T // f
         arr.set_sampling_level(k)
         S0 = arr.forward(balls).clone()
-        for chunk in (32, 128, 256, 1024, 32 | W, 512 | W, 1024 | W):
+        for chunk in (32, 128, 256, 1024, 2048, 32 | W, 512 | W, 2048 | W):
             arr.set_tiles(k, chunk, 0)
             assert arr.get_tiles(k) == (chunk, 0)
             assert torch.equal(arr.forward(balls), S0), (f, chunk)
@@ -648,7 +650,8 @@ def test_tile_choices_and_autotune(sb):
                 assert rel_l2(g[c, pick], ref[c]) <= GRAD_TOL, (f, split, c)
         arr.set_tiles(k, 0, 0)
         chunk, split = arr.autotune(balls, G=Gd)
-        assert chunk in (0, 128, 256, 512, 1024, 512 | W, 1024 | W) and split in (0, 1, 2, 4, 8)
+        assert chunk in (0, 128, 256, 512, 1024, 2048, 1024 | W, 2048 | W) and \
+            split in (0, 1, 2, 4, 8)
         assert arr.get_tiles(k) == (chunk, split)
         assert torch.equal(arr.forward(balls), S0)
         g = arr.adjoint(balls, Gd).cpu().numpy()
