@@ -522,11 +522,11 @@ def algorithmic_ops(kind, s):
 NCU_RECORD = {
     "forward": {"sources": ["paper_2601_00551_gb300/csrc/sbp_forward.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "aadb94b9ca5c532a", "bytes": 3.5635968e7,
-                "thread_inst_per_pair": 198.9},
+                "sha256": "343f94f0eb095e20", "bytes": 3.5637504e7,
+                "thread_inst_per_pair": 175.2},
     "adjoint": {"sources": ["paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "a86dc41b8daa7c37", "bytes": 5.9741696e7,
+                "sha256": "98f3eca38874521f", "bytes": 6.0106752e7,
                 "thread_inst_per_pair": 210.4},
 }
 
