@@ -1032,9 +1032,11 @@ def learned_plus_batched(sb, dev, frames=(0, 4, 8, 12, 16, 20, 24, 28), n_train=
              random cloud of `rand_frac` of the frame's plain initial count
              (the plain method as the fallback where the network sees
              nothing); then ONE sbp_reconstruct_frames call per 10-iteration
-             segment over all frames (zero-gradient filtering in the first,
-             then the Pro schedule) until every frame's residual is at or
-             below its r_f.
+             segment over the frames still running (zero-gradient filtering
+             in the first, then the Pro schedule); a frame stops once its
+             residual is at or below its r_f.
+    batched  the same batched calls from the plain method's own initial
+             clouds (no proposal): what batching alone gives.
     Times are device seconds; the learned time includes the delay-and-sum
     volumes and proposals (not the training, done once per array). The
     residual checks between segments are not timed."""
@@ -1145,52 +1147,82 @@ def learned_plus_batched(sb, dev, frames=(0, 4, 8, 12, 16, 20, 24, 28), n_train=
     rand = [workloads.uniform_balls(int(rand_frac * fw.inits[f].n), half, 0.05, 0.2, 0.0, 1.0,
                                     seed=7000 + f) for f in frames]
     rand = [r.take(workloads.morton_order(r, half)) for r in rand]
-    starts = [c + r.n for c, r in zip(counts, rand)]
-    # one batched reconstruction over all frames until each reaches its r_f
-    caps = [max(2 * align, 2 * s_, 2 * p["balls"]) for s_, p in zip(starts, plain)]
-    farr = sb.SensorArray(fw.sensors.pos, fw.sensors.normal, fw.c, fw.fs_mhz, fw.T, fw.levels,
-                          n_cap=sum((c + align - 1) // align * align for c in caps))
-    off = farr.set_frames(caps)
-    balls = torch.zeros((5, int(off[-1])), dtype=torch.float32, device=dev)
-    for q in range(F):
-        balls[:, off[q]:off[q] + counts[q]] = props[q][:, :counts[q]]
-        balls[:, off[q] + counts[q]:off[q] + starts[q]] = torch.from_numpy(rand[q].stack()).to(dev)
-    n_dev = torch.tensor(starts, dtype=torch.int32, device=dev)
     Yf = torch.stack(Y).contiguous()
     ynorm_t = torch.tensor(ynorm, dtype=torch.float64, device=dev)
-    target = torch.tensor([p["final_rel_residual"] for p in plain], dtype=torch.float64,
-                          device=dev)
+    tgt = np.array([p["final_rel_residual"] for p in plain])
     losses = torch.zeros(F, dtype=torch.float64, device=dev)
-    t, it, done, r = 0.0, 0, False, None
-    traj = []  # (seconds, largest ratio of a frame's residual to its r_f)
-    for j, (level, mask) in enumerate(pro_segments(nl, seg)):
-        a.record()
-        farr.reconstruct_frames(Yf, balls, n_dev, [sb.Stage(level, seg, mask, True, False)],
-                                zero_grad_mode=(sb.KEEP_NEG if j == 0 else None),
-                                zero_grad_level=0, grow=sb.GrowParams(seed=2000 + j, **GROW))
-        b.record()
-        torch.cuda.synchronize()
-        t += a.elapsed_time(b) / 1e3
-        it += seg
-        farr.set_sampling_level_frames(fine)
-        S = farr.forward_frames(balls, n_dev)
-        farr.residual_frames(S, Yf, loss=losses)
-        r = (losses / ynorm_t).cpu().numpy()
-        traj.append((t, float(np.max(r / target.cpu().numpy()))))
-        if bool(np.all(r <= target.cpu().numpy())):
-            done = True
-            break
-        if it >= 2 * max_iter:
-            break
-    status = farr.sync_status()
-    if status not in (0, sb.SBP_ERR_CAPACITY) or single.sync_status() not in (0, sb.SBP_ERR_CAPACITY):
+
+    def run_batched(clouds, seed0):
+        """One sbp_reconstruct_frames call per segment over the frames still
+        above their target, from `clouds` (per frame a (5, n) device tensor):
+        zero-gradient filtering in the first segment, then the Pro schedule,
+        growth seeds seed0 + segment. A frame stops once its relative
+        residual at the finest level is at or below its r_f: its live count
+        is set to 0, so later calls skip it. Device seconds of the calls."""
+        starts_ = [int(c.shape[1]) for c in clouds]
+        caps_ = [max(2 * align, 2 * s_, 2 * p["balls"]) for s_, p in zip(starts_, plain)]
+        farr = sb.SensorArray(fw.sensors.pos, fw.sensors.normal, fw.c, fw.fs_mhz, fw.T,
+                              fw.levels, n_cap=sum((c + align - 1) // align * align for c in caps_))
+        off = farr.set_frames(caps_)
+        balls = torch.zeros((5, int(off[-1])), dtype=torch.float32, device=dev)
+        for q in range(F):
+            balls[:, off[q]:off[q] + starts_[q]] = clouds[q]
+        n_dev = torch.tensor(starts_, dtype=torch.int32, device=dev)
+        t, it = 0.0, 0
+        reached = [None] * F  # per frame: (seconds, iterations, residual, balls)
+        last = np.ones(F)
+        traj = []  # (seconds, largest ratio of a running frame's residual to its r_f)
+        for j, (level, mask) in enumerate(pro_segments(nl, seg)):
+            a.record()
+            farr.reconstruct_frames(Yf, balls, n_dev, [sb.Stage(level, seg, mask, True, False)],
+                                    zero_grad_mode=(sb.KEEP_NEG if j == 0 else None),
+                                    zero_grad_level=0, grow=sb.GrowParams(seed=seed0 + j, **GROW))
+            b.record()
+            torch.cuda.synchronize()
+            t += a.elapsed_time(b) / 1e3
+            it += seg
+            farr.set_sampling_level_frames(fine)
+            S = farr.forward_frames(balls, n_dev)
+            farr.residual_frames(S, Yf, loss=losses)
+            r = (losses / ynorm_t).cpu().numpy()
+            n_now = n_dev.cpu().numpy()
+            running = [q for q in range(F) if reached[q] is None]
+            for q in running:
+                last[q] = r[q]
+            traj.append((t, float(max(r[q] / tgt[q] for q in running))))
+            newly = [q for q in running if r[q] <= tgt[q]]
+            for q in newly:
+                reached[q] = (t, it, float(r[q]), int(n_now[q]))
+            if newly:
+                n_dev[newly] = 0
+            if all(x is not None for x in reached) or it >= 2 * max_iter:
+                break
+        status = farr.sync_status()
+        if status not in (0, sb.SBP_ERR_CAPACITY):
+            raise RuntimeError("device status latched in a batched arm: " +
+                               sb.load_library().sbp_last_error().decode())
+        farr.close()
+        done_ = all(x is not None for x in reached)
+        return {"seconds": t, "iterations": it, "done": done_, "traj": traj, "status": int(status),
+                "final_rel_residual": [x[2] if x else float(last[q]) for q, x in enumerate(reached)],
+                "iterations_per_frame": [x[1] if x else None for x in reached],
+                "balls": [x[3] if x else None for x in reached]}
+
+    # the batched reconstruction alone: the plain method's own initial
+    # clouds, every frame stopped at its r_f
+    bp = run_batched([torch.from_numpy(fw.inits[f].stack()).to(dev) for f in frames], 1000)
+    # the learned proposal plus the random fallback, batched the same way
+    lb = run_batched([torch.cat([props[q][:, :counts[q]],
+                                 torch.from_numpy(rand[q].stack()).to(dev)], dim=1)
+                      for q in range(F)], 2000)
+    if single.sync_status() not in (0, sb.SBP_ERR_CAPACITY):
         raise RuntimeError("device status latched in the learned + batched arm: " +
                            sb.load_library().sbp_last_error().decode())
-    farr.close()
     single.close()
+    t, it, done, traj, status = lb["seconds"], lb["iterations"], lb["done"], lb["traj"], lb["status"]
     learned_s = t + infer_s if done else None
     # time to within a factor x of the converged residual: the plain method
-    # frame by frame (summed), the learned arm for all frames at once
+    # frame by frame (summed), the batched arms for all frames at once
     near = {}
     for x in (1.10, 1.05, 1.02):
         pt = []
@@ -1198,10 +1230,13 @@ def learned_plus_batched(sb, dev, frames=(0, 4, 8, 12, 16, 20, 24, 28), n_train=
             rf = pf["final_rel_residual"]
             pt.append(next((s_ for s_, rr in pf["trajectory"] if rr <= x * rf), None))
         lt = next((s_ for s_, q in traj if q <= x), None)
+        bt = next((s_ for s_, q in bp["traj"] if q <= x), None)
         ps = sum(pt) if all(v is not None for v in pt) else None
         ls = (lt + infer_s) if lt is not None else None
         near[f"{x:.2f}"] = {"plain_seconds": ps, "learned_plus_batched_seconds": ls,
-                            "speedup": (ps / ls) if (ps and ls) else None}
+                            "speedup": (ps / ls) if (ps and ls) else None,
+                            "batched_plain_seconds": bt,
+                            "batched_plain_speedup": (ps / bt) if (ps and bt) else None}
     for pf in plain:
         pf["trajectory"] = pf["trajectory"][-3:]
     return {
@@ -1217,9 +1252,19 @@ def learned_plus_batched(sb, dev, frames=(0, 4, 8, 12, 16, 20, 24, 28), n_train=
                     "random_balls": [r.n for r in rand],
                     "precision_mean": float(np.mean(prec)), "recall_mean": float(np.mean(rec)),
                     "reconstruction_seconds": t, "iterations": it,
-                    "final_rel_residual": r.tolist() if r is not None else None,
+                    "iterations_per_frame": lb["iterations_per_frame"],
+                    "final_rel_residual": lb["final_rel_residual"],
                     "reached_every_target": done, "status": int(status),
-                    "balls": n_dev.cpu().tolist()},
+                    "balls": lb["balls"]},
+        "batched_plain": {
+            "what": "the plain method's own initial clouds through sbp_reconstruct_frames, one "
+                    "call per segment over the frames still above their r_f",
+            "seconds": bp["seconds"], "iterations": bp["iterations"],
+            "iterations_per_frame": bp["iterations_per_frame"],
+            "plain_iterations_per_frame": [p["iterations"] for p in plain],
+            "final_rel_residual": bp["final_rel_residual"],
+            "reached_every_target": bp["done"],
+            "speedup_vs_plain": (plain_s / bp["seconds"]) if bp["done"] else None},
         "learned_plus_batched_seconds": learned_s,
         "speedup_vs_plain": (plain_s / learned_s) if learned_s else None,
         "to_within_factor_of_converged_residual": near,
