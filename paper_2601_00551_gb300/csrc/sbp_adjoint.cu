@@ -53,10 +53,12 @@
 
 namespace {
 
-constexpr int kAdjThreads = SBP_ADJ_CHUNK;  // balls (threads) per adjoint CTA
+constexpr int kAdjThreads = SBP_ADJ_CHUNK_MAX;  // balls (threads) per adjoint CTA
 constexpr int kAdjSplit = 8;      // default CTAs per chunk, each taking 1/split of the sensors
-constexpr int kAdjCap = 3072;     // cells per staging buffer (two buffers per CTA)
-constexpr int kAdjCapP0 = 1792;   // the same for the p0-only adjoint, which keeps more CTAs per SM
+constexpr int kAdjCap = 4096;     // cells per staging buffer (two buffers per CTA)
+constexpr int kAdjCapP0 = 4096;   // the same for the p0-only adjoint
+static_assert(SBP_FRAME_ALIGN % kAdjThreads == 0, "a chunk must not straddle two frames");
+static_assert(kAdjThreads % SBP_ADJ_CHUNK == 0, "the scratch is sized in whole chunks");
 constexpr int kAdjShare = 16;     // a CTA's share of the sensors is a multiple of this
 constexpr int kAdjMeta = 128;     // sensors whose set-up is held in shared memory at once
 
@@ -238,7 +240,7 @@ __device__ __forceinline__ void adj_window_sums(const float* __restrict__ sGrow,
 // fixed at compile time so that no pair branches on it.
 // `split` CTAs share a chunk, each taking 1/split of the sensors.
 template <bool P0_ONLY, int WMODE>
-__global__ void __launch_bounds__(kAdjThreads, P0_ONLY ? 10 : 7)
+__global__ void __launch_bounds__(kAdjThreads, P0_ONLY ? 5 : 4)
 adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, LevelGeo g,
                  const float* __restrict__ G_all, unsigned mask, GradOut out,
                  float* __restrict__ part_all, unsigned int* __restrict__ tickets, int split,
@@ -681,7 +683,7 @@ int launch_adj(sbp_array_s* a, const FrameTable& ft, int total, int split, const
     if (split != 1 && split != 2 && split != 4 && split != 8) split = kAdjSplit;
     static_assert(kAdjSplit <= SBP_ADJ_MAX_SPLIT, "the scratch holds at most 8 parts");
     const int chunks = (total + kAdjThreads - 1) / kAdjThreads;
-    if (chunks > a->adj_chunks) {
+    if ((long long)chunks * kAdjThreads > (long long)a->adj_chunks * SBP_ADJ_CHUNK) {
         sbp_set_error("adjoint: more balls than the array's capacity");
         return SBP_ERR_ARG;
     }

@@ -191,7 +191,10 @@ int sbp_create_array(const float* pos_host, const float* normal_host, int M, dou
                                                             (size_t)n_cap),
                                "alloc filter buffer");
     ok = ok && !sbp_cuda_check(cudaMalloc(&a->d_state, sizeof(SbpDevState)), "alloc state");
-    a->adj_chunks = (n_cap + SBP_ADJ_CHUNK - 1) / SBP_ADJ_CHUNK;
+    // in scratch units of SBP_ADJ_CHUNK balls, for n_cap rounded up to whole
+    // chunks of the largest size (both adjoints' partial sums and tickets fit)
+    a->adj_chunks = (n_cap + SBP_ADJ_CHUNK_MAX - 1) / SBP_ADJ_CHUNK_MAX *
+                    (SBP_ADJ_CHUNK_MAX / SBP_ADJ_CHUNK);
     ok = ok && !sbp_cuda_check(cudaMalloc(&a->d_adj_part, sizeof(float) * (size_t)a->adj_chunks *
                                                               SBP_ADJ_MAX_SPLIT * 5 * SBP_ADJ_CHUNK),
                                "alloc adjoint partials");

@@ -9,7 +9,8 @@
 #include "slingbag.h"
 
 #define SBP_MAX_LEVELS 16
-#define SBP_ADJ_CHUNK 128  // balls per adjoint CTA
+#define SBP_ADJ_CHUNK 128      // balls per Gaussian-adjoint CTA: the adjoint scratch's unit
+#define SBP_ADJ_CHUNK_MAX 256  // balls per sphere-adjoint CTA, the largest chunk
 #define SBP_ADJ_MAX_SPLIT 8  // most CTAs sharing one adjoint chunk
 #define SBP_MAX_EXTRA 16
 #define SBP_FG_ARRAYS (10 + SBP_MAX_EXTRA)
