@@ -522,12 +522,12 @@ def algorithmic_ops(kind, s):
 NCU_RECORD = {
     "forward": {"sources": ["paper_2601_00551_gb300/csrc/sbp_forward.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "343f94f0eb095e20", "bytes": 3.5637504e7,
+                "sha256": "6d38abae5c921b5c", "bytes": 3.5644928e7,
                 "thread_inst_per_pair": 175.2},
     "adjoint": {"sources": ["paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "98f3eca38874521f", "bytes": 6.0106752e7,
-                "thread_inst_per_pair": 210.4},
+                "sha256": "a7af4d6d5caea095", "bytes": 6.5840128e7,
+                "thread_inst_per_pair": 203.5},
 }
 
 
