@@ -446,27 +446,50 @@ int launch_halo_t(const ConvArgs& a, cudaStream_t st) {
     return SBP_OK;
 }
 
-// Persistent TMA variant (Cin 16 or 32). One CTA per SM stages the weights
-// once and walks its tiles (tile i of the CTA is global tile blockIdx.x + i
-// gridDim.x). Each tile's halo comes in by TMA: a 4-D tensor map over the
-// channels-last input (channel, x, y, z) and one box of 8 channels x 10 x 18
-// x 3 per 8-channel chunk, which lands as exactly the chunk plane the MMA
+// Persistent TMA variant (Cin 16 or 32), warp-specialised. Each CTA stages
+// the weights once and walks its tiles (tile i of the CTA is global tile
+// blockIdx.x + i gridDim.x); one or two CTAs per SM, as shared memory allows.
+// Each tile's halo comes in by TMA: a 4-D tensor map over the channels-last
+// input (channel, x, y, z) and one box of 8 channels x 10 x 18 x 3 per
+// 8-channel chunk, which lands as exactly the chunk plane the MMA
 // descriptors read (rows of 16 bytes along x); outside the volume TMA fills
-// zeros. The halos rotate through three slots, so a tile's copy is issued
-// two tiles ahead, and the accumulator alternates between two TMEM buffers,
-// so the epilogue of tile i - 1 runs while the MMAs of tile i are in flight.
-constexpr int kTmaSlots = 3;
+// zeros. Roles, linked only by mbarriers (no CTA-wide barrier per tile):
+//   warp 0, one lane   producer: the halo of tile i into slot i % kSlots,
+//                      once the MMAs of tile i - kSlots have released it
+//   warp 1, one lane   MMA issuer: the 27 Cin / 16 MMAs of tile i into TMEM
+//                      buffer i & 1, once its halo has landed and the
+//                      epilogue of tile i - 2 has read that buffer; two
+//                      commits then release the slot and publish the buffer
+//   warps 2 - 5        epilogue: tcgen05.ld of the warp's quarter of the
+//                      128 TMEM lanes, bias, ReLU, store; one arrive per warp
+//                      frees the buffer
+// So the producer runs up to kSlots tiles ahead and the MMAs of tile i + 1
+// overlap the epilogue of tile i. Every wait is bounded; a role that gives up
+// sets the status word and stops, and the others' waits then run out too.
+constexpr int kWsThreads = 192;
 constexpr int kPlanePad = (kHV * 16 + 127) / 128 * 128;  // a TMA destination is 128-byte aligned
 
 template <int CIN, int COUT>
+__host__ __device__ constexpr int tma_slots() { return CIN == 16 ? 4 : 3; }
+
+template <int CIN, int COUT>
 constexpr int tma_smem_bytes() {  // + 128: the base is rounded up to 128 bytes in the kernel
-    return 27 * (CIN / 8) * COUT * 16 + kTmaSlots * (CIN / 8) * kPlanePad + 128;
+    return 27 * (CIN / 8) * COUT * 16 + tma_slots<CIN, COUT>() * (CIN / 8) * kPlanePad + 128;
 }
+
+// CTAs per SM: two where both fit the SM's 228 KB of shared memory (with the
+// 1 KB each CTA reserves and the static part), else one
+template <int CIN, int COUT>
+constexpr int tma_ctas_per_sm() { return 2 * (tma_smem_bytes<CIN, COUT>() + 2048) <= 228 * 1024 ? 2 : 1; }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(bytes)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
@@ -480,12 +503,13 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
 }
 
 template <int CIN, int COUT, bool RELU, bool OUT_F32>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kWsThreads, 1)
 conv3d_tma_kernel(const __grid_constant__ CUtensorMap tmap, ConvArgs a, int ntx, int nty,
                   int ntiles) {
     static_assert(CIN % 16 == 0 && CIN <= 32, "two or four channel chunks");
     static_assert(COUT % 16 == 0 && COUT >= 16 && COUT <= kTcCols, "Cout must be 16, 32 or 64");
     extern __shared__ __align__(1024) uint8_t s_dyn[];
+    constexpr int kSlots = tma_slots<CIN, COUT>();
     constexpr int kChunks = CIN / 8;
     constexpr int kWBlock = COUT * 16;
     constexpr int kWBytes = 27 * kChunks * kWBlock;
@@ -494,18 +518,26 @@ conv3d_tma_kernel(const __grid_constant__ CUtensorMap tmap, ConvArgs a, int ntx,
     static_assert(kWBytes % 128 == 0, "halo slots must stay 128-byte aligned");
     uint8_t* const s_w = s_dyn + ((128u - (smem_u32(s_dyn) & 127u)) & 127u);
     uint8_t* const s_halo = s_w + kWBytes;
-    __shared__ __align__(8) uint64_t full[kTmaSlots];
-    __shared__ __align__(8) uint64_t done[2];
+    __shared__ __align__(8) uint64_t full[kSlots];   // halo of the slot landed
+    __shared__ __align__(8) uint64_t empty[kSlots];  // the slot's MMAs are done
+    __shared__ __align__(8) uint64_t tfull[2];       // accumulator buffer ready
+    __shared__ __align__(8) uint64_t tempty[2];      // accumulator buffer read
     __shared__ uint32_t s_tmem;
+    __shared__ float s_bias[COUT];
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        for (int s = 0; s < kTmaSlots; ++s) mbar_init(&full[s], 1);
-        mbar_init(&done[0], 1);
-        mbar_init(&done[1], 1);
+        for (int s = 0; s < kSlots; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);  // one arrive per epilogue warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&s_tmem)),
                      "r"(2 * kTcCols)
@@ -513,10 +545,11 @@ conv3d_tma_kernel(const __grid_constant__ CUtensorMap tmap, ConvArgs a, int ntx,
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     // the weights, once: w[n][tap * CIN + cc * 8 ...] -> [tap][cc][n] x 16 bytes
-    for (int t = tid; t < COUT * 27 * kChunks; t += kTcThreads) {
+    for (int t = tid; t < COUT * 27 * kChunks; t += kWsThreads) {
         const int n = t / (27 * kChunks), r = t - n * (27 * kChunks);
         __pipeline_memcpy_async(s_w + r * kWBlock + n * 16, a.w + (size_t)n * a.Kp + r * 8, 16);
     }
+    for (int n = tid; n < COUT; n += kWsThreads) s_bias[n] = a.bias ? a.bias[n] : 0.0f;
     __pipeline_commit();
     __pipeline_wait_prior(0);
     fence_async_smem();
@@ -531,38 +564,43 @@ conv3d_tma_kernel(const __grid_constant__ CUtensorMap tmap, ConvArgs a, int ntx,
         y0 = ((t / ntx) % nty) * kHTY;
         z0 = t / (ntx * nty);
     };
-    // thread 0: the copies of this CTA's tile i into slot i % kTmaSlots
-    auto load = [&](int i) {
-        if (i >= nmine) return;
-        int x0, y0, z0;
-        origin(i, x0, y0, z0);
-        const int s = i % kTmaSlots;
-        mbar_expect_tx(&full[s], kTxBytes);
-#pragma unroll
-        for (int cc = 0; cc < kChunks; ++cc)
-            tma_load_4d(smem_u32(s_halo + s * kSlotBytes + cc * kPlanePad), &tmap, cc * 8, x0 - 1,
-                        y0 - 1, z0 - 1, &full[s]);
-    };
-    if (tid == 0) {
-        load(0);
-        load(1);
-    }
     bool ok = true;
-    for (int i = 0; i <= nmine; ++i) {
-        if (i < nmine && tid == 0) {  // the MMAs of tile i into TMEM buffer i & 1
-            const int s = i % kTmaSlots;
-            if (!mbar_wait(&full[s], (uint32_t)((i / kTmaSlots) & 1))) {
-                ok = false;
-            } else {
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int i = 0; i < nmine; ++i) {
+                const int s = i % kSlots;
+                if (i >= kSlots && !mbar_wait(&empty[s], (uint32_t)((i / kSlots - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                int x0, y0, z0;
+                origin(i, x0, y0, z0);
+                mbar_expect_tx(&full[s], kTxBytes);
+#pragma unroll
+                for (int cc = 0; cc < kChunks; ++cc)
+                    tma_load_4d(smem_u32(s_halo + s * kSlotBytes + cc * kPlanePad), &tmap, cc * 8,
+                                x0 - 1, y0 - 1, z0 - 1, &full[s]);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = umma_idesc_bf16(kTcRows, COUT);
+            const uint32_t wb = smem_u32(s_w);
+            const uint64_t db = umma_desc(wb, kWBlock, 128);
+            for (int i = 0; i < nmine; ++i) {
+                const int s = i % kSlots, b = i & 1;
+                if (!mbar_wait(&full[s], (uint32_t)((i / kSlots) & 1)) ||
+                    (i >= 2 && !mbar_wait(&tempty[b], (uint32_t)(((i >> 1) - 1) & 1)))) {
+                    ok = false;
+                    break;
+                }
                 tc_fence_after();
-                constexpr uint32_t idesc = umma_idesc_bf16(kTcRows, COUT);
-                const uint32_t hb = smem_u32(s_halo + s * kSlotBytes), wb = smem_u32(s_w);
-                const uint32_t d = tmem + (uint32_t)((i & 1) * kTcCols);
-                // descriptors of the halo and weight bases; each MMA adds its
-                // compile-time offset (>> 4) to the start-address field, which
-                // cannot carry out of its 14 bits (shared addresses < 256 KB)
+                const uint32_t hb = smem_u32(s_halo + s * kSlotBytes);
+                const uint32_t d = tmem + (uint32_t)(b * kTcCols);
+                // the halo base descriptor; each MMA adds its compile-time
+                // offset (>> 4) to the start-address field, which cannot
+                // carry out of its 14 bits (shared addresses < 256 KB)
                 const uint64_t da = umma_desc(hb, kPlanePad, kHX * 16);
-                const uint64_t db = umma_desc(wb, kWBlock, 128);
 #pragma unroll
                 for (int tap = 0; tap < 27; ++tap) {
                     const uint32_t aoff =
@@ -573,64 +611,65 @@ conv3d_tma_kernel(const __grid_constant__ CUtensorMap tmap, ConvArgs a, int ntx,
                                db + (((tap * kChunks + 2 * kp) * kWBlock) >> 4), idesc,
                                (tap > 0 || kp > 0) ? 1u : 0u);
                 }
-                tc_commit(&done[i & 1]);
+                tc_commit(&empty[s]);
+                tc_commit(&tfull[b]);
             }
         }
-        if (i >= 1 && ok) {  // the epilogue of tile i - 1 from TMEM buffer (i - 1) & 1
-            const int j = i - 1;
-            if (!mbar_wait(&done[j & 1], (uint32_t)((j >> 1) & 1))) ok = false;
+    } else {
+        // epilogue: warp w may read TMEM lanes 32 (w % 4) .. + 31
+        const int qtr = warp & 3;
+        const int m = qtr * 32 + lane;
+        for (int i = 0; i < nmine; ++i) {
+            const int b = i & 1;
+            if (!mbar_wait(&tfull[b], (uint32_t)((i >> 1) & 1))) {
+                ok = false;
+                break;
+            }
             tc_fence_after();
-            if (ok) {
-                int x0, y0, z0;
-                origin(j, x0, y0, z0);
-                const int m = warp * 32 + (tid & 31);
-                const int x = x0 + (m & 7), y = y0 + (m >> 3);
-                const bool mv = x < a.nx && y < a.ny;
-                const long long q = ((long long)z0 * a.ny + y) * a.nx + x;
-                const uint32_t taddr =
-                    tmem + (uint32_t)((j & 1) * kTcCols) + ((uint32_t)(warp * 32) << 16);
+            int x0, y0, z0;
+            origin(i, x0, y0, z0);
+            const int x = x0 + (m & 7), y = y0 + (m >> 3);
+            const bool mv = x < a.nx && y < a.ny;
+            const long long q = ((long long)z0 * a.ny + y) * a.nx + x;
+            const uint32_t taddr = tmem + (uint32_t)(b * kTcCols) + ((uint32_t)(qtr * 32) << 16);
 #pragma unroll
-                for (int c0 = 0; c0 < COUT; c0 += 16) {
-                    float v[16];
-                    tc_ld16(taddr + c0, v);
-                    if (mv) {
+            for (int c0 = 0; c0 < COUT; c0 += 16) {
+                float v[16];
+                tc_ld16(taddr + c0, v);
+                if (mv) {
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) {
-                            float r = v[k] + (a.bias ? a.bias[c0 + k] : 0.0f);
-                            if (RELU) r = fmaxf(r, 0.0f);
-                            v[k] = r;
-                        }
-                        if constexpr (OUT_F32) {
-                            float4* o =
-                                reinterpret_cast<float4*>(static_cast<float*>(a.out) + q * COUT + c0);
+                    for (int k = 0; k < 16; ++k) {
+                        float r = v[k] + s_bias[c0 + k];
+                        if (RELU) r = fmaxf(r, 0.0f);
+                        v[k] = r;
+                    }
+                    if constexpr (OUT_F32) {
+                        float4* o =
+                            reinterpret_cast<float4*>(static_cast<float*>(a.out) + q * COUT + c0);
 #pragma unroll
-                            for (int k = 0; k < 4; ++k)
-                                o[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-                        } else {
-                            __nv_bfloat162 hh[8];
+                        for (int k = 0; k < 4; ++k)
+                            o[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                    } else {
+                        __nv_bfloat162 hh[8];
 #pragma unroll
-                            for (int k = 0; k < 8; ++k)
-                                hh[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
-                            uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.out) +
-                                                                q * COUT + c0);
-                            o[0] = *reinterpret_cast<uint4*>(&hh[0]);
-                            o[1] = *reinterpret_cast<uint4*>(&hh[4]);
-                        }
+                        for (int k = 0; k < 8; ++k)
+                            hh[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+                        uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.out) +
+                                                            q * COUT + c0);
+                        o[0] = *reinterpret_cast<uint4*>(&hh[0]);
+                        o[1] = *reinterpret_cast<uint4*>(&hh[4]);
                     }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
         }
-        tc_fence_before();
-        if (!__syncthreads_and(ok)) break;
-        tc_fence_after();
-        // slot (i + 2) % 3 last held tile i - 1, whose MMAs are done; TMEM
-        // buffer (i + 1) & 1 was read by the epilogue above
-        if (tid == 0) load(i + 2);
     }
-    if (!ok && tid == 0) atomicExch(&g_cnn_status, 1);
+    if (!ok) atomicExch(&g_cnn_status, 1);
     tc_fence_before();
     __syncthreads();
-    if (warp == 0)
+    if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(2 * kTcCols)
                      : "memory");
@@ -678,8 +717,9 @@ int launch_tma_t(const ConvArgs& a, cudaStream_t st) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int ntx = (a.nx + kHTX - 1) / kHTX, nty = (a.ny + kHTY - 1) / kHTY;
     const long long ntiles = (long long)ntx * nty * a.nz;
-    const int grid = (int)std::min<long long>(std::max(1, sms), ntiles);
-    k<<<grid, kTcThreads, smem, st>>>(map, a, ntx, nty, (int)ntiles);
+    const int grid = (int)std::min<long long>(
+        (long long)std::max(1, sms) * tma_ctas_per_sm<CIN, COUT>(), ntiles);
+    k<<<grid, kWsThreads, smem, st>>>(map, a, ntx, nty, (int)ntiles);
     return 1;
 }
 
