@@ -130,14 +130,41 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Activation layouts: channels-last [V][C], or planar [C / 8][V][8] (planes
+// of 8 channels, 16 bytes per voxel), which gives a tile's halo box rows of
+// ten voxels (160 bytes) instead of one (16 bytes).
 struct ConvArgs {
-    const __nv_bfloat16* in;  // [V][Cin]
+    const __nv_bfloat16* in;  // [V][Cin], or planar (in_planar)
     const __nv_bfloat16* w;   // [Cout][Kp]
     const float* bias;        // [Cout] or null
-    void* out;                // [V][Cout], bf16 or fp32
+    void* out;                // [V][Cout], bf16 or fp32; or planar bf16 (out_planar)
     int nx, ny, nz;
     int Kp;
+    int in_planar, out_planar;
+    long long V;
 };
+
+// Stores channels c0 .. c0 + 15 (c0 a multiple of 16) of voxel q as bf16:
+// one 32-byte run channels-last, or 16 bytes in each of two planes.
+template <int C>
+__device__ __forceinline__ void store16_bf16(const ConvArgs& a, long long q, int c0,
+                                             const float* v) {
+    __nv_bfloat162 h[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+    __nv_bfloat16* const out = static_cast<__nv_bfloat16*>(a.out);
+    uint4* o0;
+    uint4* o1;
+    if (a.out_planar) {
+        o0 = reinterpret_cast<uint4*>(out + ((long long)(c0 >> 3) * a.V + q) * 8);
+        o1 = reinterpret_cast<uint4*>(out + ((long long)((c0 >> 3) + 1) * a.V + q) * 8);
+    } else {
+        o0 = reinterpret_cast<uint4*>(out + q * C + c0);
+        o1 = o0 + 1;
+    }
+    *o0 = *reinterpret_cast<uint4*>(&h[0]);
+    *o1 = *reinterpret_cast<uint4*>(&h[4]);
+}
 
 template <int CIN, int COUT, bool RELU, bool OUT_F32>
 __global__ void __launch_bounds__(kTcThreads) conv3d_tc_kernel(ConvArgs a) {
@@ -278,12 +305,7 @@ __global__ void __launch_bounds__(kTcThreads) conv3d_tc_kernel(ConvArgs a) {
                     for (int j = 0; j < 4; ++j)
                         o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                 } else {
-                    __nv_bfloat162 h[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                    uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.out) + m * COUT + c0);
-                    o[0] = *reinterpret_cast<uint4*>(&h[0]);
-                    o[1] = *reinterpret_cast<uint4*>(&h[4]);
+                    store16_bf16<COUT>(a, m, c0, v);
                 }
             }
         }
@@ -416,12 +438,7 @@ __global__ void __launch_bounds__(kTcThreads) conv3d_halo_kernel(ConvArgs a) {
                     for (int j = 0; j < 4; ++j)
                         o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                 } else {
-                    __nv_bfloat162 h[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                    uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.out) + q * COUT + c0);
-                    o[0] = *reinterpret_cast<uint4*>(&h[0]);
-                    o[1] = *reinterpret_cast<uint4*>(&h[4]);
+                    store16_bf16<COUT>(a, q, c0, v);
                 }
             }
         }
@@ -577,9 +594,13 @@ conv3d_tma_kernel(const __grid_constant__ CUtensorMap tmap, ConvArgs a, int ntx,
                 origin(i, x0, y0, z0);
                 mbar_expect_tx(&full[s], kTxBytes);
 #pragma unroll
-                for (int cc = 0; cc < kChunks; ++cc)
-                    tma_load_4d(smem_u32(s_halo + s * kSlotBytes + cc * kPlanePad), &tmap, cc * 8,
-                                x0 - 1, y0 - 1, z0 - 1, &full[s]);
+                for (int cc = 0; cc < kChunks; ++cc) {
+                    const uint32_t dst = smem_u32(s_halo + s * kSlotBytes + cc * kPlanePad);
+                    if (a.in_planar)  // (x * 8 + channel, y, z, plane)
+                        tma_load_4d(dst, &tmap, (x0 - 1) * 8, y0 - 1, z0 - 1, cc, &full[s]);
+                    else  // (channel, x, y, z)
+                        tma_load_4d(dst, &tmap, cc * 8, x0 - 1, y0 - 1, z0 - 1, &full[s]);
+                }
             }
         }
     } else if (warp == 1) {
@@ -650,14 +671,7 @@ conv3d_tma_kernel(const __grid_constant__ CUtensorMap tmap, ConvArgs a, int ntx,
                         for (int k = 0; k < 4; ++k)
                             o[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
                     } else {
-                        __nv_bfloat162 hh[8];
-#pragma unroll
-                        for (int k = 0; k < 8; ++k)
-                            hh[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
-                        uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.out) +
-                                                            q * COUT + c0);
-                        o[0] = *reinterpret_cast<uint4*>(&hh[0]);
-                        o[1] = *reinterpret_cast<uint4*>(&hh[4]);
+                        store16_bf16<COUT>(a, q, c0, v);
                     }
                 }
             }
@@ -697,11 +711,22 @@ int launch_tma_t(const ConvArgs& a, cudaStream_t st) {
     const auto encode = tensor_map_encoder();
     if (!encode) return 0;
     CUtensorMap map;
-    const cuuint64_t dims[4] = {(cuuint64_t)CIN, (cuuint64_t)a.nx, (cuuint64_t)a.ny,
-                                (cuuint64_t)a.nz};
-    const cuuint64_t strides[3] = {(cuuint64_t)CIN * 2, (cuuint64_t)a.nx * CIN * 2,
-                                   (cuuint64_t)a.nx * a.ny * CIN * 2};
-    const cuuint32_t box[4] = {8, (cuuint32_t)kHX, (cuuint32_t)kHY, (cuuint32_t)kHZ};
+    // channels-last: (channel, x, y, z), a box of 8 channels x 10 x 18 x 3;
+    // planar: (x * 8 + channel, y, z, plane), a box of 80 x 18 x 3 x 1, whose
+    // rows are ten voxels of one plane (the same bytes in shared memory)
+    const cuuint64_t V = (cuuint64_t)a.nx * a.ny * a.nz;
+    const cuuint64_t dims_cl[4] = {(cuuint64_t)CIN, (cuuint64_t)a.nx, (cuuint64_t)a.ny,
+                                   (cuuint64_t)a.nz};
+    const cuuint64_t strides_cl[3] = {(cuuint64_t)CIN * 2, (cuuint64_t)a.nx * CIN * 2,
+                                      (cuuint64_t)a.nx * a.ny * CIN * 2};
+    const cuuint32_t box_cl[4] = {8, (cuuint32_t)kHX, (cuuint32_t)kHY, (cuuint32_t)kHZ};
+    const cuuint64_t dims_pl[4] = {(cuuint64_t)a.nx * 8, (cuuint64_t)a.ny, (cuuint64_t)a.nz,
+                                   (cuuint64_t)(CIN / 8)};
+    const cuuint64_t strides_pl[3] = {(cuuint64_t)a.nx * 16, (cuuint64_t)a.nx * a.ny * 16, V * 16};
+    const cuuint32_t box_pl[4] = {(cuuint32_t)kHX * 8, (cuuint32_t)kHY, (cuuint32_t)kHZ, 1};
+    const cuuint64_t* dims = a.in_planar ? dims_pl : dims_cl;
+    const cuuint64_t* strides = a.in_planar ? strides_pl : strides_cl;
+    const cuuint32_t* box = a.in_planar ? box_pl : box_cl;
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(a.in), dims,
                strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -747,6 +772,11 @@ int launch_conv(const ConvArgs& a, bool relu, bool out_f32, long long V, cudaStr
             else r = launch_tma_t<CIN, COUT, false, false>(a, st);
             if (r != 0) return r == 1 ? SBP_OK : r;
         }
+    }
+    // planar input is read by the TMA kernel only
+    if (a.in_planar) {
+        sbp_set_error("conv3d: planar input needs the TMA kernel (Cin 16 or 32, a tensor map)");
+        return SBP_ERR_ARG;
     }
     // the halo kernel where its staged halo and weights fit one CTA's shared
     // memory and the grid's y and z extents allow it
@@ -812,8 +842,10 @@ __device__ __forceinline__ void wg_store8(uint8_t* tile, int r0, int k8, const u
 }
 
 struct WgradArgs {
-    const __nv_bfloat16* g;  // [V][Cout]
-    const __nv_bfloat16* x;  // [V][Cin]
+    const __nv_bfloat16* g;  // [V][Cout], or planar (g_planar)
+    const __nv_bfloat16* x;  // [V][Cin], or planar (x_planar)
+    int x_planar, g_planar;
+    long long V;
     float* partial;          // [chunks][m_pad][Cout]
     int nx, ny, nz;
     int xblocks;             // ceil(nx / 64)
@@ -884,9 +916,11 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(WgradArgs a) {
             for (int j = 0; j < 8; ++j) {
                 const int xx = xv + j + dx;
                 blk[j] = make_uint4(0u, 0u, 0u, 0u);
-                if (row_in && xv + j < a.nx && xx >= 0 && xx < a.nx)
+                if (row_in && xv + j < a.nx && xx >= 0 && xx < a.nx) {
+                    const long long v = ((long long)zz * a.ny + yy) * a.nx + xx;
                     blk[j] = *reinterpret_cast<const uint4*>(
-                        a.x + (((long long)zz * a.ny + yy) * a.nx + xx) * CIN + c0);
+                        a.x + (a.x_planar ? ((long long)(c0 >> 3) * a.V + v) * 8 : v * CIN + c0));
+                }
             }
             wg_transpose8(blk, rows);
             if (m0 == 27 * CIN) {  // the bias row: ones over the volume, then zero rows
@@ -931,8 +965,11 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(WgradArgs a) {
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 blk[j] = make_uint4(0u, 0u, 0u, 0u);
-                if (xv + j < a.nx)
-                    blk[j] = *reinterpret_cast<const uint4*>(a.g + (vrow + xv + j) * COUT + r8 * 8);
+                if (xv + j < a.nx) {
+                    const long long v = vrow + xv + j;
+                    blk[j] = *reinterpret_cast<const uint4*>(
+                        a.g + (a.g_planar ? ((long long)r8 * a.V + v) * 8 : v * COUT + r8 * 8));
+                }
             }
             wg_transpose8(blk, rows);
             wg_store8(tileB, r8 * 8, k8, rows);
@@ -1049,12 +1086,16 @@ long long sbp_wgrad_scratch_floats(int nx, int ny, int nz, int cin, int cout, in
 }
 
 int sbp_wgrad_bf16(const void* g_dev, const void* x_dev, int nx, int ny, int nz, int cin,
-                   int cout, int sms, float* partial, float* dW, float* db, cudaStream_t st) {
+                   int cout, int sms, float* partial, float* dW, float* db, bool x_planar,
+                   bool g_planar, cudaStream_t st) {
     WgradArgs a;
     int chunks;
     wgrad_plan(nx, ny, nz, cin, sms, a.xblocks, a.steps, a.steps_per_chunk, chunks, a.m_pad);
     a.g = static_cast<const __nv_bfloat16*>(g_dev);
     a.x = static_cast<const __nv_bfloat16*>(x_dev);
+    a.x_planar = (x_planar && cin % 8 == 0) ? 1 : 0;
+    a.g_planar = g_planar ? 1 : 0;
+    a.V = (long long)nx * ny * nz;
     a.partial = partial;
     a.nx = nx;
     a.ny = ny;
@@ -1070,11 +1111,9 @@ namespace {
 
 }  // namespace
 
-extern "C" {
-
-int sbp_conv3d_bf16(const void* in_dev, int nx, int ny, int nz, int cin, const void* w_dev,
-                    int kp, const float* bias_dev, int cout, int relu, void* out_dev, int out_f32,
-                    sbp_stream stream) {
+int sbp_conv3d_layout(const void* in_dev, int nx, int ny, int nz, int cin, const void* w_dev,
+                      int kp, const float* bias_dev, int cout, int relu, void* out_dev,
+                      int out_f32, bool in_planar, bool out_planar, cudaStream_t st) {
     const long long V = (long long)nx * ny * nz;
     if (!in_dev || !w_dev || !out_dev || nx < 1 || ny < 1 || nz < 1 || kp < 27 * cin ||
         kp % kTcBK != 0 || V > (1LL << 31) * kTcRows) {
@@ -1086,9 +1125,21 @@ int sbp_conv3d_bf16(const void* in_dev, int nx, int ny, int nz, int cin, const v
         sbp_set_error("conv3d_bf16: arrays must be 16-byte aligned");
         return SBP_ERR_ARG;
     }
-    ConvArgs a{static_cast<const __nv_bfloat16*>(in_dev), static_cast<const __nv_bfloat16*>(w_dev),
-               bias_dev, out_dev, nx, ny, nz, kp};
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if ((in_planar && cin % 8 != 0) || (out_planar && (out_f32 || cout % 16 != 0))) {
+        sbp_set_error("conv3d: planar layouts need Cin a multiple of 8, Cout of 16, bf16 output");
+        return SBP_ERR_ARG;
+    }
+    ConvArgs a{static_cast<const __nv_bfloat16*>(in_dev),
+               static_cast<const __nv_bfloat16*>(w_dev),
+               bias_dev,
+               out_dev,
+               nx,
+               ny,
+               nz,
+               kp,
+               in_planar ? 1 : 0,
+               out_planar ? 1 : 0,
+               V};
     int rc = SBP_ERR_ARG + 100;  // "no case matched" until a case launches
 #define SBP_CONV_CASE(CI, CO) \
     if (cin == CI && cout == CO) rc = launch_conv<CI, CO>(a, relu != 0, out_f32 != 0, V, st);
@@ -1109,6 +1160,15 @@ int sbp_conv3d_bf16(const void* in_dev, int nx, int ny, int nz, int cin, const v
     if (rc != SBP_OK) return rc;
     sbp_count_launches(1);
     return sbp_cuda_check(cudaGetLastError(), "conv3d_bf16 launch") ? SBP_ERR_CUDA : SBP_OK;
+}
+
+extern "C" {
+
+int sbp_conv3d_bf16(const void* in_dev, int nx, int ny, int nz, int cin, const void* w_dev,
+                    int kp, const float* bias_dev, int cout, int relu, void* out_dev, int out_f32,
+                    sbp_stream stream) {
+    return sbp_conv3d_layout(in_dev, nx, ny, nz, cin, w_dev, kp, bias_dev, cout, relu, out_dev,
+                             out_f32, false, false, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int sbp_cnn_status(sbp_stream stream, int* status) {

@@ -201,8 +201,17 @@ int sbp_launch_sort(sbp_array_s* a, float* const* rows, int nrows, const int* n_
 
 // weight gradient of the proposal CNN's convolutions on the tensor cores (sbp_cnn.cu)
 long long sbp_wgrad_scratch_floats(int nx, int ny, int nz, int cin, int cout, int sms);
+// The 3x3x3 convolution of sbp_conv3d_bf16 with a choice of activation
+// layouts: channels-last [V][C] or planar [C / 8][V][8] for the input (Cin a
+// multiple of 8, read by the TMA kernel only) and the bf16 output (Cout a
+// multiple of 16).
+int sbp_conv3d_layout(const void* in_dev, int nx, int ny, int nz, int cin, const void* w_dev,
+                      int kp, const float* bias_dev, int cout, int relu, void* out_dev,
+                      int out_f32, bool in_planar, bool out_planar, cudaStream_t st);
+// x and g are channels-last or planar (x_planar, g_planar; Cin = 1 is [V]).
 int sbp_wgrad_bf16(const void* g_dev, const void* x_dev, int nx, int ny, int nz, int cin,
-                   int cout, int sms, float* partial, float* dW, float* db, cudaStream_t st);
+                   int cout, int sms, float* partial, float* dW, float* db, bool x_planar,
+                   bool g_planar, cudaStream_t st);
 
 // ----------------------------------------------------------------------------
 // device helpers

@@ -14,8 +14,12 @@
 //     over voxels on the tensor cores too, sbp_wgrad_bf16, reduced in a
 //     fixed order so that a training step is reproducible bit for bit) and
 //     Adam on FP32 master weights;
-//   * the proposal: one ball per voxel whose occupancy probability exceeds a
-//     threshold, at a seeded random point of the voxel, in voxel order.
+//   * the proposal: a given number of balls in every voxel whose occupancy
+//     probability exceeds a threshold, each at a seeded random point of the
+//     voxel, in voxel order.
+// The hidden activations h1, h2 and their gradients g1, g2 are kept planar
+// ([C / 8][V][8]), so that the TMA-fed convolutions that read them copy halo
+// rows of ten voxels instead of one; h3 and g3 are channels-last.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -26,10 +30,6 @@
 
 #include "sbp_internal.cuh"
 #include "sbp_scan.cuh"
-
-extern "C" int sbp_conv3d_bf16(const void* in_dev, int nx, int ny, int nz, int cin,
-                               const void* w_dev, int kp, const float* bias_dev, int cout,
-                               int relu, void* out_dev, int out_f32, sbp_stream stream);
 
 namespace {
 
@@ -59,12 +59,12 @@ struct sbp_cnn_s {
     __nv_bfloat16* w2t = nullptr;  // dgrad of conv2: [16][padded_k(32)]
     __nv_bfloat16* w3t = nullptr;  // dgrad of conv3: [32][padded_k(64)]
     __nv_bfloat16* x0 = nullptr;   // [V] scaled input
-    __nv_bfloat16* h1 = nullptr;   // [V][16]
-    __nv_bfloat16* h2 = nullptr;   // [V][32]
+    __nv_bfloat16* h1 = nullptr;   // [2][V][8] (planar)
+    __nv_bfloat16* h2 = nullptr;   // [4][V][8] (planar)
     __nv_bfloat16* h3 = nullptr;   // [V][64]
     __nv_bfloat16* g3 = nullptr;   // [V][64] gradient before conv3's ReLU
-    __nv_bfloat16* g2 = nullptr;   // [V][32]
-    __nv_bfloat16* g1 = nullptr;   // [V][16]
+    __nv_bfloat16* g2 = nullptr;   // [4][V][8] (planar)
+    __nv_bfloat16* g1 = nullptr;   // [2][V][8] (planar)
     float* out = nullptr;          // [V][2]
     float* dout = nullptr;         // [V][2]
     unsigned int* vmax = nullptr;  // bits of max |volume|
@@ -419,20 +419,21 @@ int pack_all(sbp_cnn c, cudaStream_t st) {
 // input scaling and the three convolutions and the head
 int forward(sbp_cnn c, const float* vol, cudaStream_t st) {
     const long long V = c->V;
-    void* s = reinterpret_cast<void*>(st);
     if (sbp_cuda_check(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned int), st), "cnn: reset"))
         return SBP_ERR_CUDA;
     absmax_kernel<<<blocks_for(V), 256, 0, st>>>(vol, V, c->vmax);
     scale_input_kernel<<<blocks_for(V), 256, 0, st>>>(vol, V, c->vmax, c->x0);
     sbp_count_launches(2);
-    if (int e = sbp_conv3d_bf16(c->x0, c->nx, c->ny, c->nz, 1, c->w1, padded_k(1),
-                                c->p + kOB1, kC1, 1, c->h1, 0, s))
+    // h1 and h2 are planar ([C / 8][V][8]): the next layer's TMA halo boxes
+    // then have rows of ten voxels; h3 is channels-last for the head
+    if (int e = sbp_conv3d_layout(c->x0, c->nx, c->ny, c->nz, 1, c->w1, padded_k(1), c->p + kOB1,
+                                  kC1, 1, c->h1, 0, false, true, st))
         return e;
-    if (int e = sbp_conv3d_bf16(c->h1, c->nx, c->ny, c->nz, kC1, c->w2, padded_k(kC1),
-                                c->p + kOB2, kC2, 1, c->h2, 0, s))
+    if (int e = sbp_conv3d_layout(c->h1, c->nx, c->ny, c->nz, kC1, c->w2, padded_k(kC1),
+                                  c->p + kOB2, kC2, 1, c->h2, 0, true, true, st))
         return e;
-    if (int e = sbp_conv3d_bf16(c->h2, c->nx, c->ny, c->nz, kC2, c->w3, padded_k(kC2),
-                                c->p + kOB3, kC3, 1, c->h3, 0, s))
+    if (int e = sbp_conv3d_layout(c->h2, c->nx, c->ny, c->nz, kC2, c->w3, padded_k(kC2),
+                                  c->p + kOB3, kC3, 1, c->h3, 0, true, false, st))
         return e;
     head_fwd_kernel<<<blocks_for(V), 256, 0, st>>>(c->h3, V, c->p, c->out);
     sbp_count_launches(1);
@@ -603,7 +604,6 @@ namespace {
 // fixed order of additions, and the two loss terms into c->loss.
 int backward(sbp_cnn c, const float* vol_dev, const float* occ_dev, const float* p0_dev,
              float pos_weight, cudaStream_t st) {
-    void* s = reinterpret_cast<void*>(st);
     const long long V = c->V;
     const int nx = c->nx, ny = c->ny, nz = c->nz;
     if (int e = forward(c, vol_dev, st)) return e;
@@ -619,24 +619,25 @@ int backward(sbp_cnn c, const float* vol_dev, const float* occ_dev, const float*
     head_param_reduce_kernel<<<1, 256, 0, st>>>(c->hd_part, (int)hb, G);
     sbp_count_launches(4);
     // conv3: weights (tensor cores), then the data gradient into g2 (masked by conv2's ReLU)
+    // g3 is channels-last like h3; g2 and g1 are planar like h2 and h1
     if (int e = sbp_wgrad_bf16(c->g3, c->h2, nx, ny, nz, kC2, kC3, c->sms, c->wg_part, G + kOW3,
-                               G + kOB3, st))
+                               G + kOB3, true, false, st))
         return e;
-    if (int e = sbp_conv3d_bf16(c->g3, nx, ny, nz, kC3, c->w3t, padded_k(kC3), nullptr, kC2, 0,
-                                c->g2, 0, s))
+    if (int e = sbp_conv3d_layout(c->g3, nx, ny, nz, kC3, c->w3t, padded_k(kC3), nullptr, kC2, 0,
+                                  c->g2, 0, false, true, st))
         return e;
     relu_mask_kernel<<<blocks_for(V * kC2), 256, 0, st>>>(c->g2, c->h2, V * kC2);
     sbp_count_launches(1);
     if (int e = sbp_wgrad_bf16(c->g2, c->h1, nx, ny, nz, kC1, kC2, c->sms, c->wg_part, G + kOW2,
-                               G + kOB2, st))
+                               G + kOB2, true, true, st))
         return e;
-    if (int e = sbp_conv3d_bf16(c->g2, nx, ny, nz, kC2, c->w2t, padded_k(kC2), nullptr, kC1, 0,
-                                c->g1, 0, s))
+    if (int e = sbp_conv3d_layout(c->g2, nx, ny, nz, kC2, c->w2t, padded_k(kC2), nullptr, kC1, 0,
+                                  c->g1, 0, true, true, st))
         return e;
     relu_mask_kernel<<<blocks_for(V * kC1), 256, 0, st>>>(c->g1, c->h1, V * kC1);
     sbp_count_launches(1);
     if (int e = sbp_wgrad_bf16(c->g1, c->x0, nx, ny, nz, 1, kC1, c->sms, c->wg_part, G + kOW1,
-                               G + kOB1, st))
+                               G + kOB1, false, true, st))
         return e;
     return sbp_cuda_check(cudaGetLastError(), "cnn backward") ? SBP_ERR_CUDA : SBP_OK;
 }
