@@ -339,6 +339,149 @@ constexpr int halo_smem_bytes() {
     return CIN / 8 * kHV * 16 + 27 * (CIN / 8) * COUT * 16;
 }
 
+// One input channel (the network's first layer). A CTA takes an 8 x 16 x 4
+// block of voxels, four MMA tiles of 128 stacked along z, and stages the
+// block's 10 x 18 x 6 input halo in shared memory (zero outside the volume).
+// Each thread then writes its voxel row of every tile's im2col operand from
+// the halo: the 27 taps padded with zeros to K = 32, in the canonical K-major
+// layout (core matrices 128 bytes apart along K, 8-row groups 512 bytes
+// apart). One thread issues two K = 16 MMAs per tile, each tile into its own
+// COUT columns of TMEM, and one commit; the epilogue then reads all four.
+// (The gather kernel read its 27 values per voxel from global memory and
+// built one tile per CTA.)
+constexpr int kC1Tiles = 4;                 // z-slices per CTA
+constexpr int kC1HZ = kC1Tiles + 2;         // halo depth
+constexpr int kC1K = 32;                    // 27 taps padded
+constexpr int kC1TileBytes = kTcRows * kC1K * 2;
+
+template <int COUT, bool RELU, bool OUT_F32>
+__global__ void __launch_bounds__(kTcThreads) conv3d_c1_kernel(ConvArgs a) {
+    static_assert(COUT % 16 == 0 && COUT * kC1Tiles <= kTcCols, "every tile needs its columns");
+    __shared__ __align__(1024) uint8_t s_a[kC1Tiles * kC1TileBytes];
+    __shared__ __align__(128) uint8_t s_b[COUT * kC1K * 2];
+    __shared__ __nv_bfloat16 s_h[kC1HZ * kHY * kHX];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_tmem;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int x0 = blockIdx.x * kHTX, y0 = blockIdx.y * kHTY, z0 = blockIdx.z * kC1Tiles;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // the halo, x fastest
+    for (int i = tid; i < kC1HZ * kHY * kHX; i += kTcThreads) {
+        const int hx = i % kHX, hy = (i / kHX) % kHY, hz = i / (kHX * kHY);
+        const int x = x0 - 1 + hx, y = y0 - 1 + hy, z = z0 - 1 + hz;
+        __nv_bfloat16 v = __float2bfloat16(0.0f);
+        if (x >= 0 && x < a.nx && y >= 0 && y < a.ny && z >= 0 && z < a.nz)
+            v = a.in[((long long)z * a.ny + y) * a.nx + x];
+        s_h[i] = v;
+    }
+    // the weights' first 32 K values: row n, chunk kc at (n / 8) 512 + kc 128 + (n % 8) 16
+    for (int t = tid; t < COUT * (kC1K / 8); t += kTcThreads) {
+        const int n = t / (kC1K / 8), kc = t % (kC1K / 8);
+        *reinterpret_cast<uint4*>(s_b + (n >> 3) * 512 + kc * 128 + (n & 7) * 16) =
+            *reinterpret_cast<const uint4*>(a.w + (size_t)n * a.Kp + kc * 8);
+    }
+    __syncthreads();
+    // this thread's row m of each tile: voxel (x0 + m % 8, y0 + m / 8, z0 + t)
+    const int m = tid, mx = m & 7, my = m >> 3;
+#pragma unroll
+    for (int t = 0; t < kC1Tiles; ++t) {
+        union {
+            uint4 u[4];
+            __nv_bfloat16 h[32];
+        } row;
+#pragma unroll
+        for (int k = 0; k < kC1K; ++k) {
+            if (k < 27) {
+                const int dx = k % 3, dy = (k / 3) % 3, dz = k / 9;
+                row.h[k] = s_h[((t + dz) * kHY + my + dy) * kHX + mx + dx];
+            } else {
+                row.h[k] = __float2bfloat16(0.0f);
+            }
+        }
+        uint8_t* dst = s_a + t * kC1TileBytes + (m >> 3) * 512 + (m & 7) * 16;
+#pragma unroll
+        for (int kc = 0; kc < 4; ++kc) *reinterpret_cast<uint4*>(dst + kc * 128) = row.u[kc];
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    if (tid == 0) {
+        constexpr uint32_t idesc = umma_idesc_bf16(kTcRows, COUT);
+        const uint32_t a0 = smem_u32(s_a), b0 = smem_u32(s_b);
+#pragma unroll
+        for (int t = 0; t < kC1Tiles; ++t)
+#pragma unroll
+            for (int ks = 0; ks < kC1K / 16; ++ks)
+                tc_mma(tmem + (uint32_t)(t * COUT),
+                       umma_desc(a0 + t * kC1TileBytes + ks * 256, 128, 512),
+                       umma_desc(b0 + ks * 256, 128, 512), idesc, ks > 0 ? 1u : 0u);
+        tc_commit(&bar);
+    }
+    const bool ok = mbar_wait(&bar, 0u);
+    tc_fence_after();
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicExch(&g_cnn_status, 1);
+    } else {
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        const int x = x0 + mx, y = y0 + my;
+#pragma unroll
+        for (int t = 0; t < kC1Tiles; ++t) {
+            const int z = z0 + t;
+            const bool mv = x < a.nx && y < a.ny && z < a.nz;
+            const long long q = ((long long)z * a.ny + y) * a.nx + x;
+#pragma unroll
+            for (int c0 = 0; c0 < COUT; c0 += 16) {
+                float v[16];
+                tc_ld16(taddr + (uint32_t)(t * COUT + c0), v);
+                if (mv) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        float r = v[j] + (a.bias ? a.bias[c0 + j] : 0.0f);
+                        if (RELU) r = fmaxf(r, 0.0f);
+                        v[j] = r;
+                    }
+                    if constexpr (OUT_F32) {
+                        float4* o =
+                            reinterpret_cast<float4*>(static_cast<float*>(a.out) + q * COUT + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                    } else {
+                        store16_bf16<COUT>(a, q, c0, v);
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTcCols)
+                     : "memory");
+}
+
+template <int COUT, bool RELU, bool OUT_F32>
+int launch_c1_t(const ConvArgs& a, cudaStream_t st) {
+    const dim3 grid((a.nx + kHTX - 1) / kHTX, (a.ny + kHTY - 1) / kHTY,
+                    (a.nz + kC1Tiles - 1) / kC1Tiles);
+    conv3d_c1_kernel<COUT, RELU, OUT_F32><<<grid, kTcThreads, 0, st>>>(a);
+    return SBP_OK;
+}
+
 template <int CIN, int COUT, bool RELU, bool OUT_F32>
 __global__ void __launch_bounds__(kTcThreads) conv3d_halo_kernel(ConvArgs a) {
     static_assert(CIN % 16 == 0, "one MMA (K = 16) takes two channel chunks of one tap");
@@ -761,6 +904,15 @@ int launch_conv_t(const ConvArgs& a, unsigned blocks, cudaStream_t st) {
 
 template <int CIN, int COUT>
 int launch_conv(const ConvArgs& a, bool relu, bool out_f32, long long V, cudaStream_t st) {
+    // one input channel: the staged-halo kernel, four tiles per CTA
+    if constexpr (CIN == 1 && COUT * kC1Tiles <= kTcCols) {
+        if ((a.ny + kHTY - 1) / kHTY <= 65535 && (a.nz + kC1Tiles - 1) / kC1Tiles <= 65535) {
+            if (relu && out_f32) return launch_c1_t<COUT, true, true>(a, st);
+            if (relu) return launch_c1_t<COUT, true, false>(a, st);
+            if (out_f32) return launch_c1_t<COUT, false, true>(a, st);
+            return launch_c1_t<COUT, false, false>(a, st);
+        }
+    }
     // the persistent TMA kernel for 16 or 32 input channels, where its three
     // halo slots and the weights fit one CTA's shared memory
     if constexpr (CIN % 16 == 0 && CIN <= 32 && tma_smem_bytes<CIN, COUT>() <= 220 * 1024) {
