@@ -522,22 +522,33 @@ def algorithmic_ops(kind, s):
 NCU_RECORD = {
     "forward": {"sources": ["paper_2601_00551_gb300/csrc/sbp_forward.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "6d38abae5c921b5c", "bytes": 3.5644928e7,
+                "sha256": "ac7e4f88cefc5535", "bytes": 3.5644928e7,
                 "thread_inst_per_pair": 175.2},
     "adjoint": {"sources": ["paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "a7af4d6d5caea095", "bytes": 6.5840128e7,
+                "sha256": "7ea5bec7147c4b1e", "bytes": 6.5840128e7,
                 "thread_inst_per_pair": 203.5},
 }
 
 
+DEVICE_MARK = b"// device helpers"
+
+
 def sources_sha(name):
+    """Hash of the kernel's own source file and, of the shared header, its
+    #define lines and its device-code part (from the "device helpers"
+    section on): what the compiled kernel depends on, not the header's host
+    declarations."""
     import hashlib
 
     m = hashlib.sha256()
     for src in NCU_RECORD[name]["sources"]:
         with open(os.path.join(ROOT, src), "rb") as f:
-            m.update(f.read())
+            data = f.read()
+        if src.endswith(".cuh") and DEVICE_MARK in data:
+            defines = b"".join(ln for ln in data.splitlines(True) if ln.startswith(b"#define"))
+            data = defines + data[data.index(DEVICE_MARK):]
+        m.update(data)
     return m.hexdigest()[:16]
 
 

@@ -119,6 +119,30 @@ def test_ncu_record_holds_only_for_the_measured_sources(monkeypatch):
     assert bench.ncu_record("adjoint") == (None, None)
 
 
+def test_record_hash_follows_the_kernel_not_host_declarations(monkeypatch, tmp_path):
+    """The ncu record's source hash changes with the kernel's file, with a
+    #define of the shared header and with the header's device code, but not
+    with a host declaration added to the header."""
+    import shutil
+
+    rec = bench.NCU_RECORD["adjoint"]
+    for src in rec["sources"]:
+        (tmp_path / src).parent.mkdir(parents=True, exist_ok=True)
+        shutil.copy(os.path.join(bench.ROOT, src), tmp_path / src)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    base = bench.sources_sha("adjoint")
+    hdr = tmp_path / [s for s in rec["sources"] if s.endswith(".cuh")][0]
+    text = hdr.read_text()
+    mark = bench.DEVICE_MARK.decode()
+    i = text.index(mark)
+    hdr.write_text(text[:i] + "int some_host_function(int);\n" + text[i:])
+    assert bench.sources_sha("adjoint") == base
+    hdr.write_text(text.replace("#define SBP_ADJ_MAX_SPLIT 8", "#define SBP_ADJ_MAX_SPLIT 16"))
+    assert bench.sources_sha("adjoint") != base
+    hdr.write_text(text + "// a device-side change\n")
+    assert bench.sources_sha("adjoint") != base
+
+
 def test_stage_schedules():
     """Coarse stage (p0 and R) 40 iterations per level coarse to fine, then
     the fine stage (all components) 30 per coarser level and the rest at the
