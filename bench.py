@@ -1805,31 +1805,53 @@ def unsorted_vessel(sb, dev, steps=5, warmup=2):
     return out
 
 
-def autograd_memory(sb, arr, wl, init, n0, dev):
-    """Per-level trace checkpointing: the autograd Function saves only the
-    cloud and recomputes the geometry in the adjoint. Peak device memory of
-    one radiate() forward + backward at the finest level of the vessel
-    workload, against what storing every pair's window would take (pairs x
-    mean window cells x 4 bytes)."""
+def autograd_memory(sb, arr, wl, init, n0, dev, reps=3):
+    """Per-level trace checkpointing against stored windows, at the finest
+    level of the vessel workload (200k balls x 512 sensors, T = 4096). The
+    checkpointing autograd Function (radiate) saves only the cloud and the
+    adjoint recomputes each pair's geometry; the stored-window one
+    (radiate_stored) also writes every pair's window record (20 bytes) in
+    the forward and the adjoint reads it back. For each: peak device memory
+    of one forward + backward above the inputs, and its device time (CUDA
+    events, mean of `reps` after a warm-up)."""
     import torch
 
     nl = len(wl.levels)
     k = nl - 1
-    x, y, z, R, p0 = (init[c, :n0].clone().requires_grad_(True) for c in range(5))
-    torch.cuda.synchronize()
-    base = torch.cuda.memory_allocated()
-    torch.cuda.reset_peak_memory_stats()
-    S = sb.radiate(arr, x, y, z, R, p0, level=k)
-    (S * S).sum().backward()
-    torch.cuda.synchronize()
-    peak = torch.cuda.max_memory_allocated() - base
-    h = wl.c * wl.levels[k] / wl.fs_mhz
-    cells = 2.0 * float(np.mean(wl.init.R)) / h + 1.0
-    pairs = float(n0) * wl.sensors.M
-    return {"balls": n0, "sensors": wl.sensors.M, "T": arr.level_info(k)[0],
-            "peak_bytes_forward_backward": int(peak),
-            "stored_windows_bytes_estimate": int(pairs * cells * 4),
-            "ratio": pairs * cells * 4 / max(1, peak)}
+    out = {"balls": n0, "sensors": wl.sensors.M, "T": arr.level_info(k)[0]}
+    for name, fn in (("checkpointed", sb.radiate), ("stored_windows", sb.radiate_stored)):
+        x, y, z, R, p0 = (init[c, :n0].clone().requires_grad_(True) for c in range(5))
+
+        def once():
+            for t in (x, y, z, R, p0):
+                t.grad = None
+            S = fn(arr, x, y, z, R, p0, level=k)
+            (S * S).sum().backward()
+
+        once()  # warm-up (and the level's first-use allocations)
+        torch.cuda.synchronize()
+        base = torch.cuda.memory_allocated()
+        torch.cuda.reset_peak_memory_stats()
+        once()
+        torch.cuda.synchronize()
+        peak = torch.cuda.max_memory_allocated() - base
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            once()
+        b.record()
+        torch.cuda.synchronize()
+        out[name] = {"peak_bytes_forward_backward": int(peak),
+                     "ms_forward_backward": a.elapsed_time(b) / reps}
+        del x, y, z, R, p0
+    if arr.sync_status() != 0:
+        raise RuntimeError("device status latched in the autograd memory arm")
+    out["memory_ratio"] = (out["stored_windows"]["peak_bytes_forward_backward"] /
+                           max(1, out["checkpointed"]["peak_bytes_forward_backward"]))
+    out["time_ratio"] = (out["stored_windows"]["ms_forward_backward"] /
+                         out["checkpointed"]["ms_forward_backward"])
+    return out
 
 
 def run_e2e(args, sb, arr, wl, y_host, init, n0, n_cap, stages, adam, pairs_per_step, dev):

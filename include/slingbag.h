@@ -210,6 +210,27 @@ int sbp_residual(sbp_array arr, const float* S_dev, const float* y_k_dev, float*
 int sbp_adjoint(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap,
                 const float* G_dev, sbp_grads out, unsigned grad_mask, sbp_stream stream);
 
+/* Stored windows: the alternative to sbp_adjoint's recomputation of every
+ * pair's geometry in the backpropagation step of Algorithm 1 (kept to
+ * measure the memory / time trade; sbp_adjoint is the path the loop uses).
+ * sbp_store_windows writes, for every (sensor m, ball i) pair of the live
+ * balls at the current level, a record into rec_dev: five planes of
+ * [M][n_cap] 4-byte words (20 M n_cap bytes, caller-owned device memory,
+ * 4-byte aligned): the offset of the first boundary inside the support
+ * (float), the orientation weight (float), ~1/d (float), the first and the
+ * last boundary inside the support (int; first = -1 when the pair adds
+ * nothing, bit 31 of the last set when the weight's derivative is non-zero).
+ * sbp_adjoint_stored then computes what sbp_adjoint computes (same
+ * gradients up to float summation order, same masks, each live ball's
+ * components written once) from those records, G_dev and the cloud, without
+ * evaluating distances, windows or weights. The records must come from the
+ * same cloud, level and array. SBP_ERR_ARG for null or misaligned pointers. */
+int sbp_store_windows(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap,
+                      void* rec_dev, sbp_stream stream);
+int sbp_adjoint_stored(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap,
+                       const void* rec_dev, const float* G_dev, sbp_grads out,
+                       unsigned grad_mask, sbp_stream stream);
+
 /* Tile choice of the single-cloud sbp_forward and sbp_adjoint at level k
  * (a launch parameter only: the forward is bitwise identical for every
  * choice, the adjoint differs by float summation order). fwd_chunk: balls

@@ -288,6 +288,33 @@ int sbp_adjoint(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap, con
                               as_stream(stream));
 }
 
+int sbp_store_windows(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap,
+                      void* rec_dev, sbp_stream stream) {
+    if (int e = check_array(arr, "store_windows")) return e;
+    if (int e = check_cap(arr, n_cap, "store_windows")) return e;
+    if (!balls_ok(balls) || !rec_dev || (reinterpret_cast<uintptr_t>(rec_dev) & 3u)) {
+        sbp_set_error("store_windows: null or misaligned pointer");
+        return SBP_ERR_ARG;
+    }
+    if (n_cap == 0) return SBP_OK;
+    return sbp_launch_store_windows(arr, to_dev(balls), n_dev, n_cap, rec_dev, as_stream(stream));
+}
+
+int sbp_adjoint_stored(sbp_array arr, sbp_balls balls, const int* n_dev, int n_cap,
+                       const void* rec_dev, const float* G_dev, sbp_grads out,
+                       unsigned grad_mask, sbp_stream stream) {
+    if (int e = check_array(arr, "adjoint_stored")) return e;
+    if (int e = check_cap(arr, n_cap, "adjoint_stored")) return e;
+    if (!balls_ok(balls) || !grads_ok(out) || !rec_dev || !G_dev ||
+        (reinterpret_cast<uintptr_t>(rec_dev) & 3u) || (grad_mask & ~SBP_MASK_ALL)) {
+        sbp_set_error("adjoint_stored: null or misaligned pointer, or unknown mask bit");
+        return SBP_ERR_ARG;
+    }
+    if (n_cap == 0) return SBP_OK;
+    return sbp_launch_adjoint_stored(arr, to_dev(balls), n_dev, n_cap, rec_dev, G_dev, out,
+                                     grad_mask, as_stream(stream));
+}
+
 namespace {
 
 bool fwd_chunk_ok(int c) { return c == 0 || sbp_fwd_tile_valid(c); }

@@ -199,6 +199,14 @@ int sbp_launch_downsample_rows(sbp_array_s* a, int k, int rows, const float* y_f
 int sbp_launch_sort(sbp_array_s* a, float* const* rows, int nrows, const int* n_dev, int n_cap,
                     cudaStream_t st);
 
+// Stored-window forward records and the adjoint that reads them (sbp_stored.cu):
+// rec_dev holds five [M][n_cap] planes of 4-byte words.
+int sbp_launch_store_windows(sbp_array_s* a, const BallsDev& b, const int* n_dev, int n_cap,
+                             void* rec_dev, cudaStream_t st);
+int sbp_launch_adjoint_stored(sbp_array_s* a, const BallsDev& b, const int* n_dev, int n_cap,
+                              const void* rec_dev, const float* G, sbp_grads out, unsigned mask,
+                              cudaStream_t st);
+
 // weight gradient of the proposal CNN's convolutions on the tensor cores (sbp_cnn.cu)
 long long sbp_wgrad_scratch_floats(int nx, int ny, int nz, int cin, int cout, int sms);
 // The 3x3x3 convolution of sbp_conv3d_bf16 with a choice of activation

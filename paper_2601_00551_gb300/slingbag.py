@@ -99,6 +99,9 @@ _SIGS = {
                                           _P, _P]),
     "sbp_residual": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "sbp_adjoint": (ctypes.c_int, [_P, _Balls, _P, ctypes.c_int, _P, _Balls, ctypes.c_uint, _P]),
+    "sbp_store_windows": (ctypes.c_int, [_P, _Balls, _P, ctypes.c_int, _P, _P]),
+    "sbp_adjoint_stored": (ctypes.c_int, [_P, _Balls, _P, ctypes.c_int, _P, _P, _Balls,
+                                          ctypes.c_uint, _P]),
     "sbp_filter_grow": (ctypes.c_int, [_P, _Balls, _Balls, ctypes.POINTER(_P), ctypes.c_int, _P,
                                        ctypes.c_int, ctypes.POINTER(_GrowParams), ctypes.c_int,
                                        _P]),
@@ -419,6 +422,34 @@ class SensorArray:
                                                     mask, _stream()))
         return out
 
+    def store_windows(self, balls: torch.Tensor, n=None, out: torch.Tensor | None = None):
+        """Per-pair window records of the current level (sbp_store_windows):
+        an int32 tensor (5, M, n_cap) whose planes 0-2 hold float32 bits."""
+        if out is None:
+            out = torch.empty((5, self.M, balls.shape[1]), dtype=torch.int32, device=balls.device)
+        if out.dtype != torch.int32 or not out.is_cuda or not out.is_contiguous() or \
+                tuple(out.shape) != (5, self.M, balls.shape[1]):
+            raise ValueError("out must be a contiguous int32 CUDA tensor (5, M, n_cap)")
+        nd = self._n(n, balls.shape[1])
+        _check("sbp_store_windows", self._lib.sbp_store_windows(
+            self._h, _rows(balls), _dptr(nd), balls.shape[1], _dptr(out), _stream()))
+        return out
+
+    def adjoint_stored(self, balls: torch.Tensor, G: torch.Tensor, rec: torch.Tensor, n=None,
+                       mask: int = MASK_ALL, out: torch.Tensor | None = None):
+        """Per-ball gradients from stored window records (sbp_adjoint_stored)."""
+        self._check_traces(G, self.Tk)
+        if rec.dtype != torch.int32 or not rec.is_cuda or not rec.is_contiguous() or \
+                tuple(rec.shape) != (5, self.M, balls.shape[1]):
+            raise ValueError("rec must come from store_windows of this cloud")
+        if out is None:
+            out = torch.empty_like(balls)
+        nd = self._n(n, balls.shape[1])
+        _check("sbp_adjoint_stored", self._lib.sbp_adjoint_stored(
+            self._h, _rows(balls), _dptr(nd), balls.shape[1], _dptr(rec), _dptr(G), _rows(out),
+            mask, _stream()))
+        return out
+
     def filter_grow(self, balls: torch.Tensor, grads: torch.Tensor, n_dev: torch.Tensor,
                     mode: int = KEEP_NEG, grow: GrowParams | None = None, extra=()):
         """Filter/grow in place (sbp_filter_grow); n_dev is updated on the device."""
@@ -724,6 +755,35 @@ def radiate(array: SensorArray, x, y, z, R, p0, level: int = 0) -> torch.Tensor:
     centres (x, y, z), radii R and pressures p0 (float32 CUDA vectors) at
     sampling level `level` of `array`."""
     return _Radiator.apply(x, y, z, R, p0, array, level)
+
+
+class _RadiatorStored(torch.autograd.Function):
+    """The same traces, but the forward also stores every pair's window
+    record (20 bytes per pair) for the backward, which then reads them
+    instead of recomputing the geometry: the stored-window alternative to
+    _Radiator, kept to measure the trade."""
+
+    @staticmethod
+    def forward(ctx, x, y, z, R, p0, array, level):
+        balls = torch.stack([x, y, z, R, p0]).contiguous()
+        array.set_sampling_level(level)
+        S = array.forward(balls)
+        rec = array.store_windows(balls)
+        ctx.save_for_backward(balls, rec)
+        ctx.array, ctx.level = array, level
+        return S
+
+    @staticmethod
+    def backward(ctx, gS):
+        balls, rec = ctx.saved_tensors
+        ctx.array.set_sampling_level(ctx.level)
+        g = ctx.array.adjoint_stored(balls, gS.contiguous(), rec, mask=MASK_ALL)
+        return g[0], g[1], g[2], g[3], g[4], None, None
+
+
+def radiate_stored(array: SensorArray, x, y, z, R, p0, level: int = 0) -> torch.Tensor:
+    """radiate() with stored per-pair windows instead of recomputation."""
+    return _RadiatorStored.apply(x, y, z, R, p0, array, level)
 
 
 # --------------------------------------------------------------------------
