@@ -463,7 +463,7 @@ def test_reconstruct_matches_oracle_loop(sb):
 
 
 def test_fifty_iteration_run_matches_the_oracle_loop(sb):
-    """The 2,000-ball x 64-sensor configuration as its survey states it:
+    """The whole plain-method run of the 2,000-ball x 64-sensor case:
     zero-gradient filtering, then 50 Adam iterations of forward, adjoint and
     filter/grow at 40 MHz, through sbp_reconstruct against the oracle's loop.
     Ball counts per iteration are compared exactly; losses within 1e-3 (float32
@@ -657,6 +657,28 @@ def test_tile_choices_and_autotune(sb):
         g = arr.adjoint(balls, Gd).cpu().numpy()
         for c in range(5):
             assert rel_l2(g[c, pick], ref[c]) <= GRAD_TOL, (f, "tuned", c)
+
+
+def test_forward_tiles_with_a_ragged_sensor_group(sb):
+    """20 sensors: one group of 32 lanes with 12 empty ones. Every tile shape
+    gives the default's traces bit for bit, at parity with the oracle, also
+    where windows spill past the record's end (T = 600)."""
+    wl = workloads.tiny(M=20, T=600)
+    b = wl.init.stack()
+    arr = make_array(sb, wl, (2, 1), b.shape[1])
+    balls = torch.from_numpy(b).cuda()
+    W = sb.TILE_WIDE
+    for k, f in enumerate((2, 1)):
+        arr.set_sampling_level(k)
+        arr.set_tiles(k, 0, 0)
+        S0 = arr.forward(balls).clone()
+        ref = oracle.forward(b, wl.sensors.pos, wl.sensors.normal, wl.c, dt_of(wl, f),
+                             -(-wl.T // f), threads=threads())
+        assert rel_l2(S0.cpu().numpy(), ref) <= TRACE_TOL
+        for tile in (32, 2048, 32 | W, 512 | W, 2048 | W):
+            arr.set_tiles(k, tile, 0)
+            assert torch.equal(arr.forward(balls), S0), (f, tile)
+        arr.set_tiles(k, 0, 0)
 
 
 @pytest.mark.parametrize("sort", [False, True])
