@@ -27,28 +27,39 @@ def large():
     return workloads.large()
 
 
-def test_large_forward_and_adjoint_sampled(sb, large):
+# (level, forward tile): the default tile and the tiles the benchmark's tuner
+# picks for the step (2048 balls per CTA, the wide window at 40 and 80 MHz)
+CASES = [(2, 0), (2, 2048 | 0x10000), (1, 2048 | 0x10000), (0, 2048)]
+
+
+@pytest.mark.parametrize("k,tile", CASES)
+def test_large_forward_and_adjoint_sampled(sb, large, k, tile):
     wl = large
     n = wl.init.n
     arr = sb.SensorArray(wl.sensors.pos, wl.sensors.normal, wl.c, wl.fs_mhz, wl.T, wl.levels,
                          n_cap=n)
     b = wl.init.stack()
     B = torch.from_numpy(b).cuda()
-    k = len(wl.levels) - 1  # 80 MHz, T = 8192
+    f = wl.levels[k]
+    Tk = wl.T // f
     arr.set_sampling_level(k)
+    arr.set_tiles(k, tile, 0)
     S = arr.forward(B).cpu().numpy()
     assert arr.sync_status() == 0
-    rng = np.random.default_rng(0)
+    rng = np.random.default_rng(k)
     ms = rng.choice(wl.sensors.M, size=3, replace=False)
-    ref = oracle.forward(b, wl.sensors.pos[ms], wl.sensors.normal[ms], wl.c, 1.0 / wl.fs_mhz,
-                         wl.T, threads=oracle.num_procs())
+    ref = oracle.forward(b, wl.sensors.pos[ms], wl.sensors.normal[ms], wl.c, f / wl.fs_mhz,
+                         Tk, threads=oracle.num_procs())
     for r, m in enumerate(ms):
         assert np.linalg.norm(S[m] - ref[r]) / np.linalg.norm(ref[r]) <= 1e-5
-    G = rng.normal(size=(wl.sensors.M, wl.T)).astype(np.float32)
+    if tile:  # every tile renders the default's traces bit for bit
+        arr.set_tiles(k, 0, 0)
+        assert np.array_equal(arr.forward(B).cpu().numpy(), S)
+    G = rng.normal(size=(wl.sensors.M, Tk)).astype(np.float32)
     g = arr.adjoint(B, torch.from_numpy(G).cuda()).cpu().numpy()
     idx = rng.choice(n, size=64, replace=False)
-    gref = oracle.adjoint(b[:, idx], wl.sensors.pos, wl.sensors.normal, wl.c, 1.0 / wl.fs_mhz,
-                          wl.T, G, threads=oracle.num_procs())
+    gref = oracle.adjoint(b[:, idx], wl.sensors.pos, wl.sensors.normal, wl.c, f / wl.fs_mhz,
+                          Tk, G, threads=oracle.num_procs())
     for c in range(5):
         err = np.linalg.norm(g[c, idx] - gref[c]) / np.linalg.norm(gref[c])
         assert err <= 1e-4, (c, err)
