@@ -58,6 +58,30 @@ __device__ __forceinline__ int g_frac_bits(unsigned int bits) {
     return F < 0 ? 0 : (F > 60 ? 60 : F);
 }
 
+// Calls f(k, g(b_k), b_k) for k = klo .. khi, b_k = e - k h, g(b) = 2^(b^2 nc),
+// by the ratio recurrence g_{k+1} = g_k r_k, r_{k+1} = r_k q with
+// r_k = 2^((h^2 - 2 b_k h) nc) and q = 2^(2 h^2 nc), restarted from exp2f
+// every 8 boundaries: two exp2f per 8 values instead of eight. Against the
+// exact Gaussian, in float32 over a in [0.05, 0.4] mm and h from 0.019 to
+// 0.15 mm, values above 1e-4 of the peak are off by 5e-7 rms and 9e-6 at
+// worst (exp2f of the rounded argument alone: 2.5e-6 at worst).
+template <typename F>
+__device__ __forceinline__ void g_gauss_run(int klo, int khi, float e, float h, float nc, F&& f) {
+    const float h2 = h * h;
+    const float q = exp2f(2.0f * h2 * nc);
+    for (int k0 = klo; k0 <= khi; k0 += 8) {
+        const float b0 = fmaf(-(float)k0, h, e);
+        float gk = exp2f(b0 * b0 * nc);
+        float rk = exp2f(fmaf(-2.0f * h, b0, h2) * nc);
+        const int kend = min(k0 + 7, khi);
+        for (int k = k0; k <= kend; ++k) {
+            f(k, gk, fmaf(-(float)k, h, e));
+            gk *= rk;
+            rk *= q;
+        }
+    }
+}
+
 __global__ void gpmax_kernel(const float* __restrict__ p0, const int* n_dev, int n_cap,
                              unsigned int* bits) {
     const int n = sbp_read_n(n_dev, n_cap);
@@ -162,13 +186,22 @@ gfwd_group_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restri
             // (which lie inside the record 0 .. Tk)
             const int klo = max(k0, base - jr), khi = min(k1, base + lim - jr);
             unsigned int* cb = col + (jr - base) * 32;
-            for (int k = klo; k <= khi; ++k) {
-                const float bj = fmaf(-(float)k, h, e);
-                const long long v = g_f2ll(Ks * exp2f(bj * bj * nc));
-                if (v == 0) continue;
-                atomicAdd(cb + k * 32, (unsigned int)v);
-                atomicAdd(cb + k * 32 + kGWindow * 32, (unsigned int)(int)(v >> kGLoBits));
-            }
+            // g at consecutive boundaries by the ratio recurrence (g_gauss_run);
+            // every value is at most Ks, so below 2^30 a 32-bit conversion and
+            // 32-bit words do (their arithmetic shift gives the 64-bit one's
+            // high word)
+            const bool small = fabsf(Ks) < 1073741824.0f;
+            g_gauss_run(klo, khi, e, h, nc, [&](int k, float gk, float) {
+                if (small) {
+                    const int v = __float2int_rn(Ks * gk);
+                    atomicAdd(cb + k * 32, (unsigned int)v);
+                    atomicAdd(cb + k * 32 + kGWindow * 32, (unsigned int)(v >> kGLoBits));
+                } else {
+                    const long long v = g_f2ll(Ks * gk);
+                    atomicAdd(cb + k * 32, (unsigned int)v);
+                    atomicAdd(cb + k * 32 + kGWindow * 32, (unsigned int)(int)(v >> kGLoBits));
+                }
+            });
         }
         __syncthreads();
         const int used = min(wmax - p * kGWindow, kGWindow) * 32;
@@ -266,6 +299,8 @@ gadj_kernel(BallsDev b, const int* n_dev, int n_cap, const float* __restrict__ s
             const int klo = max(k0, -jr), khi = min(k1, Tk - jr);
             int j = jr + klo;
             float gprev = j >= 1 ? Gm[j - 1] : 0.0f;
+            // (one exp2f per boundary here: the ratio recurrence of the
+            // forward made this loop, which waits on its loads of G, slower)
             for (int k = klo; k <= khi; ++k, ++j) {
                 const float gcur = j < Tk ? Gm[j] : 0.0f;
                 const float cj = gprev - gcur;
