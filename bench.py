@@ -689,8 +689,11 @@ def run_native(args, rank, world, local):
             "clocks": vclk, "roofline": roofline(vlevels, vclk, probes),
             "zero_gradient_adjoint": {"pairs": vzero["pairs"], "ms": vzero["ms"]}}
         vwl = vctx.wl
-        result["time_to_residual"] = time_to_residual(sb, vctx.arr, vwl, vctx.y_full,
-                                                      vctx.init, vctx.n0)
+        try:
+            result["time_to_residual"] = time_to_residual(sb, vctx.arr, vwl, vctx.y_full,
+                                                          vctx.init, vctx.n0)
+        except Exception as exc:  # keep the main measurement if this part fails
+            result["time_to_residual"] = {"error": f"{type(exc).__name__}: {exc}"}
         if not args.no_learned:
             try:
                 result["learned_init"] = learned_init(
