@@ -143,6 +143,56 @@ def test_record_hash_follows_the_kernel_not_host_declarations(monkeypatch, tmp_p
     assert bench.sources_sha("adjoint") != base
 
 
+def test_run_to_residual_interpolates_every_crossing(monkeypatch):
+    """run_to_residual with a fake array whose segments take 1 ms of device
+    time each and a residual falling 0.9, 0.6, 0.4, 0.25, 0.15: the target
+    (0.2) and the looser targets (0.5, 0.3) are reached at the linear
+    interpolation of their two neighbouring checkpoints."""
+    torch = pytest.importorskip("torch")
+
+    class FakeEvent:
+        clock = [0.0]
+
+        def __init__(self, enable_timing=True):
+            self.t = None
+
+        def record(self, stream=None):
+            self.t = FakeEvent.clock[0]
+
+        def elapsed_time(self, other):
+            return other.t - self.t
+
+    class FakeArr:
+        def reconstruct(self, *args, **kwargs):
+            FakeEvent.clock[0] += 1.0  # 1 ms per segment
+
+    class FakeSb:
+        KEEP_NEG = 0
+
+        @staticmethod
+        def Stage(*a):
+            return a
+
+        @staticmethod
+        def GrowParams(**kw):
+            return kw
+
+    monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    seq = iter([0.9, 0.6, 0.4, 0.25, 0.15])
+    init = torch.zeros((5, 8))
+    out = bench.run_to_residual(FakeSb, FakeArr(), None, None, init, 8,
+                                iter([(0, 3)] * 10), True, 0.2, 10, 1000,
+                                lambda balls, n: next(seq), also=(0.5, 0.3, 0.2))
+    # checkpoints (ms, r): (1, .9) (2, .6) (3, .4) (4, .25) (5, .15)
+    assert out["iterations"] == 50 and out["final_rel_residual"] == 0.15
+    assert abs(out["seconds"] - (4.0 + (0.25 - 0.2) / (0.25 - 0.15)) * 1e-3) < 1e-12
+    to = out["seconds_to"]
+    assert abs(to["0.5"] - (2.0 + (0.6 - 0.5) / (0.6 - 0.4)) * 1e-3) < 1e-12
+    assert abs(to["0.3"] - (3.0 + (0.4 - 0.3) / (0.4 - 0.25)) * 1e-3) < 1e-12
+    assert abs(to["0.2"] - out["seconds"]) < 1e-15
+
+
 def test_stage_schedules():
     """Coarse stage (p0 and R) 40 iterations per level coarse to fine, then
     the fine stage (all components) 30 per coarser level and the rest at the
