@@ -200,16 +200,32 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+def _on_current_device(t: torch.Tensor):
+    """Every pointer handed to the library is device memory of the current
+    device, where its kernels run: a host tensor or one on another GPU is
+    refused here, before anything is enqueued."""
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor, got one on " + str(t.device))
+    cur = torch.cuda.current_device()
+    if t.device.index != cur:
+        raise ValueError(f"tensor on {t.device}, but the current device is cuda:{cur} "
+                         "(select it with torch.cuda.set_device)")
+
+
 def _rows(t: torch.Tensor) -> _Balls:
     if t.dtype != torch.float32 or not t.is_cuda or t.dim() != 2 or t.shape[0] != 5 \
             or not t.is_contiguous():
         raise ValueError("expected a contiguous (5, n) float32 CUDA tensor")
+    _on_current_device(t)
     base, stride = t.data_ptr(), t.stride(0) * 4
     return _Balls(*(base + k * stride for k in range(5)))
 
 
 def _dptr(t):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+    if t is None:
+        return None
+    _on_current_device(t)
+    return ctypes.c_void_p(t.data_ptr())
 
 
 @dataclasses.dataclass

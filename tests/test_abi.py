@@ -147,3 +147,17 @@ def test_forward_static_binding_checks_its_arguments_on_the_host():
     for sensors in (on_host, three_rows, doubles):
         with pytest.raises(ValueError):
             slingbag.forward_static(sensors, 1.5, 0.025, 16, balls)
+
+
+def test_pointers_must_be_device_memory():
+    """The binding refuses host tensors for every device pointer, before any
+    call into the library (a host pointer would reach a kernel)."""
+    import torch
+
+    from paper_2601_00551_gb300 import slingbag as sb
+
+    with pytest.raises(ValueError):
+        sb._dptr(torch.zeros(4))
+    with pytest.raises(ValueError):
+        sb._rows(torch.zeros((5, 4)))
+    assert sb._dptr(None) is None
