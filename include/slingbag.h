@@ -396,6 +396,15 @@ int sbp_adam_step_frames(sbp_array arr, sbp_balls packed, sbp_grads grads, sbp_b
 int sbp_reconstruct_frames(sbp_array arr, const float* y_full_dev, sbp_balls packed, int* n_dev,
                            const sbp_recon_params* rp, sbp_stream stream);
 
+/* Tiles of the batched path (the values sbp_autotune_frames chooses, or the
+ * caller's own): the forward's balls per CTA, 0 (default: 512) or a power of
+ * two in [32, 1024] optionally or'ed with SBP_TILE_WIDE, and the adjoint's
+ * CTAs per ball chunk, 0 (default 8), 1, 2, 4 or 8. Launch parameters only:
+ * the forward's traces are the same bit for bit for every choice. SBP_ERR_ARG
+ * for other values or an array without a frame layout. */
+int sbp_set_frame_tiles(sbp_array arr, int fwd_chunk, int adj_split);
+int sbp_get_frame_tiles(sbp_array arr, int* fwd_chunk, int* adj_split);
+
 /* Tile autotuner for the batched path: times the forward with 256, 512 and
  * 1024 balls per CTA and 1024 with SBP_TILE_WIDE, and the adjoint with 1, 2, 4 and 8 CTAs per ball chunk on
  * the given cloud at the current level (S_dev, G_dev: [F][M][T_k] scratch of

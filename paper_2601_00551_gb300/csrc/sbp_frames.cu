@@ -300,6 +300,30 @@ int sbp_reconstruct_frames(sbp_array arr, const float* y_full_dev, sbp_balls bal
     return SBP_OK;
 }
 
+int sbp_set_frame_tiles(sbp_array arr, int fwd_chunk, int adj_split) {
+    if (int e = check_frames(arr, "set_frame_tiles")) return e;
+    // a chunk must not straddle two frames: at most one alignment unit
+    const bool chunk_ok = fwd_chunk == 0 || (sbp_fwd_tile_valid(fwd_chunk) &&
+                                             (fwd_chunk & ~SBP_TILE_WIDE) <= SBP_FRAME_ALIGN);
+    const bool split_ok = adj_split == 0 || adj_split == 1 || adj_split == 2 || adj_split == 4 ||
+                          adj_split == 8;
+    if (!chunk_ok || !split_ok) {
+        sbp_set_error("set_frame_tiles: chunk must be 0 or a power of two in [32, 1024] "
+                      "(optionally with SBP_TILE_WIDE), split 0, 1, 2, 4 or 8");
+        return SBP_ERR_ARG;
+    }
+    arr->fwd_chunk_frames = fwd_chunk;
+    arr->adj_split_frames = adj_split;
+    return SBP_OK;
+}
+
+int sbp_get_frame_tiles(sbp_array arr, int* fwd_chunk, int* adj_split) {
+    if (int e = check_frames(arr, "get_frame_tiles")) return e;
+    if (fwd_chunk) *fwd_chunk = arr->fwd_chunk_frames;
+    if (adj_split) *adj_split = arr->adj_split_frames;
+    return SBP_OK;
+}
+
 int sbp_autotune_frames(sbp_array arr, sbp_balls balls, const int* n_dev, float* S_dev,
                         float* G_dev, int* fwd_chunk_out, int* adj_split_out) {
     if (int e = check_frames(arr, "autotune_frames")) return e;

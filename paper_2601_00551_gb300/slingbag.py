@@ -124,6 +124,9 @@ _SIGS = {
                                             ctypes.POINTER(_AdamParams), ctypes.c_uint, _P]),
     "sbp_reconstruct_frames": (ctypes.c_int, [_P, _P, _Balls, _P, ctypes.POINTER(_ReconParams),
                                               _P]),
+    "sbp_set_frame_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "sbp_get_frame_tiles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]),
     "sbp_autotune_frames": (ctypes.c_int, [_P, _Balls, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int)]),
     "sbp_set_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -685,6 +688,17 @@ class SensorArray:
             self._h, _dptr(y_full), _rows(balls), _dptr(n_dev), ctypes.byref(rp), _stream()))
         if stages:
             self.level = stages[-1].level
+
+    def set_frame_tiles(self, fwd_chunk: int = 0, adj_split: int = 0):
+        """Tiles of the batched path (sbp_set_frame_tiles; 0 = default)."""
+        _check("sbp_set_frame_tiles", self._lib.sbp_set_frame_tiles(self._h, fwd_chunk,
+                                                                    adj_split))
+
+    def get_frame_tiles(self):
+        c, sp = ctypes.c_int(), ctypes.c_int()
+        _check("sbp_get_frame_tiles", self._lib.sbp_get_frame_tiles(self._h, ctypes.byref(c),
+                                                                    ctypes.byref(sp)))
+        return c.value, sp.value
 
     def autotune_frames(self, balls, n_dev):
         """Tile autotuner of the batched path (sbp_autotune_frames); returns

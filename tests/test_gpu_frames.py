@@ -153,6 +153,40 @@ def test_autotune_frames_keeps_results(sb):
     assert torch.equal(arr.forward_frames(packed, n_dev), S0)
 
 
+def test_frame_tiles_change_only_the_launch(sb):
+    """Every forward tile of the batched path, narrow or wide, renders the
+    default's traces bit for bit; every adjoint split gives the default's
+    gradients within float summation order; invalid tiles are refused."""
+    wl, arr, single, off, packed, n_dev, clouds = setup(sb)
+    W = sb.TILE_WIDE
+    with pytest.raises(sb.SlingbagError):
+        arr.set_frame_tiles(2048, 0)  # a chunk would straddle two frames
+    with pytest.raises(sb.SlingbagError):
+        arr.set_frame_tiles(0, 3)
+    rng = np.random.default_rng(5)
+    for k in range(2):
+        arr.set_sampling_level(k)
+        arr.set_frame_tiles(0, 0)
+        S0 = arr.forward_frames(packed, n_dev).clone()
+        G = torch.from_numpy(rng.normal(size=(len(COUNTS), wl.sensors.M, arr.Tk))
+                             .astype(np.float32)).cuda()
+        g0 = arr.adjoint_frames(packed, n_dev, G).cpu().numpy()
+        for tile in (32, 256, 1024, 32 | W, 1024 | W):
+            arr.set_frame_tiles(tile, 0)
+            assert arr.get_frame_tiles() == (tile, 0)
+            assert torch.equal(arr.forward_frames(packed, n_dev), S0), (k, tile)
+        for split in (1, 2, 4, 8):
+            arr.set_frame_tiles(0, split)
+            g = arr.adjoint_frames(packed, n_dev, G).cpu().numpy()
+            for f in range(len(COUNTS)):
+                sl = slice(off[f], off[f] + COUNTS[f])
+                for c in range(5):
+                    ref = g0[c, sl]
+                    err = np.linalg.norm(g[c, sl] - ref) / max(np.linalg.norm(ref), 1e-30)
+                    assert err <= 1e-5, (k, split, f, c)
+    arr.set_frame_tiles(0, 0)
+
+
 def test_reconstruct_frames_replays_in_cuda_graph(sb):
     wl, arr, single, off, packed, n_dev, clouds = setup(sb)
     F = len(COUNTS)
