@@ -533,13 +533,23 @@ adj_group_kernel(BallsDev b, FrameTable ft, const float* __restrict__ sens, Leve
                     const int Lm = max(LA, LB);
                     float2 run = f2(0.f);
                     int q = Lm - 1;
-                    for (; q >= 2; q -= 2) {
-                        const float2 d1 = f2add(make_float2(GwA[q], GwB[q]), ngl);
-                        const float2 d0 = f2add(make_float2(GwA[q - 1], GwB[q - 1]), ngl);
-                        run = f2add(run, d1);
-                        E1 = f2add(E1, run);
-                        run = f2add(run, d0);
-                        E1 = f2add(E1, run);
+                    if (q >= 2) {
+                        // cells q and q - 1 loaded one step ahead (q - 3 >= -1
+                        // stays inside the staged window)
+                        float2 c1 = make_float2(GwA[q], GwB[q]);
+                        float2 c0 = make_float2(GwA[q - 1], GwB[q - 1]);
+                        for (; q >= 2; q -= 2) {
+                            const float2 n1 = make_float2(GwA[q - 2], GwB[q - 2]);
+                            const float2 n0 = make_float2(GwA[q - 3], GwB[q - 3]);
+                            const float2 d1 = f2add(c1, ngl);
+                            const float2 d0 = f2add(c0, ngl);
+                            run = f2add(run, d1);
+                            E1 = f2add(E1, run);
+                            run = f2add(run, d0);
+                            E1 = f2add(E1, run);
+                            c1 = n1;
+                            c0 = n0;
+                        }
                     }
                     if (q == 1) {
                         run = f2add(run, f2add(make_float2(GwA[1], GwB[1]), ngl));
