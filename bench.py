@@ -526,8 +526,8 @@ NCU_RECORD = {
                 "thread_inst_per_pair": 175.2},
     "adjoint": {"sources": ["paper_2601_00551_gb300/csrc/sbp_adjoint.cu",
                             "paper_2601_00551_gb300/csrc/sbp_internal.cuh"],
-                "sha256": "7ea5bec7147c4b1e", "bytes": 6.5840128e7,
-                "thread_inst_per_pair": 203.5},
+                "sha256": "d61d68a8bdd49168", "bytes": 6.53376e7,
+                "thread_inst_per_pair": 205.3},
 }
 
 
